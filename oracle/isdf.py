@@ -1,0 +1,467 @@
+"""Plain FP64 NumPy/SciPy multigrid ISDF and THC exchange (test oracle).
+
+TEST INFRASTRUCTURE ONLY (see the package docstring).  Nothing here is tuned;
+every step follows the paper's definitions in the paper's order:
+
+  * Section II ("THEORY"): THC form of the ERIs, interpolative decomposition of
+    the pair densities (mu nu | R) = sum_xi (mu nu | xi) xi(R), and the
+    two-centre Coulomb matrix (xi|xi') of Eq. 1 evaluated with FFTs.
+  * Section II.A: Eq. 2 (M(R,R') = sum_{mu nu} (mu nu|R)(mu nu|R')), pivoted
+    Cholesky on M for the interpolation points, Eq. 3 (least-squares fit of the
+    interpolation vectors xi(R)).
+  * Section II.B / III: the basis is split by exponent; a product is only
+    represented on the grid of its sharper factor (Eq. 7 with the L / G / N
+    function sets).
+  * Section III.A: the four-term multigrid THC form of the ERIs, Eq. 8, used to
+    build the exchange matrix.
+
+Readings of places where the paper is silent or garbled (each also listed in
+the design notes):
+  R1 levels: a function of exponent a lives on level l = #{edges e : a < e};
+     level 0 is the finest grid.  Level l holds the pairs whose sharper factor
+     is on level l: L_l = {mu: l(mu)=l}, N_l = {mu: l(mu)>l}, G_l = L_l u N_l.
+     The pair set of level l is (L_l x G_l) u (N_l x L_l) (ordered pairs), so
+     M_l = A_L o A_L + 2 A_L o A_N with A_X(g,g') = sum_{mu in X} phi_mu(g) phi_mu(g').
+  R2 selection: one greedy pivoted Cholesky over the block-diagonal matrix
+     (+)_l w_l M_l with w_l = dV_l (grid volume element), so a pivot value is a
+     quadrature of squared pair density on every level.
+  R3 ties: among points with d >= d_max - max(tie_rel*d_max, tie_abs*d_0) the
+     smallest (level, g) wins; the chosen point's residual is then set to 0.
+  R4 fit regularisation: lambda = reg_rel * tr(CC^T) / k_l (per level).
+  R5 Coulomb: every grid function stands for its trigonometric interpolant (a
+     coefficient whose mode sits at +-n/2 on an axis is split evenly between
+     the two); (f|g) is the exact periodic Coulomb integral of the interpolants
+     with the G=0 term dropped.  Cross-level pairs therefore sum over the
+     coarser level's (extended) mode set.
+  R6 Eq. 8 reading: c_{mu lam}(P) = X^L_{mu P} X^G_{lam P} + X^N_{mu P} X^L_{lam P}
+     where X^L_{mu P} = phi_mu(P) for mu in L_{l(P)} (else 0) and X^N likewise
+     for N_{l(P)}; (mu lam|sig nu) = sum_PQ c_{mu lam}(P) V_PQ c_{sig nu}(Q).
+  R7 images: on an orthorhombic cell the image sum of a Cartesian Gaussian is
+     taken over the box of lattice translations t (per axis) whose shifted
+     centre A + t L lies within r_cut = sqrt(ln(1/image_tol)/alpha) of [0, L].
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+import scipy.linalg
+
+PIVOT_SHIFT = 40  # pivot code = (level << 40) | g
+
+
+# ---------------------------------------------------------------------------
+# Basis functions and levels (Section II.B / III, Fig. Grids; reading R1, R7)
+# ---------------------------------------------------------------------------
+
+
+def expand_functions(system):
+    """Expand the shell list into functions (atom, alpha, lx, ly, lz, norm, level).
+
+    Normalisation of an uncontracted Cartesian Gaussian x^l exp(-alpha r^2):
+    s: (2 alpha/pi)^(3/4); p: (2 alpha/pi)^(3/4) * 2 sqrt(alpha).
+    Level of a function (reading R1): the number of level edges above alpha.
+    """
+    edges = np.asarray(system["level_min_exp"], dtype=np.float64)
+    atom, alpha, lvec, norm, level = [], [], [], [], []
+    for ia, l, e in zip(system["shell_atom"], system["shell_l"], system["shell_exp"]):
+        comps = [(0, 0, 0)] if l == 0 else [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+        for c in comps:
+            atom.append(int(ia))
+            alpha.append(float(e))
+            lvec.append(c)
+            nrm = (2.0 * e / math.pi) ** 0.75
+            if l == 1:
+                nrm *= 2.0 * math.sqrt(e)
+            norm.append(nrm)
+            level.append(int(np.sum(float(e) < edges)))
+    return {
+        "atom": np.array(atom, dtype=np.int64),
+        "alpha": np.array(alpha),
+        "lvec": np.array(lvec, dtype=np.int64),
+        "norm": np.array(norm),
+        "level": np.array(level, dtype=np.int64),
+    }
+
+
+def level_sets(funcs, lev):
+    """(L, N, G) index arrays for level ``lev`` (reading R1, Eq. 7 notation)."""
+    fl = funcs["level"]
+    L = np.flatnonzero(fl == lev)
+    N = np.flatnonzero(fl > lev)
+    G = np.flatnonzero(fl >= lev)
+    return L, N, G
+
+
+def _images_1d(A, L, alpha, tol):
+    """Lattice translations t (integers) kept for one axis (reading R7)."""
+    rcut = math.sqrt(math.log(1.0 / tol) / alpha)
+    tmax = int(math.ceil((rcut + L) / L)) + 1
+    keep = []
+    for t in range(-tmax, tmax + 1):
+        c = A + t * L
+        dist = 0.0 if 0.0 <= c <= L else min(abs(c), abs(c - L))
+        if dist <= rcut:
+            keep.append(t)
+    return keep
+
+
+def _periodic_gaussian_1d(x, A, L, alpha, l, tol):
+    out = np.zeros_like(x)
+    for t in _images_1d(A, L, alpha, tol):
+        u = x - A - t * L
+        out += (u ** l) * np.exp(-alpha * u * u)
+    return out
+
+
+def grid_points_1d(system, lev):
+    n = system["grids"][lev]
+    return [np.arange(n[a]) * (system["edges"][a] / n[a]) for a in range(3)]
+
+
+def basis_on_level(system, funcs, idx, lev):
+    """Phi[f, g] = phi_idx[f](r_g) on level ``lev``; g = i + nx (j + ny k).
+
+    The image-summed Cartesian Gaussian on an orthorhombic lattice is a
+    product of three 1-D image sums (the Gaussian and the monomial both
+    separate over x, y, z and the kept translations form a box), so each
+    function is the outer product of three 1-D periodic factors.  Pinned
+    against ``basis_direct`` (literal 3-D image sum) and against the
+    Poisson-summation Fourier series.
+    """
+    xs = grid_points_1d(system, lev)
+    n = system["grids"][lev]
+    tol = system["image_tol"]
+    out = np.empty((len(idx), int(n[0] * n[1] * n[2])))
+    for r, mu in enumerate(idx):
+        A = system["xyz"][funcs["atom"][mu]]
+        a = funcs["alpha"][mu]
+        f = [
+            _periodic_gaussian_1d(xs[ax], A[ax], system["edges"][ax], a, funcs["lvec"][mu][ax], tol)
+            for ax in range(3)
+        ]
+        # array index [k, j, i] -> flat g = i + nx (j + ny k)
+        out[r] = funcs["norm"][mu] * np.einsum("k,j,i->kji", f[2], f[1], f[0]).ravel()
+    return out
+
+
+def basis_direct(system, funcs, idx, lev):
+    """Literal 3-D image sum of each function over the kept translations."""
+    xs = grid_points_1d(system, lev)
+    Z, Y, X = np.meshgrid(xs[2], xs[1], xs[0], indexing="ij")
+    P = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+    tol = system["image_tol"]
+    E = system["edges"]
+    out = np.zeros((len(idx), P.shape[0]))
+    for r, mu in enumerate(idx):
+        A = system["xyz"][funcs["atom"][mu]]
+        a = funcs["alpha"][mu]
+        lv = funcs["lvec"][mu]
+        T = [_images_1d(A[ax], E[ax], a, tol) for ax in range(3)]
+        for tx in T[0]:
+            for ty in T[1]:
+                for tz in T[2]:
+                    u = P - (A + np.array([tx * E[0], ty * E[1], tz * E[2]]))
+                    poly = (u[:, 0] ** lv[0]) * (u[:, 1] ** lv[1]) * (u[:, 2] ** lv[2])
+                    out[r] += poly * np.exp(-a * np.sum(u * u, axis=1))
+        out[r] *= funcs["norm"][mu]
+    return out
+
+
+def level_weight(system, lev):
+    """w_l = dV_l = Omega / N_g,l (reading R2)."""
+    n = system["grids"][lev]
+    return float(np.prod(system["edges"]) / np.prod(n))
+
+
+# ---------------------------------------------------------------------------
+# Point selection: pivoted Cholesky on M (Section II.A, Eq. 2; readings R1-R3)
+# ---------------------------------------------------------------------------
+
+
+def _level_data(system, funcs):
+    nlev = len(system["grids"])
+    out = []
+    for lev in range(nlev):
+        L, N, G = level_sets(funcs, lev)
+        out.append(
+            {
+                "L": L,
+                "N": N,
+                "PhiL": basis_on_level(system, funcs, L, lev),
+                "PhiN": basis_on_level(system, funcs, N, lev),
+                "w": level_weight(system, lev),
+            }
+        )
+    return out
+
+
+def m_columns(ld, cols):
+    """M_l[:, cols] = A_L o (A_L + 2 A_N) at the given grid points (reading R1, Eq. 2)."""
+    AL = ld["PhiL"].T @ ld["PhiL"][:, cols]
+    AN = ld["PhiN"].T @ ld["PhiN"][:, cols]
+    return AL * (AL + 2.0 * AN)
+
+
+def initial_diagonal(ld):
+    """w_l * M_l(g, g) on one level."""
+    aL = np.sum(ld["PhiL"] ** 2, axis=0)
+    aN = np.sum(ld["PhiN"] ** 2, axis=0)
+    return ld["w"] * aL * (aL + 2.0 * aN)
+
+
+def select_points(levels, nip, tol=0.0, tie_rel=1e-9, tie_abs=1e-13, cand=None):
+    """Greedy pivoted Cholesky over (+)_l w_l M_l (Eq. 2; readings R2, R3).
+
+    At step k: d_max = max residual; p = smallest (level, g) with
+    d(p) >= d_max - max(tie_rel d_max, tie_abs d_0); new factor column on
+    p's level  L[:, k] = (w M[:, p] - L[:, :k] L[p, :k]^T) / sqrt(d_p) with
+    L[p, k] = sqrt(d_p); d -= L[:, k]^2; d(p) = 0.  Stops after ``nip``
+    pivots or when d_max < tol * d_0.  ``cand`` optionally restricts the
+    candidate points: a list of pivot codes (level << 40 | g).
+    Returns pivot codes, pivot values d_k and the per-level factor columns.
+    """
+    nlev = len(levels)
+    d = [initial_diagonal(ld) for ld in levels]
+    active = [np.ones(di.shape[0], dtype=bool) for di in d]
+    if cand is not None:
+        active = [np.zeros(di.shape[0], dtype=bool) for di in d]
+        for c in np.asarray(cand, dtype=np.int64):
+            active[int(c >> PIVOT_SHIFT)][int(c & ((1 << PIVOT_SHIFT) - 1))] = True
+    for lev in range(nlev):
+        d[lev] = np.where(active[lev], d[lev], 0.0)
+    # factor columns of each level, stored [g, column] with growing capacity
+    fac = [np.zeros((di.shape[0], min(64, nip))) for di in d]
+    nk = [0] * nlev
+    pivots, dvals = [], []
+    d0 = None
+    for _k in range(nip):
+        dmax = max(float(np.max(di)) if di.size else 0.0 for di in d)
+        if d0 is None:
+            d0 = dmax
+        if dmax <= 0.0 or dmax < tol * d0:
+            break
+        thr = dmax - max(tie_rel * dmax, tie_abs * d0)
+        lev, p = None, None
+        for l in range(nlev):
+            hit = np.flatnonzero(d[l] >= thr)
+            if hit.size:
+                lev, p = l, int(hit[0])
+                break
+        dp = float(d[lev][p])
+        ld = levels[lev]
+        mcol = ld["w"] * m_columns(ld, [p])[:, 0]
+        kl = nk[lev]
+        if kl:
+            Lprev = fac[lev][:, :kl]
+            mcol = mcol - Lprev @ Lprev[p, :]
+        col = mcol / math.sqrt(dp)
+        col[p] = math.sqrt(dp)
+        col = np.where(active[lev], col, 0.0) if cand is not None else col
+        d[lev] = d[lev] - col * col
+        d[lev][p] = 0.0
+        if kl == fac[lev].shape[1]:
+            grown = np.zeros((fac[lev].shape[0], min(2 * kl, nip)))
+            grown[:, :kl] = fac[lev]
+            fac[lev] = grown
+        fac[lev][:, kl] = col
+        nk[lev] = kl + 1
+        pivots.append((lev << PIVOT_SHIFT) | p)
+        dvals.append(dp)
+    return {
+        "pivots": np.array(pivots, dtype=np.int64),
+        "dvals": np.array(dvals),
+        "factor": [fac[l][:, :nk[l]] for l in range(nlev)],
+        "residual": d,
+    }
+
+
+# ---------------------------------------------------------------------------
+# Least-squares fit of the interpolation vectors (Section II.A, Eq. 3; R4)
+# ---------------------------------------------------------------------------
+
+
+def split_pivots(pivots, nlev):
+    pivots = np.asarray(pivots, dtype=np.int64)
+    lev = pivots >> PIVOT_SHIFT
+    g = pivots & ((1 << PIVOT_SHIFT) - 1)
+    return [g[lev == l] for l in range(nlev)]
+
+
+def fit(levels, pivots, reg_rel=1e-14):
+    """Xi_l = (ZC^T)_l (CC^T + lambda I)^-1 on every level (Eq. 3).
+
+    With Z the pair densities of level l (pairs x grid) and C = Z[:, P], the
+    normal equations of min || Z - C Xi^T || give (ZC^T)_l = M_l[:, P] and
+    (CC^T)_l = M_l[P, P].  Solved with an FP64 Cholesky (LAPACK).
+    """
+    out = []
+    for ld, P in zip(levels, split_pivots(pivots, len(levels))):
+        if P.size == 0:
+            out.append(np.zeros((ld["PhiL"].shape[1], 0)))
+            continue
+        ZCt = m_columns(ld, P)
+        CCt = ZCt[P, :]
+        lam = reg_rel * np.trace(CCt) / P.size
+        cf = scipy.linalg.cho_factor(CCt + lam * np.eye(P.size), lower=True)
+        out.append(scipy.linalg.cho_solve(cf, ZCt.T).T)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# Coulomb matrix (xi|xi') by FFT (Section II, Eq. 1; Section III; reading R5)
+# ---------------------------------------------------------------------------
+
+
+def fourier_coeffs(cols, grid):
+    """f~(m) = (1/N_g) sum_g f(r_g) exp(-i G_m . r_g); array [c, mz, my, mx]."""
+    nx, ny, nz = (int(v) for v in grid)
+    F = np.fft.fftn(cols.T.reshape(-1, nz, ny, nx), axes=(1, 2, 3))
+    return F / float(nx * ny * nz)
+
+
+def _interp_coeff(F, grid, mz, my, mx):
+    """Coefficient of the trigonometric interpolant at extended modes (R5)."""
+    nx, ny, nz = (int(v) for v in grid)
+    c = F[:, mz % nz][:, :, my % ny][:, :, :, mx % nx]
+    fz = np.where(np.abs(mz) * 2 == nz, 0.5, 1.0)
+    fy = np.where(np.abs(my) * 2 == ny, 0.5, 1.0)
+    fx = np.where(np.abs(mx) * 2 == nx, 0.5, 1.0)
+    return c * (fz[:, None, None] * fy[None, :, None] * fx[None, None, :])[None]
+
+
+def coulomb_pair(Fa, grid_a, Fb, grid_b, edges):
+    """(f_a | f_b) for all column pairs; grid_b must be the coarser (or same).
+
+    Sum over the extended modes m of the coarser grid, -n/2 <= m <= n/2 per
+    axis, m != 0:  4 pi Omega Re[conj c_a(m) c_b(m)] / |G_m|^2.
+    The sum is accumulated plane by plane in m_z (same sum, bounded memory).
+    """
+    nx, ny, nz = (int(v) for v in grid_b)
+    omega = float(np.prod(edges))
+    my = np.arange(-(ny // 2), ny // 2 + 1)
+    mx = np.arange(-(nx // 2), nx // 2 + 1)
+    V = np.zeros((Fa.shape[0], Fb.shape[0]))
+    for mzv in range(-(nz // 2), nz // 2 + 1):
+        mz = np.array([mzv])
+        ca = _interp_coeff(Fa, grid_a, mz, my, mx).reshape(Fa.shape[0], -1)
+        cb = _interp_coeff(Fb, grid_b, mz, my, mx).reshape(Fb.shape[0], -1)
+        Gz = 2 * math.pi * mzv / edges[2]
+        Gy = 2 * math.pi * my / edges[1]
+        Gx = 2 * math.pi * mx / edges[0]
+        G2 = (Gz * Gz + Gy[:, None] ** 2 + Gx[None, :] ** 2).ravel()
+        kern = np.zeros_like(G2)
+        nz_mask = G2 > 0
+        kern[nz_mask] = 4.0 * math.pi * omega / G2[nz_mask]
+        V += np.real(np.conj(ca) @ (cb * kern[None, :]).T)
+    return V
+
+
+def coulomb(system, Xi):
+    """V = (xi_P | xi_Q) over all levels, in global pivot order per level blocks.
+
+    Returns the full symmetric matrix ordered level by level (level 0 pivots
+    first, each level's pivots in selection order).
+    """
+    nlev = len(Xi)
+    F = [fourier_coeffs(Xi[l], system["grids"][l]) for l in range(nlev)]
+    sizes = [x.shape[1] for x in Xi]
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    V = np.zeros((off[-1], off[-1]))
+    for a in range(nlev):
+        for b in range(a, nlev):
+            if sizes[a] == 0 or sizes[b] == 0:
+                continue
+            blk = coulomb_pair(F[a], system["grids"][a], F[b], system["grids"][b], system["edges"])
+            V[off[a]:off[a + 1], off[b]:off[b + 1]] = blk
+            V[off[b]:off[b + 1], off[a]:off[a + 1]] = blk.T
+    return V
+
+
+# ---------------------------------------------------------------------------
+# Exchange matrix from the four-term multigrid THC form (Section III.A, Eq. 8)
+# ---------------------------------------------------------------------------
+
+
+def level_ordered(pivots, nlev):
+    """Permutation that orders pivots level by level, selection order within."""
+    pivots = np.asarray(pivots, dtype=np.int64)
+    lev = pivots >> PIVOT_SHIFT
+    return np.concatenate([np.flatnonzero(lev == l) for l in range(nlev)]).astype(np.int64)
+
+
+def pivot_factors(system, funcs, pivots):
+    """X^L and X^N (N x N_ip, level-ordered pivot columns), reading R6."""
+    nlev = len(system["grids"])
+    per = split_pivots(pivots, nlev)
+    nfun = funcs["level"].shape[0]
+    XL = np.zeros((nfun, sum(p.size for p in per)))
+    XN = np.zeros_like(XL)
+    c0 = 0
+    for lev in range(nlev):
+        P = per[lev]
+        if P.size == 0:
+            continue
+        L, N, _ = level_sets(funcs, lev)
+        XL[L, c0:c0 + P.size] = basis_on_level(system, funcs, L, lev)[:, P]
+        XN[N, c0:c0 + P.size] = basis_on_level(system, funcs, N, lev)[:, P]
+        c0 += P.size
+    return XL, XN
+
+
+def exchange(XL, XN, V, C):
+    """K_{mu nu} = sum_{lam sig} D_{lam sig} (mu lam|sig nu), D = C C^T (Eq. 8, R6).
+
+    With c(P) the N x N matrix c_{mu lam}(P), E(P) = c(P) C and
+    K = sum_PQ V_PQ c(P) D c(Q) = sum_P E(P) (sum_Q V_PQ E(Q))^T.
+    E_x = -Tr(D K).
+    """
+    XG = XL + XN
+    yG = C.T @ XG  # (n, nip): y_G(P) = C^T x_G(P)
+    yL = C.T @ XL
+    # E[P, mu, i] = XL[mu,P] yG[i,P] + XN[mu,P] yL[i,P]
+    E = XL.T[:, :, None] * yG.T[:, None, :] + XN.T[:, :, None] * yL.T[:, None, :]
+    Fv = np.tensordot(V, E, axes=(1, 0))  # sum_Q V_PQ E(Q)
+    K = np.einsum("pmi,pni->mn", E, Fv)
+    D = C @ C.T
+    Ex = -float(np.sum(D * K))
+    return K, Ex
+
+
+# ---------------------------------------------------------------------------
+# Whole path
+# ---------------------------------------------------------------------------
+
+
+def run(system, C, nip, tol=0.0, tie_rel=1e-9, tie_abs=1e-13, reg_rel=1e-14, pivots=None, cand=None):
+    """Selection -> fit -> Coulomb -> exchange, all FP64 on the CPU.
+
+    If ``pivots`` is given the selection is skipped and those pivots are fitted
+    (used to judge the later steps on their own).
+    """
+    funcs = expand_functions(system)
+    levels = _level_data(system, funcs)
+    sel = None
+    if pivots is None:
+        sel = select_points(levels, nip, tol, tie_rel, tie_abs, cand)
+        pivots = sel["pivots"]
+    pivots = np.asarray(pivots, dtype=np.int64)
+    Xi = fit(levels, pivots, reg_rel)
+    V = coulomb(system, Xi)
+    order = level_ordered(pivots, len(levels))
+    XL, XN = pivot_factors(system, funcs, pivots)
+    K, Ex = exchange(XL, XN, V, C)
+    return {
+        "pivots": pivots,
+        "dvals": None if sel is None else sel["dvals"],
+        "sel": sel,
+        "levels": levels,
+        "funcs": funcs,
+        "Xi": Xi,
+        "V": V,
+        "order": order,
+        "XL": XL,
+        "XN": XN,
+        "K": K,
+        "Ex": Ex,
+    }

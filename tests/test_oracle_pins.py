@@ -1,0 +1,359 @@
+"""Pins of the FP64 oracle against things other than itself.
+
+Each test ties one oracle function to the paper's definitions or to
+mathematics: closed forms (Poisson summation, analytic Gaussian Coulomb
+series), textbook routines (pivoted QR / LAPACK dpstrf, least squares),
+brute force (the 4-index tensor), exact reproduction at full pair rank, and
+invariants (symmetry, PSD, monotone fall, interpolation identity).
+"""
+import math
+
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle
+from oracle import isdf as O
+from paper_2404_09373_gb300 import systems as S
+
+ONE_ATOM = np.array([[0.11, 0.23, 0.31]])
+TWO_ATOMS = np.array([[0.1, 0.2, 0.3], [0.55, 0.6, 0.7]])
+
+
+def tiny(levels=1, n=(16, 8, 4), sites=ONE_ATOM, a=4.0, tol=1e-10):
+    grids = tuple((m, m, m) for m in n[:levels])
+    edges = (1.6, 0.4)[: levels - 1]
+    return S.make_system((1, 1, 1), 0.0, None, grids, edges, a=a, sites=sites, image_tol=tol)
+
+
+def orbitals(sysd, n_occ=2, seed=1):
+    return S.make_orbitals(sysd, n_occ, np.random.default_rng(seed))
+
+
+# --------------------------------------------------------------------------- basis
+
+
+def test_basis_separable_equals_direct_image_sum():
+    sysd = tiny(sites=TWO_ATOMS, n=(10,), a=4.5)
+    f = O.expand_functions(sysd)
+    idx = np.arange(f["level"].size)
+    a = O.basis_on_level(sysd, f, idx, 0)
+    b = O.basis_direct(sysd, f, idx, 0)
+    assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(a))
+
+
+@pytest.mark.parametrize("alpha,lx", [(0.1, 0), (1.6, 0), (6.4, 0), (0.6, 1), (2.4, 1)])
+def test_basis_matches_poisson_summation(alpha, lx):
+    """Image sum of exp(-a|r-A|^2) (and x times it) equals its Fourier series
+    (1/Omega)(pi/a)^{3/2} sum_G exp(-G^2/4a) cos G.(r-A)  (s),
+    (1/Omega)(pi/a)^{3/2} sum_G (G_x/2a) exp(-G^2/4a) sin G.(r-A)  (p_x)."""
+    L = 5.0
+    sysd = S.make_system((1, 1, 1), 0.0, None, ((6, 6, 6),), (), a=L, sites=ONE_ATOM,
+                         s_exps=(alpha,) if lx == 0 else (), p_exps=(alpha,) if lx == 1 else (), image_tol=1e-16)
+    f = O.expand_functions(sysd)
+    phi = O.basis_on_level(sysd, f, [0], 0)[0] / f["norm"][0]
+    xs = O.grid_points_1d(sysd, 0)
+    A = sysd["xyz"][0]
+    mmax = int(math.ceil(math.sqrt(4 * alpha * 40) * L / (2 * math.pi))) + 1
+    m = np.arange(-mmax, mmax + 1)
+    Gx = 2 * math.pi * m / L
+    # separable series: product of 1-D series (cell is cubic)
+    def series_1d(x, A0, deriv):
+        ph = np.outer(x - A0, Gx)
+        w = np.exp(-Gx ** 2 / (4 * alpha)) * math.sqrt(math.pi / alpha) / L
+        if deriv:
+            return (np.sin(ph) * (Gx / (2 * alpha)) * w).sum(axis=1)
+        return (np.cos(ph) * w).sum(axis=1)
+    fx = series_1d(xs[0], A[0], lx == 1)
+    fy = series_1d(xs[1], A[1], False)
+    fz = series_1d(xs[2], A[2], False)
+    ref = np.einsum("k,j,i->kji", fz, fy, fx).ravel()
+    assert np.max(np.abs(phi - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+# --------------------------------------------------------------------------- Coulomb
+
+
+def _gauss_coeff_exact(alpha, A, L, m):
+    G = [2 * math.pi * mi / L for mi in m]
+    G2 = sum(g * g for g in G)
+    return (math.pi / alpha) ** 1.5 / L ** 3 * math.exp(-G2 / (4 * alpha)) * np.exp(-1j * sum(g * a for g, a in zip(G, A))), G2
+
+
+def _analytic_coulomb(alpha, A, beta, B, L, mmax=20):
+    tot = 0.0
+    rng = range(-mmax, mmax + 1)
+    for mx in rng:
+        for my in rng:
+            for mz in rng:
+                if mx == my == mz == 0:
+                    continue
+                fa, G2 = _gauss_coeff_exact(alpha, A, L, (mx, my, mz))
+                fb, _ = _gauss_coeff_exact(beta, B, L, (mx, my, mz))
+                tot += (np.conj(fa) * fb).real / G2
+    return 4 * math.pi * L ** 3 * tot
+
+
+def _periodic_gauss_on_grid(alpha, A, L, n):
+    sysd = S.make_system((1, 1, 1), 0.0, None, ((n, n, n),), (), a=L, sites=np.array([A]) / L,
+                         s_exps=(alpha,), p_exps=(), image_tol=1e-16)
+    f = O.expand_functions(sysd)
+    return O.basis_on_level(sysd, f, [0], 0)[0] / f["norm"][0]
+
+
+@pytest.mark.parametrize("na,nb", [(32, 32), (32, 16), (16, 16)])
+def test_coulomb_fft_matches_analytic_gaussian_series(na, nb):
+    """(f|g) by FFT on one or two grid levels equals the analytic series
+    4 pi Omega sum_{G != 0} Re[conj f~(G) g~(G)] / G^2 for resolved Gaussians."""
+    L = 7.0
+    A = np.array([1.0, 2.0, 2.5])
+    B = np.array([4.0, 3.5, 5.0])
+    alpha, beta = 0.45, 0.3
+    fa = _periodic_gauss_on_grid(alpha, A, L, na)
+    fb = _periodic_gauss_on_grid(beta, B, L, nb)
+    Fa = O.fourier_coeffs(fa[:, None], (na, na, na))
+    Fb = O.fourier_coeffs(fb[:, None], (nb, nb, nb))
+    got = O.coulomb_pair(Fa, (na, na, na), Fb, (nb, nb, nb), np.array([L, L, L]))[0, 0]
+    ref = _analytic_coulomb(alpha, A, beta, B, L)
+    assert abs(got - ref) <= 1e-10 * abs(ref)
+
+
+def test_coulomb_cross_level_equals_fine_level_for_bandlimited():
+    """Cross-level (xi|xi') equals the same integral with the coarse function
+    resampled (trigonometrically) on the fine grid: reading R5."""
+    L = 6.0
+    rng = np.random.default_rng(3)
+    nc, nf = 8, 16
+    f_c = rng.standard_normal(nc ** 3)
+    g_f = rng.standard_normal(nf ** 3)
+    Fc = O.fourier_coeffs(f_c[:, None], (nc, nc, nc))
+    Ff = O.fourier_coeffs(g_f[:, None], (nf, nf, nf))
+    cross = O.coulomb_pair(Ff, (nf,) * 3, Fc, (nc,) * 3, np.array([L] * 3))[0, 0]
+    # interpolate f_c onto the fine grid by zero padding with split Nyquist
+    full = np.zeros((nf, nf, nf), dtype=complex)
+    for mz in range(-nc // 2, nc // 2 + 1):
+        for my in range(-nc // 2, nc // 2 + 1):
+            for mx in range(-nc // 2, nc // 2 + 1):
+                w = 1.0
+                for mm in (mx, my, mz):
+                    if abs(mm) * 2 == nc:
+                        w *= 0.5
+                full[mz % nf, my % nf, mx % nf] += w * Fc[0, mz % nc, my % nc, mx % nc]
+    f_interp = np.fft.ifftn(full * nf ** 3)
+    assert np.max(np.abs(f_interp.imag)) < 1e-12
+    F_int = O.fourier_coeffs(f_interp.real.ravel()[:, None], (nf,) * 3)
+    same = O.coulomb_pair(Ff, (nf,) * 3, F_int, (nf,) * 3, np.array([L] * 3))[0, 0]
+    # the interpolant has no mode at the fine Nyquist, so the same-level rule
+    # on the fine grid is the plain sum: both must agree
+    assert abs(cross - same) <= 1e-12 * max(1.0, abs(same))
+
+
+# --------------------------------------------------------------------------- selection
+
+
+def _pair_matrix(levels, lev):
+    """Explicit Z (ordered pairs x grid points) of one level, reading R1."""
+    ld = levels[lev]
+    rows = [ld["PhiL"][i] * ld["PhiL"][j] for i in range(ld["PhiL"].shape[0]) for j in range(ld["PhiL"].shape[0])]
+    rows += [ld["PhiL"][i] * ld["PhiN"][j] for i in range(ld["PhiL"].shape[0]) for j in range(ld["PhiN"].shape[0])]
+    rows += [ld["PhiN"][j] * ld["PhiL"][i] for i in range(ld["PhiL"].shape[0]) for j in range(ld["PhiN"].shape[0])]
+    return np.array(rows)
+
+
+def _levels(sysd):
+    f = O.expand_functions(sysd)
+    return f, O._level_data(sysd, f)
+
+
+def test_m_matches_explicit_pair_gram():
+    """M_l = Z_l^T Z_l for the ordered pair set of each level (Eq. 2, R1)."""
+    sysd = tiny(levels=3, sites=TWO_ATOMS, n=(8, 4, 2), a=4.0)
+    _, levels = _levels(sysd)
+    for lev in range(3):
+        Z = _pair_matrix(levels, lev)
+        ng = levels[lev]["PhiL"].shape[1]
+        M = O.m_columns(levels[lev], np.arange(ng))
+        assert np.max(np.abs(M - Z.T @ Z)) <= 1e-12 * np.max(np.abs(M))
+
+
+def test_selection_matches_pivoted_qr_and_dpstrf():
+    """Single level: pivoted Cholesky on M picks the same points as pivoted QR
+    on the pair matrix (Section II.A) and as LAPACK dpstrf on M."""
+    sysd = S.make_system((1, 1, 1), 0.04, np.random.default_rng(11), ((10, 10, 10),), (), a=5.0,
+                         sites=TWO_ATOMS, s_exps=(0.3, 1.2), p_exps=(0.8,))
+    _, levels = _levels(sysd)
+    k = 30
+    sel = O.select_points(levels, k, tie_rel=0.0, tie_abs=0.0)
+    piv = sel["pivots"] & ((1 << O.PIVOT_SHIFT) - 1)
+    Z = _pair_matrix(levels, 0)
+    _, _, qr_piv = scipy.linalg.qr(Z, pivoting=True, mode="economic")
+    np.testing.assert_array_equal(piv, qr_piv[:k])
+    M = levels[0]["w"] * O.m_columns(levels[0], np.arange(Z.shape[1]))
+    _, lp, rank, info = scipy.linalg.lapack.dpstrf(M, lower=1, tol=-1.0)
+    np.testing.assert_array_equal(piv, (lp - 1)[:k])
+
+
+def test_selection_tie_rule_smallest_index():
+    """Undisplaced symmetric cell: exact ties resolve to the smallest (level, g)."""
+    sysd = S.make_system((1, 1, 1), 0.0, None, ((8, 8, 8),), (), a=6.74)
+    _, levels = _levels(sysd)
+    d = O.initial_diagonal(levels[0])
+    dmax = d.max()
+    ties = np.flatnonzero(d >= dmax - 1e-9 * dmax)
+    assert ties.size > 1  # the symmetric cell really has ties
+    sel = O.select_points(levels, 1)
+    assert int(sel["pivots"][0]) == int(ties[0])
+
+
+def test_residual_trace_equals_fit_error():
+    """Sum_g d_k(g) = sum_l w_l ||Z_l - C_l Xi_l^T||_F^2 (Schur complement)."""
+    sysd = tiny(levels=3, sites=TWO_ATOMS, n=(8, 4, 2), a=4.0)
+    _, levels = _levels(sysd)
+    sel = O.select_points(levels, 40)
+    Xi = O.fit(levels, sel["pivots"], reg_rel=0.0)
+    per = O.split_pivots(sel["pivots"], 3)
+    err = 0.0
+    for lev in range(3):
+        Z = _pair_matrix(levels, lev)
+        if per[lev].size:
+            R = Z - Z[:, per[lev]] @ Xi[lev].T
+        else:
+            R = Z
+        err += levels[lev]["w"] * np.sum(R * R)
+    tr = sum(float(np.sum(r)) for r in sel["residual"])
+    assert abs(err - tr) <= 1e-9 * abs(err) + 1e-14
+
+
+def test_fit_matches_lstsq_and_interpolates():
+    """Xi = argmin ||Z - Z[:,P] Xi^T|| (Eq. 3) and Xi[P, :] = I."""
+    sysd = tiny(levels=3, sites=TWO_ATOMS, n=(8, 4, 2), a=4.0)
+    _, levels = _levels(sysd)
+    sel = O.select_points(levels, 30)
+    Xi = O.fit(levels, sel["pivots"], reg_rel=0.0)
+    for lev, P in enumerate(O.split_pivots(sel["pivots"], 3)):
+        if P.size == 0:
+            continue
+        Z = _pair_matrix(levels, lev)
+        ref = np.linalg.lstsq(Z[:, P], Z, rcond=None)[0].T
+        assert np.max(np.abs(Xi[lev] - ref)) <= 1e-8 * max(1.0, np.max(np.abs(ref)))
+        assert np.max(np.abs(Xi[lev][P, :] - np.eye(P.size))) <= 1e-10
+
+
+def test_selection_nested_and_residual_monotone():
+    sysd = tiny(levels=3, sites=TWO_ATOMS, n=(8, 4, 2), a=4.0)
+    _, levels = _levels(sysd)
+    prev = None
+    traces = []
+    for k in (5, 10, 20, 40):
+        sel = O.select_points(levels, k)
+        if prev is not None:
+            np.testing.assert_array_equal(sel["pivots"][: prev.size], prev)
+        prev = sel["pivots"]
+        traces.append(sum(float(np.sum(r)) for r in sel["residual"]))
+    assert all(b <= a * (1 + 1e-12) for a, b in zip(traces, traces[1:]))
+
+
+# --------------------------------------------------------------------------- exchange
+
+
+@pytest.mark.parametrize("levels", [1, 3])
+def test_nofit_equals_brute_4index(levels):
+    sysd = tiny(levels=levels, n=(12, 6, 4))
+    C = orbitals(sysd)
+    Kn, En = oracle.nofit_exchange(sysd, C)
+    Kb, Eb, eri = oracle.brute_exchange(sysd, C)
+    assert np.max(np.abs(Kn - Kb)) <= 1e-13 * np.max(np.abs(Kb))
+    # ERI symmetries of the exact tensor
+    assert np.max(np.abs(eri - eri.transpose(1, 0, 2, 3))) <= 1e-13 * np.max(np.abs(eri))
+    assert np.max(np.abs(eri - eri.transpose(2, 3, 0, 1))) <= 1e-13 * np.max(np.abs(eri))
+
+
+@pytest.mark.parametrize("levels,rank", [(1, 91), (3, 91)])
+def test_isdf_exact_at_full_pair_rank(levels, rank):
+    """With N_ip at the pair-space rank ISDF reproduces the no-fit exchange."""
+    sysd = tiny(levels=levels)
+    C = orbitals(sysd)
+    Kn, En = oracle.nofit_exchange(sysd, C)
+    r = oracle.run(sysd, C, 200, tol=1e-14, reg_rel=0.0)
+    assert len(r["pivots"]) == rank
+    assert np.max(np.abs(r["K"] - Kn)) <= 1e-9
+    assert abs(r["Ex"] - En) <= 1e-9
+
+
+def test_isdf_eri_four_term_form():
+    """exchange() contracts the Eq. 8 tensor: build (mu lam|sig nu) explicitly
+    from c(P) V c(Q), check its pair symmetries and K = D-contraction."""
+    sysd = tiny(levels=3)
+    C = orbitals(sysd)
+    r = oracle.run(sysd, C, 40)
+    XL, XN = r["XL"], r["XN"]
+    XG = XL + XN
+    c = np.einsum("mp,lp->pml", XL, XG) + np.einsum("mp,lp->pml", XN, XL)
+    eri = np.einsum("pml,pq,qsn->mlsn", c, r["V"], c)
+    assert np.max(np.abs(eri - eri.transpose(1, 0, 2, 3))) <= 1e-12 * np.max(np.abs(eri))
+    assert np.max(np.abs(eri - eri.transpose(2, 3, 0, 1))) <= 1e-12 * np.max(np.abs(eri))
+    D = C @ C.T
+    K = np.einsum("ls,mlsn->mn", D, eri)
+    assert np.max(np.abs(K - r["K"])) <= 1e-12 * np.max(np.abs(K))
+
+
+def test_invariants_symmetry_psd_sign():
+    sysd, C = S.small_multigrid(per_cell=(12, 6, 4), seed=5)
+    r = oracle.run(sysd, C, 120)
+    K, V = r["K"], r["V"]
+    assert np.max(np.abs(K - K.T)) <= 1e-13 * np.max(np.abs(K))
+    assert np.max(np.abs(V - V.T)) <= 1e-13 * np.max(np.abs(V))
+    ev = np.linalg.eigvalsh(V)
+    assert ev.min() >= -1e-10 * ev.max()
+    assert r["Ex"] < 0.0
+
+
+def test_error_falls_with_nip():
+    """|K - K_nofit| falls along N_ip = N, 2N, 4N, 8N (with slack)."""
+    sysd = tiny(levels=3, n=(12, 6, 4))
+    C = orbitals(sysd)
+    Kn, _ = oracle.nofit_exchange(sysd, C)
+    N = 13
+    errs = [np.max(np.abs(oracle.run(sysd, C, k)["K"] - Kn)) for k in (N, 2 * N, 4 * N, 7 * N)]
+    assert errs[-1] < 1e-6
+    for a, b in zip(errs, errs[1:]):
+        assert b <= 1.5 * a
+
+
+# --------------------------------------------------------------------------- planted mistakes
+
+
+def test_planted_mistake_in_m_breaks_exact_reproduction(monkeypatch):
+    """Dropping the factor 2 of the cross term in M (reading R1) changes the
+    pivots and breaks exact reproduction: the pins above would catch it."""
+    sysd = tiny(levels=3)
+    C = orbitals(sysd)
+    Kn, _ = oracle.nofit_exchange(sysd, C)
+
+    def wrong(ld, cols):
+        AL = ld["PhiL"].T @ ld["PhiL"][:, cols]
+        AN = ld["PhiN"].T @ ld["PhiN"][:, cols]
+        return AL * (AL + AN)
+
+    monkeypatch.setattr(O, "m_columns", wrong)
+    try:
+        r = oracle.run(sysd, C, 200, tol=1e-14, reg_rel=0.0)
+    except np.linalg.LinAlgError:
+        return  # the wrong M is not even a Gram matrix: its Cholesky breaks down
+    assert np.max(np.abs(r["K"] - Kn)) > 1e-6
+
+
+def test_planted_mistake_in_eq8_breaks_brute_agreement(monkeypatch):
+    """Using X^G on both factors (dropping the L/N bookkeeping of Eq. 8)
+    double counts diffuse pairs and no longer matches the exact exchange."""
+    sysd = tiny(levels=3)
+    C = orbitals(sysd)
+    Kn, _ = oracle.nofit_exchange(sysd, C)
+    orig = O.exchange
+
+    def wrong(XL, XN, V, C_):
+        return orig(XL + XN, XN, V, C_)
+
+    monkeypatch.setattr(O, "exchange", wrong)
+    r = oracle.run(sysd, C, 200, tol=1e-14, reg_rel=0.0)
+    assert np.max(np.abs(r["K"] - Kn)) > 1e-6
