@@ -1,0 +1,221 @@
+/*
+ * isdf.h -- C ABI of the GB300 (sm_103a) multigrid ISDF / THC exchange library.
+ *
+ * Method: Smyser, White & Sharma, "Use of multigrids to reduce the cost of
+ * performing interpolative separable density fitting" (arXiv:2404.09373).
+ *
+ * The library factorises the electron-repulsion integrals of a periodic,
+ * uncontracted Cartesian Gaussian basis into tensor-hypercontraction form by
+ * interpolative separable density fitting (ISDF) on a hierarchy of real-space
+ * grids, and builds the exact-exchange matrix from the factors:
+ *
+ *   isdf_plan           set-up: basis, grid levels, device buffers (no math)
+ *   isdf_select_points  interpolation points by pivoted Cholesky on M (Eq. 2)
+ *   isdf_fit            interpolation vectors xi(R) by least squares (Eq. 3)
+ *   isdf_coulomb        two-centre Coulomb matrix (xi|xi') by FFT (Eq. 1)
+ *   isdf_exchange       exchange matrix K from the four-term THC form (Eq. 8)
+ *
+ * Conventions shared by every call
+ *   - Units: bohr and hartree.  All floating point arguments are FP64.
+ *   - Pointers: every array argument may be host memory or device memory of
+ *     the plan's device; the library tells them apart with
+ *     cudaPointerGetAttributes.  The caller owns all inputs and outputs; the
+ *     plan owns every device buffer it allocates and frees them in
+ *     isdf_destroy.
+ *   - Stream: all device work is enqueued on the stream given to isdf_plan.
+ *     Calls return after the results they write to HOST memory are complete;
+ *     results written to DEVICE memory are valid once that stream reaches
+ *     the point where the call returned.
+ *   - Errors: every call returns an isdf_status; nothing throws or exits
+ *     across the ABI.  isdf_last_error(plan) gives a message.  After a failed
+ *     call the plan can always be destroyed.  Calls must come in the order
+ *     plan -> select_points -> fit -> coulomb -> exchange (exchange may be
+ *     repeated, e.g. once per SCF iteration); a call out of order returns
+ *     ISDF_ERR_STATE and changes nothing.
+ *   - Basis function order: shells in the order given; an s shell gives one
+ *     function, a p shell three (x, y, z).  Function mu has level
+ *     l(mu) = #{e in level_min_exp : exponent < e} (level 0 = finest grid).
+ *   - Grid point g of a level with (nx, ny, nz) points is r_g = (i Lx/nx,
+ *     j Ly/ny, k Lz/nz) with g = i + nx (j + ny k).
+ *   - Pivot code: (level << 40) | g  (int64).
+ */
+#ifndef ISDF_H
+#define ISDF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ISDF_MAX_LEVELS 4
+
+typedef struct isdf_plan_s* isdf_plan_t;
+
+typedef enum {
+  ISDF_OK = 0,
+  ISDF_ERR_ARG = 1,     /* invalid argument (nothing was changed)          */
+  ISDF_ERR_OOM = 2,     /* device allocation failed                        */
+  ISDF_ERR_NOT_PD = 3,  /* Cholesky of C C^T broke down (non-positive pivot)*/
+  ISDF_ERR_CUDA = 4,    /* a CUDA runtime call or kernel launch failed     */
+  ISDF_ERR_CUFFT = 5,   /* a cuFFT call failed                             */
+  ISDF_ERR_TIMEOUT = 6, /* the selection loop exceeded options.timeout_ms  */
+  ISDF_ERR_STATE = 7    /* call out of order                               */
+} isdf_status;
+
+/* The periodic system.  Read once by isdf_plan (copied; not referenced
+ * afterwards).  All pointers here are HOST pointers.
+ *   lattice        row-major 3x3 lattice vectors a1, a2, a3 (bohr); must be
+ *                  diagonal (orthorhombic cell), else ISDF_ERR_ARG
+ *   xyz            natom x 3 Cartesian atom positions (any image)
+ *   shell_*        nshell uncontracted shells: atom index, angular momentum
+ *                  l in {0, 1}, Gaussian exponent alpha > 0
+ *   grid           nlevel x 3 points per axis (nx, ny, nz); level 0 finest;
+ *                  every count even, and per axis strictly decreasing from
+ *                  one level to the next (so a coarser level's mode set is
+ *                  inside every finer one)
+ *   level_min_exp  nlevel-1 strictly decreasing exponent edges
+ *   image_tol      image-sum truncation: on each axis a lattice translation
+ *                  t is kept when the shifted centre A + t L lies within
+ *                  r_cut = sqrt(ln(1/image_tol)/alpha) of [0, L]            */
+typedef struct {
+  double lattice[9];
+  int natom;
+  const double* xyz;
+  int nshell;
+  const int* shell_atom;
+  const int* shell_l;
+  const double* shell_exp;
+  int nlevel;
+  const int* grid;
+  const double* level_min_exp;
+  double image_tol;
+} isdf_system;
+
+/* Options.  Fill with isdf_options_default, then override.
+ *   precision   0: every contraction in FP64 on the SIMT pipes ("plain");
+ *               1: the dense contractions of the fit, the Coulomb matrix and
+ *                  the exchange build on the tensor cores with FP64-accurate
+ *                  sliced BF16 products (FP64 pivot decisions, Cholesky and
+ *                  energy reduction are unchanged)
+ *   tie_rel, tie_abs  pivot tie rule: among points whose residual is at
+ *               least d_max - max(tie_rel d_max, tie_abs d_0) the smallest
+ *               (level, g) wins (defaults 1e-9, 1e-13)
+ *   reg_rel     fit regularisation lambda = reg_rel tr(CC^T)/k per level
+ *               (default 0)
+ *   col_batch   interpolation vectors per cuFFT batch (0 = automatic)
+ *   timeout_ms  wall-clock budget of the selection loop, measured on the
+ *               device (0 = none); exceeding it ends the loop early with
+ *               ISDF_ERR_TIMEOUT
+ *   prefilter   0: every grid point is a candidate.  1: exact prefilter --
+ *               points whose initial residual is below a threshold tau are
+ *               dropped; the call verifies that the last pivot value stays
+ *               above tau plus the tie margin (then the result equals the
+ *               full greedy one, residuals never grow) and otherwise repeats
+ *               the selection with a lower tau
+ *   profile     1: time every kernel family with CUDA events on the plan's
+ *               stream and count its algorithmic work (isdf_profile_json)  */
+typedef struct {
+  int precision;
+  double tie_rel;
+  double tie_abs;
+  double reg_rel;
+  int col_batch;
+  int timeout_ms;
+  int prefilter;
+  int profile;
+} isdf_options;
+
+void isdf_options_default(isdf_options* opt);
+
+/* Create a plan for one system (Section III, Fig. Grids: basis split by
+ * exponent, one grid per level).  Validates the system, expands the shells,
+ * assigns levels, allocates the basis tables and evaluates the basis on
+ * every level.  stream: a cudaStream_t (NULL = legacy default stream).
+ * On success *out receives the plan; on failure *out is NULL. */
+isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* stream, isdf_plan_t* out);
+
+/* Select up to nip interpolation points (Section II.A, Eq. 2): greedy
+ * pivoted Cholesky on the block-diagonal matrix (+)_l w_l M_l, with
+ * M_l = A_L o A_L + 2 A_L o A_N, A_X(g,g') = sum_{mu in X} phi_mu(g)phi_mu(g'),
+ * L_l = functions of level l, N_l = functions of coarser levels, and
+ * w_l = Omega / N_g,l.  Stops after nip pivots or once the largest residual
+ * falls below tol * d_0 (tol = 0: never).
+ *   cand, ncand   optional candidate pivot codes (NULL / 0 = all points)
+ *   piv_out       nip int64 pivot codes in selection order (host or device)
+ *   dval_out      nip FP64 pivot values d_k (nullable)
+ *   nip_out       number of pivots actually selected (host int)
+ * The factor columns are freed when the call returns.  Returns
+ * ISDF_ERR_TIMEOUT when the loop ran out of options.timeout_ms (the pivots
+ * found so far are valid and are returned). */
+isdf_status isdf_select_points(isdf_plan_t plan, int nip, double tol, const int64_t* cand, int64_t ncand,
+                               int64_t* piv_out, double* dval_out, int* nip_out);
+
+/* Fit the interpolation vectors (Section II.A, Eq. 3) for the given pivots
+ * (any pivot set, e.g. the one returned by isdf_select_points):
+ * Xi_l = (ZC^T)_l ((CC^T)_l + lambda I)^-1 with (ZC^T)_l = M_l[:, P_l],
+ * (CC^T)_l = M_l[P_l, P_l], via an FP64 Cholesky.  Also forms X^L and X^N,
+ * the basis values at the pivots.  piv: nip pivot codes (host or device);
+ * duplicates or out-of-range codes give ISDF_ERR_ARG.  Internally pivots are
+ * ordered level by level (selection order kept within a level); that order
+ * is used by every matrix the library returns (see isdf_get). */
+isdf_status isdf_fit(isdf_plan_t plan, const int64_t* piv, int nip);
+
+/* Two-centre Coulomb matrix V_PQ = (xi_P|xi_Q) (Section II, Eq. 1) by
+ * batched 3-D FFTs of the interpolation vectors: every grid function stands
+ * for its trigonometric interpolant (a mode at +-n/2 on an axis is split
+ * evenly between the two), the G = 0 term is dropped, and pairs on two
+ * levels are summed over the coarser level's mode set.  V_out: nullable,
+ * nip x nip row-major FP64 in level-ordered pivot order (host or device). */
+isdf_status isdf_coulomb(isdf_plan_t plan, double* V_out);
+
+/* Exchange matrix (Section III.A, Eq. 8) for the density D = C C^T:
+ *   K_{mu nu} = sum_{lam sig} D_{lam sig} (mu lam|sig nu),
+ *   (mu lam|sig nu) = sum_PQ c_{mu lam}(P) V_PQ c_{sig nu}(Q),
+ *   c_{mu lam}(P) = X^L_{mu P} X^G_{lam P} + X^N_{mu P} X^L_{lam P},
+ * and E_x = -Tr(D K).
+ *   C      N x n row-major FP64 occupied-orbital coefficients (host/device)
+ *   K_out  nullable N x N row-major FP64 (host or device)
+ *   Ex_out nullable host double                                            */
+isdf_status isdf_exchange(isdf_plan_t plan, const double* C, int n, double* K_out, double* Ex_out);
+
+/* Copy plan data out (host or device destination) for tests and tools.
+ * isdf_get_size returns the number of elements (0 if not available yet). */
+enum {
+  ISDF_GET_NBASIS = 0,     /* int32[1]                                     */
+  ISDF_GET_NIP_LEVEL = 1,  /* int32[nlevel] pivots per level               */
+  ISDF_GET_PIVOTS = 2,     /* int64[nip] pivot codes, level-ordered        */
+  ISDF_GET_XL = 3,         /* double[N x nip] X^L (level-ordered columns)  */
+  ISDF_GET_XN = 4,         /* double[N x nip] X^N                          */
+  ISDF_GET_V = 5,          /* double[nip x nip]                            */
+  ISDF_GET_XI_LEVEL0 = 6,  /* double[k_l x N_g,l] Xi^T of level 0; add the
+                              level index for the others                   */
+  ISDF_GET_PHI_LEVEL0 = 10 /* double[|G_l| x N_g,l] basis values of level
+                              0 (rows: functions of the level in index order,
+                              then coarser ones); add the level index      */
+};
+int64_t isdf_get_size(isdf_plan_t plan, int what);
+isdf_status isdf_get(isdf_plan_t plan, int what, void* dst);
+
+/* Kernel timing report of a plan created with options.profile = 1: a JSON
+ * object {"kernels": {name: {"launches": L, "ms": T, "work": W, "unit": U}}}
+ * accumulated over all calls so far (U is "flop" or "byte": the algorithmic
+ * work the method needs, not what the kernel executes).  Synchronises the
+ * plan's stream.  The string stays valid until the next call on the plan. */
+const char* isdf_profile_json(isdf_plan_t plan);
+
+/* Number of kernels this library has launched in this process so far (its
+ * own kernels; cuFFT's are not counted).  Host-side counter. */
+int64_t isdf_kernel_launches(void);
+
+/* Message of the last failed call on this plan (or of the last failed
+ * isdf_plan when plan is NULL).  Valid until the next call. */
+const char* isdf_last_error(isdf_plan_t plan);
+
+/* Free every device buffer and the plan.  NULL is ignored. */
+void isdf_destroy(isdf_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ISDF_H */

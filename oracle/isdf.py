@@ -214,7 +214,7 @@ def select_points(levels, nip, tol=0.0, tie_rel=1e-9, tie_abs=1e-13, cand=None):
     """Greedy pivoted Cholesky over (+)_l w_l M_l (Eq. 2; readings R2, R3).
 
     At step k: d_max = max residual; p = smallest (level, g) with
-    d(p) >= d_max - max(tie_rel d_max, tie_abs d_0); new factor column on
+    d(p) >= d_max - max(tie_rel d_max, tie_abs d_0) and d(p) > 0; new factor column on
     p's level  L[:, k] = (w M[:, p] - L[:, :k] L[p, :k]^T) / sqrt(d_p) with
     L[p, k] = sqrt(d_p); d -= L[:, k]^2; d(p) = 0.  Stops after ``nip``
     pivots or when d_max < tol * d_0.  ``cand`` optionally restricts the
@@ -244,7 +244,7 @@ def select_points(levels, nip, tol=0.0, tie_rel=1e-9, tie_abs=1e-13, cand=None):
         thr = dmax - max(tie_rel * dmax, tie_abs * d0)
         lev, p = None, None
         for l in range(nlev):
-            hit = np.flatnonzero(d[l] >= thr)
+            hit = np.flatnonzero((d[l] >= thr) & (d[l] > 0.0))
             if hit.size:
                 lev, p = l, int(hit[0])
                 break

@@ -1,0 +1,544 @@
+// C ABI of the multigrid ISDF library: argument checks, plan life cycle,
+// host/device marshalling and the call-order state machine.  Every step of
+// the computation runs in this library's kernels (basis.cu, select.cu,
+// fit.cu, coulomb.cu, exchange.cu, dgemm.cu).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <set>
+
+#include "internal.cuh"
+
+struct isdf_plan_s {
+  isdf::Plan p;
+};
+
+namespace isdf {
+
+static thread_local std::string g_plan_error;  // failures before a plan exists
+std::atomic<long long> g_launches{0};
+
+Prof::Prof(Plan* p_, const char* name, double work, const char* unit, int64_t launches) : p(p_) {
+  count_launches(launches);
+  if (!p || !p->opt.profile) return;
+  e.name = name;
+  e.work = work;
+  e.unit = unit;
+  e.launches = launches;
+  cudaEventCreate(&e.a);
+  cudaEventCreate(&e.b);
+  cudaEventRecord(e.a, p->stream);
+}
+
+Prof::~Prof() {
+  if (!p || !p->opt.profile || !e.a) return;
+  cudaEventRecord(e.b, p->stream);
+  p->pend.push_back(e);
+}
+
+void prof_flush(Plan* p) {
+  for (ProfEvent& e : p->pend) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+      KStat& k = p->stats[e.name];
+      k.launches += e.launches;
+      k.ms += ms;
+      k.work += e.work;
+      k.unit = e.unit;
+    }
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  p->pend.clear();
+  cudaGetLastError();
+}
+
+isdf_status fail(Plan* p, isdf_status s, const std::string& msg) {
+  if (p) p->err = msg;
+  return s;
+}
+
+isdf_status cuda_check(Plan* p, cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return ISDF_OK;
+  return fail(p, ISDF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+isdf_status dalloc(Plan* p, void** ptr, size_t bytes, const char* what) {
+  *ptr = nullptr;
+  if (p && p->fault == "oom") return fail(p, ISDF_ERR_OOM, std::string("device allocation failed (injected): ") + what);
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    *ptr = nullptr;
+    return fail(p, e == cudaErrorMemoryAllocation ? ISDF_ERR_OOM : ISDF_ERR_CUDA,
+                std::string("cudaMalloc of ") + std::to_string(bytes) + " bytes for " + what + ": " +
+                    cudaGetErrorString(e));
+  }
+  return ISDF_OK;
+}
+
+void dfree(void* ptr) {
+  if (ptr) cudaFree(ptr);
+}
+
+bool is_device_ptr(const void* ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+namespace {
+
+void free_plan(Plan* p) {
+  for (int l = 0; l < ISDF_MAX_LEVELS; ++l) {
+    Level& lv = p->lev[l];
+    for (int a = 0; a < 3; ++a) dfree(lv.tab[a]);
+    dfree(lv.phi);
+    dfree(lv.fac);
+    dfree(lv.d_pg);
+    dfree(lv.xiT);
+    dfree(lv.spec);
+    lv = Level();
+  }
+  dfree(p->d_diag);
+  dfree(p->d_active);
+  dfree(p->d_selstate);
+  dfree(p->d_piv);
+  dfree(p->d_dval);
+  dfree(p->XL);
+  dfree(p->XN);
+  dfree(p->V);
+  dfree(p->d_err);
+  p->d_diag = nullptr;
+  p->d_active = nullptr;
+  p->d_selstate = nullptr;
+  p->d_piv = nullptr;
+  p->d_dval = nullptr;
+  p->XL = p->XN = p->V = nullptr;
+  p->d_err = nullptr;
+}
+
+// Copy n elements from a host or device source into a host vector.
+template <class T>
+isdf_status to_host(Plan* p, const T* src, size_t n, std::vector<T>& out) {
+  out.resize(n);
+  if (n == 0) return ISDF_OK;
+  if (is_device_ptr(src)) {
+    isdf_status st = cuda_check(p, cudaMemcpyAsync(out.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost, p->stream),
+                                "device to host copy");
+    if (st) return st;
+    return cuda_check(p, cudaStreamSynchronize(p->stream), "device to host copy");
+  }
+  std::memcpy(out.data(), src, n * sizeof(T));
+  return ISDF_OK;
+}
+
+// Copy n elements from device memory to a host or device destination.
+template <class T>
+isdf_status from_device(Plan* p, T* dst, const T* dsrc, size_t n, bool sync) {
+  if (n == 0) return ISDF_OK;
+  const bool dev = is_device_ptr(dst);
+  isdf_status st = cuda_check(
+      p, cudaMemcpyAsync(dst, dsrc, n * sizeof(T), dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, p->stream),
+      "copy out");
+  if (st) return st;
+  if (!dev || sync) return cuda_check(p, cudaStreamSynchronize(p->stream), "copy out");
+  return ISDF_OK;
+}
+
+isdf_status validate_system(const isdf_system* sys, std::string& why) {
+  auto bad = [&](const std::string& m) {
+    why = m;
+    return ISDF_ERR_ARG;
+  };
+  if (!sys) return bad("system is NULL");
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      const double v = sys->lattice[3 * i + j];
+      if (i != j && v != 0.0) return bad("lattice must be diagonal (orthorhombic cell)");
+      if (i == j && !(v > 0.0 && std::isfinite(v))) return bad("lattice edge lengths must be positive");
+    }
+  if (sys->natom < 1 || !sys->xyz) return bad("need natom >= 1 and xyz");
+  for (int i = 0; i < 3 * sys->natom; ++i)
+    if (!std::isfinite(sys->xyz[i])) return bad("atom coordinates must be finite");
+  if (sys->nshell < 1 || !sys->shell_atom || !sys->shell_l || !sys->shell_exp) return bad("need nshell >= 1 and shells");
+  for (int i = 0; i < sys->nshell; ++i) {
+    if (sys->shell_atom[i] < 0 || sys->shell_atom[i] >= sys->natom) return bad("shell_atom out of range");
+    if (sys->shell_l[i] != 0 && sys->shell_l[i] != 1) return bad("only s and p shells (l = 0, 1) are supported");
+    if (!(sys->shell_exp[i] > 0.0 && std::isfinite(sys->shell_exp[i]))) return bad("shell exponents must be > 0");
+  }
+  if (sys->nlevel < 1 || sys->nlevel > ISDF_MAX_LEVELS || !sys->grid) return bad("need 1 <= nlevel <= 4 and grid");
+  for (int l = 0; l < sys->nlevel; ++l)
+    for (int a = 0; a < 3; ++a) {
+      const int n = sys->grid[3 * l + a];
+      if (n < 2 || (n % 2) != 0) return bad("grid counts must be even and >= 2");
+      if (n > (1 << 20)) return bad("grid count too large");
+      if (l > 0 && !(n < sys->grid[3 * (l - 1) + a])) return bad("grid counts must decrease from level to level");
+    }
+  if (sys->nlevel > 1) {
+    if (!sys->level_min_exp) return bad("level_min_exp is NULL");
+    for (int l = 0; l + 1 < sys->nlevel; ++l) {
+      const double e = sys->level_min_exp[l];
+      if (!(e > 0.0 && std::isfinite(e))) return bad("level edges must be positive");
+      if (l > 0 && !(e < sys->level_min_exp[l - 1])) return bad("level edges must decrease");
+    }
+  }
+  if (!(sys->image_tol > 0.0 && sys->image_tol < 1.0)) return bad("image_tol must be in (0, 1)");
+  return ISDF_OK;
+}
+
+isdf_status validate_options(const isdf_options* o, std::string& why) {
+  auto bad = [&](const std::string& m) {
+    why = m;
+    return ISDF_ERR_ARG;
+  };
+  if (o->precision != 0) return bad("precision must be 0 (plain FP64)");
+  if (!(o->tie_rel >= 0.0) || !(o->tie_abs >= 0.0) || !(o->reg_rel >= 0.0)) return bad("tolerances must be >= 0");
+  if (o->col_batch < 0 || o->timeout_ms < 0) return bad("col_batch and timeout_ms must be >= 0");
+  if (o->prefilter != 0 && o->prefilter != 1) return bad("prefilter must be 0 or 1");
+  if (o->profile != 0 && o->profile != 1) return bad("profile must be 0 or 1");
+  return ISDF_OK;
+}
+
+}  // namespace
+}  // namespace isdf
+
+using namespace isdf;
+
+extern "C" {
+
+void isdf_options_default(isdf_options* o) {
+  if (!o) return;
+  o->precision = 0;
+  o->tie_rel = 1e-9;
+  o->tie_abs = 1e-13;
+  o->reg_rel = 0.0;
+  o->col_batch = 0;
+  o->timeout_ms = 0;
+  o->prefilter = 0;
+  o->profile = 0;
+}
+
+isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* stream, isdf_plan_t* out) {
+  if (!out) {
+    g_plan_error = "out is NULL";
+    return ISDF_ERR_ARG;
+  }
+  *out = nullptr;
+  std::string why;
+  if (validate_system(sys, why)) {
+    g_plan_error = why;
+    return ISDF_ERR_ARG;
+  }
+  isdf_options o;
+  isdf_options_default(&o);
+  if (opt) o = *opt;
+  if (validate_options(&o, why)) {
+    g_plan_error = why;
+    return ISDF_ERR_ARG;
+  }
+  isdf_plan_s* h = new (std::nothrow) isdf_plan_s();
+  if (!h) {
+    g_plan_error = "host allocation failed";
+    return ISDF_ERR_OOM;
+  }
+  Plan* p = &h->p;
+  p->stream = static_cast<cudaStream_t>(stream);
+  p->opt = o;
+  if (const char* f = std::getenv("ISDF_FAULT")) p->fault = f;
+  for (int a = 0; a < 3; ++a) p->edge[a] = sys->lattice[4 * a];
+  p->omega = p->edge[0] * p->edge[1] * p->edge[2];
+  p->image_tol = sys->image_tol;
+  p->natom = sys->natom;
+  p->xyz.assign(sys->xyz, sys->xyz + 3 * sys->natom);
+  // functions and their levels (Section III: split by exponent)
+  for (int i = 0; i < sys->nshell; ++i) {
+    const double e = sys->shell_exp[i];
+    int lev = 0;
+    for (int l = 0; l + 1 < sys->nlevel; ++l)
+      if (e < sys->level_min_exp[l]) ++lev;
+    const int ncomp = sys->shell_l[i] == 0 ? 1 : 3;
+    for (int c = 0; c < ncomp; ++c) {
+      p->f_atom.push_back(sys->shell_atom[i]);
+      p->f_alpha.push_back(e);
+      double nrm = std::pow(2.0 * e / M_PI, 0.75);
+      if (sys->shell_l[i] == 1) nrm *= 2.0 * std::sqrt(e);
+      p->f_norm.push_back(nrm);
+      for (int a = 0; a < 3; ++a) p->f_l[a].push_back(sys->shell_l[i] == 1 && a == c ? 1 : 0);
+      p->f_level.push_back(lev);
+    }
+  }
+  p->nfun = int(p->f_atom.size());
+  p->nlev = sys->nlevel;
+  p->off[0] = 0;
+  for (int l = 0; l < p->nlev; ++l) {
+    Level& lv = p->lev[l];
+    for (int a = 0; a < 3; ++a) lv.n[a] = sys->grid[3 * l + a];
+    lv.ng = int64_t(lv.n[0]) * lv.n[1] * lv.n[2];
+    lv.w = p->omega / double(lv.ng);
+    for (int mu = 0; mu < p->nfun; ++mu) {
+      if (p->f_level[mu] == l) lv.L.push_back(mu);
+      if (p->f_level[mu] > l) lv.N.push_back(mu);
+    }
+    lv.nL = int(lv.L.size());
+    lv.nN = int(lv.N.size());
+    lv.nG = lv.nL + lv.nN;
+    p->off[l + 1] = p->off[l] + lv.ng;
+  }
+  p->ntot = p->off[p->nlev];
+  // device checks
+  int dev = 0;
+  cudaDeviceProp prop;
+  isdf_status st = cuda_check(p, cudaGetDevice(&dev), "cudaGetDevice");
+  if (!st) st = cuda_check(p, cudaGetDeviceProperties(&prop, dev), "cudaGetDeviceProperties");
+  if (!st && !(prop.major == 10 && prop.minor == 3))
+    st = fail(p, ISDF_ERR_CUDA,
+              "this library is built for sm_103a; device compute capability is " + std::to_string(prop.major) + "." +
+                  std::to_string(prop.minor));
+  if (!st) st = dalloc_t(p, &p->d_err, 1, "error word");
+  if (!st) st = basis_build(p);
+  if (!st) st = cuda_check(p, cudaStreamSynchronize(p->stream), "plan");
+  if (st) {
+    g_plan_error = p->err;
+    free_plan(p);
+    delete h;
+    return st;
+  }
+  *out = h;
+  return ISDF_OK;
+}
+
+isdf_status isdf_select_points(isdf_plan_t h, int nip, double tol, const int64_t* cand, int64_t ncand,
+                               int64_t* piv_out, double* dval_out, int* nip_out) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (nip < 1 || !piv_out || !nip_out || !(tol >= 0.0) || (cand && ncand < 1) || (!cand && ncand != 0))
+    return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_select_points");
+  if (nip > p->ntot) return fail(p, ISDF_ERR_ARG, "nip exceeds the number of grid points");
+  std::vector<int64_t> cv;
+  if (cand) {
+    isdf_status st = to_host(p, cand, size_t(ncand), cv);
+    if (st) return st;
+    for (int64_t c : cv) {
+      const int64_t l = c >> kPivShift, g = c & kPivMask;
+      if (c < 0 || l >= p->nlev || g >= p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "candidate code out of range");
+    }
+  }
+  int found = 0;
+  isdf_status st = select_run(p, nip, tol, cand ? &cv : nullptr, &found);
+  if (st && st != ISDF_ERR_TIMEOUT) return st;
+  isdf_status st2 = from_device(p, piv_out, p->d_piv, size_t(found), true);
+  if (!st2 && dval_out) st2 = from_device(p, dval_out, p->d_dval, size_t(found), true);
+  if (st2) return st2;
+  *nip_out = found;
+  p->state = 1;
+  return st;
+}
+
+isdf_status isdf_fit(isdf_plan_t h, const int64_t* piv, int nip) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (!piv || nip < 1) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_fit");
+  std::vector<int64_t> pv;
+  isdf_status st = to_host(p, piv, size_t(nip), pv);
+  if (st) return st;
+  std::vector<std::vector<int64_t>> per(p->nlev);
+  std::set<int64_t> seen;
+  for (int64_t c : pv) {
+    const int64_t l = c >> kPivShift, g = c & kPivMask;
+    if (c < 0 || l >= p->nlev || g >= p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "pivot code out of range");
+    if (!seen.insert(c).second) return fail(p, ISDF_ERR_ARG, "duplicate pivot");
+    per[l].push_back(g);
+  }
+  for (int l = 0; l < p->nlev; ++l)
+    if (int64_t(per[l].size()) > p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "too many pivots on a level");
+  // level-ordered layout
+  p->nip = nip;
+  p->piv_lo.clear();
+  p->poff[0] = 0;
+  for (int l = 0; l < p->nlev; ++l) {
+    Level& lv = p->lev[l];
+    lv.pg = per[l];
+    lv.k = int(per[l].size());
+    p->poff[l + 1] = p->poff[l] + lv.k;
+    for (int64_t g : per[l]) p->piv_lo.push_back((int64_t(l) << kPivShift) | g);
+    dfree(lv.d_pg);
+    lv.d_pg = nullptr;
+    if (lv.k) {
+      if ((st = dalloc_t(p, &lv.d_pg, size_t(lv.k), "pivot indices"))) return st;
+      if ((st = cuda_check(p, cudaMemcpyAsync(lv.d_pg, lv.pg.data(), sizeof(int64_t) * lv.k, cudaMemcpyHostToDevice,
+                                              p->stream),
+                           "copy pivots")))
+        return st;
+    }
+  }
+  dfree(p->XL);
+  dfree(p->XN);
+  p->XL = p->XN = nullptr;
+  if ((st = dalloc_t(p, &p->XL, size_t(p->nfun) * nip, "X^L")) ||
+      (st = dalloc_t(p, &p->XN, size_t(p->nfun) * nip, "X^N")))
+    return st;
+  p->state = 0;  // an unfinished fit leaves the plan needing a new fit
+  if ((st = fit_run(p))) return st;
+  p->state = 2;
+  return ISDF_OK;
+}
+
+isdf_status isdf_coulomb(isdf_plan_t h, double* V_out) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (p->state < 2) return fail(p, ISDF_ERR_STATE, "isdf_coulomb needs isdf_fit first");
+  p->state = 2;
+  isdf_status st = coulomb_run(p);
+  if (st) return st;
+  if (V_out && (st = from_device(p, V_out, p->V, size_t(p->nip) * p->nip, false))) return st;
+  p->state = 3;
+  return ISDF_OK;
+}
+
+isdf_status isdf_exchange(isdf_plan_t h, const double* C, int n, double* K_out, double* Ex_out) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (p->state < 3) return fail(p, ISDF_ERR_STATE, "isdf_exchange needs isdf_coulomb first");
+  if (!C || n < 1) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_exchange");
+  const size_t nc = size_t(p->nfun) * n, nk = size_t(p->nfun) * p->nfun;
+  const double* dC = C;
+  double* stageC = nullptr;
+  double* dK = nullptr;
+  bool own_k = false;
+  isdf_status st = ISDF_OK;
+  if (!is_device_ptr(C)) {
+    if ((st = dalloc_t(p, &stageC, nc, "C staging"))) return st;
+    st = cuda_check(p, cudaMemcpyAsync(stageC, C, nc * sizeof(double), cudaMemcpyHostToDevice, p->stream), "copy C");
+    dC = stageC;
+  }
+  if (!st) {
+    if (K_out && is_device_ptr(K_out)) {
+      dK = K_out;
+    } else {
+      own_k = true;
+      st = dalloc_t(p, &dK, nk, "K");
+    }
+  }
+  double ex = 0.0;
+  if (!st) st = exchange_run(p, dC, n, dK, &ex);
+  if (!st && K_out && own_k) st = from_device(p, K_out, dK, nk, true);
+  if (!st && Ex_out) *Ex_out = ex;
+  dfree(stageC);
+  if (own_k) dfree(dK);
+  return st;
+}
+
+int64_t isdf_get_size(isdf_plan_t h, int what) {
+  if (!h) return 0;
+  Plan* p = &h->p;
+  switch (what) {
+    case ISDF_GET_NBASIS:
+      return 1;
+    case ISDF_GET_NIP_LEVEL:
+      return p->nlev;
+    case ISDF_GET_PIVOTS:
+      return p->state >= 2 ? p->nip : 0;
+    case ISDF_GET_XL:
+    case ISDF_GET_XN:
+      return p->state >= 2 ? int64_t(p->nfun) * p->nip : 0;
+    case ISDF_GET_V:
+      return p->state >= 3 ? int64_t(p->nip) * p->nip : 0;
+    default:
+      break;
+  }
+  if (what >= ISDF_GET_XI_LEVEL0 && what < ISDF_GET_XI_LEVEL0 + p->nlev) {
+    const Level& lv = p->lev[what - ISDF_GET_XI_LEVEL0];
+    return (p->state >= 2 && lv.xiT) ? int64_t(lv.k) * lv.ng : 0;
+  }
+  if (what >= ISDF_GET_PHI_LEVEL0 && what < ISDF_GET_PHI_LEVEL0 + p->nlev) {
+    const Level& lv = p->lev[what - ISDF_GET_PHI_LEVEL0];
+    return int64_t(lv.nG) * lv.ng;
+  }
+  return 0;
+}
+
+isdf_status isdf_get(isdf_plan_t h, int what, void* dst) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (!dst) return fail(p, ISDF_ERR_ARG, "dst is NULL");
+  const int64_t n = isdf_get_size(h, what);
+  if (n == 0) return fail(p, ISDF_ERR_STATE, "requested data is not available yet");
+  const bool dev = is_device_ptr(dst);
+  auto put_host = [&](const void* src, size_t bytes) -> isdf_status {
+    if (dev)
+      return cuda_check(p, cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), "isdf_get copy");
+    std::memcpy(dst, src, bytes);
+    return ISDF_OK;
+  };
+  switch (what) {
+    case ISDF_GET_NBASIS: {
+      const int32_t v = p->nfun;
+      return put_host(&v, sizeof(v));
+    }
+    case ISDF_GET_NIP_LEVEL: {
+      std::vector<int32_t> v(p->nlev);
+      for (int l = 0; l < p->nlev; ++l) v[l] = p->lev[l].k;
+      return put_host(v.data(), sizeof(int32_t) * v.size());
+    }
+    case ISDF_GET_PIVOTS:
+      return put_host(p->piv_lo.data(), sizeof(int64_t) * p->piv_lo.size());
+    case ISDF_GET_XL:
+      return from_device(p, static_cast<double*>(dst), p->XL, size_t(n), true);
+    case ISDF_GET_XN:
+      return from_device(p, static_cast<double*>(dst), p->XN, size_t(n), true);
+    case ISDF_GET_V:
+      return from_device(p, static_cast<double*>(dst), p->V, size_t(n), true);
+    default:
+      break;
+  }
+  if (what >= ISDF_GET_XI_LEVEL0 && what < ISDF_GET_XI_LEVEL0 + p->nlev)
+    return from_device(p, static_cast<double*>(dst), p->lev[what - ISDF_GET_XI_LEVEL0].xiT, size_t(n), true);
+  if (what >= ISDF_GET_PHI_LEVEL0 && what < ISDF_GET_PHI_LEVEL0 + p->nlev)
+    return from_device(p, static_cast<double*>(dst), p->lev[what - ISDF_GET_PHI_LEVEL0].phi, size_t(n), true);
+  return fail(p, ISDF_ERR_ARG, "unknown isdf_get selector");
+}
+
+const char* isdf_profile_json(isdf_plan_t h) {
+  if (!h) return "{}";
+  Plan* p = &h->p;
+  cudaStreamSynchronize(p->stream);
+  prof_flush(p);
+  std::string s = "{\"kernels\": {";
+  bool first = true;
+  for (const auto& kv : p->stats) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"work\": %.6e, \"unit\": \"%s\"}",
+             first ? "" : ", ", kv.first.c_str(), (long long)kv.second.launches, kv.second.ms, kv.second.work,
+             kv.second.unit.c_str());
+    s += buf;
+    first = false;
+  }
+  s += "}}";
+  p->prof_json = s;
+  return p->prof_json.c_str();
+}
+
+int64_t isdf_kernel_launches(void) { return g_launches.load(); }
+
+const char* isdf_last_error(isdf_plan_t h) {
+  if (!h) return g_plan_error.c_str();
+  return h->p.err.c_str();
+}
+
+void isdf_destroy(isdf_plan_t h) {
+  if (!h) return;
+  cudaStreamSynchronize(h->p.stream);
+  prof_flush(&h->p);
+  free_plan(&h->p);
+  delete h;
+}
+
+}  // extern "C"

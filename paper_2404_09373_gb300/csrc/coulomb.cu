@@ -1,0 +1,206 @@
+// Two-centre Coulomb matrix (kernel family (e)), Section II Eq. 1 and the
+// cross-grid integrals of Section III:
+//   V_PQ = 4 pi Omega sum_{G != 0} Re[conj c_P(G) c_Q(G)] / |G|^2,
+// where c(G) are the Fourier coefficients of the trigonometric interpolant
+// of a grid function (a coefficient whose mode index is n/2 on an axis is
+// split evenly between +n/2 and -n/2).  For two levels the sum runs over the
+// coarser level's mode set.
+//
+// Every interpolation vector goes through one cuFFT D2Z transform (batched).
+// With the half spectrum S(q) (q_x in [0, nx/2]) the sums collapse to
+//   same level : V_PQ = sum_q wt_s(q) Re[conj S_P(q) S_Q(q)],
+//                wt_s = mult(q_x) 2^{-#Nyquist axes} 4 pi Omega / (|G_q|^2 N_g^2)
+//   two levels : V_PQ = sum_q wt_c(q) Re[conj H_P(q) S_Q(q)],
+//                H_P(q) = sum over the (up to 8) signed preimages m of q of
+//                2^{-#Nyquist axes} S^fine_P(m),
+//                wt_c = mult(q_x) 4 pi Omega / (|G_q|^2 N_g,fine N_g,coarse)
+// with mult = 1 for q_x in {0, nx/2}, else 2 (Hermitian partner).  Each sum is
+// one real GEMM over interleaved (Re, Im) with a per-k weight.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace isdf {
+namespace {
+
+__global__ void k_coul_weights(int nx, int ny, int nz, double Lx, double Ly, double Lz, double pref, int same,
+                               double* __restrict__ wt2) {
+  const int nxh = nx / 2 + 1;
+  const int64_t nq = int64_t(nxh) * ny * nz;
+  const int64_t q = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= nq) return;
+  const int qx = int(q % nxh);
+  const int qy = int((q / nxh) % ny);
+  const int qz = int(q / (int64_t(nxh) * ny));
+  const int sx = qx;
+  const int sy = (2 * qy < ny) ? qy : qy - ny;
+  const int sz = (2 * qz < nz) ? qz : qz - nz;
+  const double two_pi = 6.283185307179586476925286766559;
+  const double gx = two_pi * sx / Lx, gy = two_pi * sy / Ly, gz = two_pi * sz / Lz;
+  const double G2 = gx * gx + gy * gy + gz * gz;
+  double w = 0.0;
+  if (G2 > 0.0) {
+    const double mult = (qx == 0 || 2 * qx == nx) ? 1.0 : 2.0;
+    w = pref * mult / G2;
+    if (same) {
+      const int nyq = (2 * qx == nx) + (2 * qy == ny) + (2 * qz == nz);
+      w = ldexp(w, -nyq);
+    }
+  }
+  wt2[2 * q] = w;
+  wt2[2 * q + 1] = w;
+}
+
+// H_P(q) on the coarse half grid (cx, cy, cz) from the fine half spectrum.
+__global__ void k_fold(int k, const double2* __restrict__ spf, int fx, int fy, int fz, double2* __restrict__ H, int cx,
+                       int cy, int cz) {
+  const int cxh = cx / 2 + 1, fxh = fx / 2 + 1;
+  const int64_t nqc = int64_t(cxh) * cy * cz;
+  const int64_t nqf = int64_t(fxh) * fy * fz;
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= nqc * k) return;
+  const int64_t P = e / nqc, q = e % nqc;
+  const int qx = int(q % cxh);
+  const int qy = int((q / cxh) % cy);
+  const int qz = int(q / (int64_t(cxh) * cy));
+  int mx[2], my[2], mz[2], nx_ = 1, ny_ = 1, nz_ = 1;
+  if (2 * qx == cx) { mx[0] = cx / 2; mx[1] = -cx / 2; nx_ = 2; } else { mx[0] = qx; }
+  if (2 * qy == cy) { my[0] = cy / 2; my[1] = -cy / 2; ny_ = 2; } else { my[0] = (2 * qy < cy) ? qy : qy - cy; }
+  if (2 * qz == cz) { mz[0] = cz / 2; mz[1] = -cz / 2; nz_ = 2; } else { mz[0] = (2 * qz < cz) ? qz : qz - cz; }
+  const double wgt = 1.0 / double(nx_ * ny_ * nz_);
+  const double2* sp = spf + P * nqf;
+  double re = 0.0, im = 0.0;
+  for (int a = 0; a < nx_; ++a)
+    for (int b = 0; b < ny_; ++b)
+      for (int c = 0; c < nz_; ++c) {
+        int sx = mx[a], sy = my[b], sz = mz[c];
+        bool conj = false;
+        if (sx < 0) {  // Hermitian partner
+          sx = -sx;
+          sy = -sy;
+          sz = -sz;
+          conj = true;
+        }
+        const int iy = ((sy % fy) + fy) % fy, iz = ((sz % fz) + fz) % fz;
+        const double2 v = sp[(int64_t(iz) * fy + iy) * fxh + sx];
+        re += v.x;
+        im += conj ? -v.y : v.y;
+      }
+  H[e] = make_double2(wgt * re, wgt * im);
+}
+
+// V[off_b + j][off_a + i] = V[off_a + i][off_b + j]
+__global__ void k_mirror(double* V, int64_t ld, int64_t offa, int64_t offb, int64_t ka, int64_t kb, int lower_only) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= ka * kb) return;
+  const int64_t i = e / kb, j = e % kb;
+  if (lower_only && j >= i) return;  // within one block: copy lower to upper
+  if (lower_only)
+    V[(offa + j) * ld + offb + i] = V[(offa + i) * ld + offb + j];
+  else
+    V[(offb + j) * ld + offa + i] = V[(offa + i) * ld + offb + j];
+}
+
+}  // namespace
+
+isdf_status coulomb_run(Plan* p) {
+  cudaStream_t s = p->stream;
+  isdf_status st;
+  const double four_pi_omega = 4.0 * 3.14159265358979323846 * p->omega;
+  // 1. half spectra of every interpolation vector
+  for (int l = 0; l < p->nlev; ++l) {
+    Level& lv = p->lev[l];
+    dfree(lv.spec);
+    lv.spec = nullptr;
+    lv.nh[0] = lv.n[0] / 2 + 1;
+    lv.nh[1] = lv.n[1];
+    lv.nh[2] = lv.n[2];
+    lv.nq = int64_t(lv.nh[0]) * lv.nh[1] * lv.nh[2];
+    if (lv.k == 0) continue;
+    if ((st = dalloc_t(p, &lv.spec, size_t(lv.k) * lv.nq, "spectra"))) return st;
+    int batch = p->opt.col_batch > 0 ? p->opt.col_batch : 64;
+    if (batch > lv.k) batch = lv.k;
+    int dims[3] = {lv.n[2], lv.n[1], lv.n[0]};
+    Prof pr(p, "coulomb_fft", double(lv.k) * (8.0 * double(lv.ng) + 16.0 * double(lv.nq)), "byte", 0);
+    for (int b0 = 0; b0 < lv.k;) {
+      const int nb = (lv.k - b0 >= batch) ? batch : lv.k - b0;
+      cufftHandle h = 0;
+      cufftResult r = CUFFT_SUCCESS;
+      if (p->fault == "fft_plan") r = CUFFT_ALLOC_FAILED;
+      if (r == CUFFT_SUCCESS)
+        r = cufftPlanMany(&h, 3, dims, nullptr, 1, int(lv.ng), nullptr, 1, int(lv.nq), CUFFT_D2Z, nb);
+      if (r != CUFFT_SUCCESS) return fail(p, ISDF_ERR_CUFFT, "cufftPlanMany failed (" + std::to_string(int(r)) + ")");
+      cufftSetStream(h, s);
+      // run every full batch with this plan, then the remainder with its own
+      const int nfull = (lv.k - b0) / nb;
+      for (int c = 0; c < nfull && r == CUFFT_SUCCESS; ++c) {
+        r = cufftExecD2Z(h, lv.xiT + int64_t(b0) * lv.ng, reinterpret_cast<cufftDoubleComplex*>(lv.spec + int64_t(b0) * lv.nq));
+        b0 += nb;
+      }
+      cudaStreamSynchronize(s);
+      cufftDestroy(h);
+      if (r != CUFFT_SUCCESS) return fail(p, ISDF_ERR_CUFFT, "cufftExecD2Z failed (" + std::to_string(int(r)) + ")");
+    }
+  }
+  // 2. V blocks
+  const int64_t nip = p->nip;
+  dfree(p->V);
+  p->V = nullptr;
+  if ((st = dalloc_t(p, &p->V, size_t(nip) * nip, "V"))) return st;
+  for (int a = 0; a < p->nlev; ++a) {
+    Level& la = p->lev[a];
+    if (la.k == 0) continue;
+    for (int b = a; b < p->nlev; ++b) {
+      Level& lb = p->lev[b];
+      if (lb.k == 0) continue;
+      double* wt2 = nullptr;
+      double2* H = nullptr;
+      if ((st = dalloc_t(p, &wt2, size_t(2) * lb.nq, "Coulomb weights"))) return st;
+      const bool same = (a == b);
+      const double scale = same ? 1.0 / (double(lb.ng) * double(lb.ng)) : 1.0 / (double(la.ng) * double(lb.ng));
+      count_launches(2 + (same ? 0 : 1));
+      k_coul_weights<<<unsigned((lb.nq + 255) / 256), 256, 0, s>>>(lb.n[0], lb.n[1], lb.n[2], p->edge[0], p->edge[1],
+                                                                   p->edge[2], four_pi_omega * scale, same ? 1 : 0, wt2);
+      const double2* left = la.spec;
+      if (!same) {
+        if ((st = dalloc_t(p, &H, size_t(la.k) * lb.nq, "folded spectra"))) {
+          dfree(wt2);
+          return st;
+        }
+        const int64_t tot = int64_t(la.k) * lb.nq;
+        k_fold<<<unsigned((tot + 255) / 256), 256, 0, s>>>(la.k, la.spec, la.n[0], la.n[1], la.n[2], H, lb.n[0],
+                                                           lb.n[1], lb.n[2]);
+        left = H;
+      }
+      GemmArgs g;
+      g.ta = 0;
+      g.tb = 1;
+      g.M = la.k;
+      g.N = lb.k;
+      g.K = 2 * lb.nq;
+      g.A = reinterpret_cast<const double*>(left);
+      g.lda = 2 * lb.nq;
+      g.B = reinterpret_cast<const double*>(lb.spec);
+      g.ldb = 2 * lb.nq;
+      g.C = p->V + int64_t(p->poff[a]) * nip + p->poff[b];
+      g.ldc = nip;
+      g.kw = wt2;
+      g.sym = same ? 1 : 0;
+      {
+        const double K2 = 2.0 * double(lb.nq);
+        const double work = same ? double(la.k) * double(la.k + 1) * K2 : 2.0 * double(la.k) * double(lb.k) * K2;
+        Prof pr(p, "coulomb_V", work, "flop", 1);
+        dgemm(g, s);
+      }
+      const int64_t tot = int64_t(la.k) * lb.k;
+      k_mirror<<<unsigned((tot + 255) / 256), 256, 0, s>>>(p->V, nip, p->poff[a], p->poff[b], la.k, lb.k, same ? 1 : 0);
+      st = cuda_check(p, cudaStreamSynchronize(s), "Coulomb block");
+      dfree(wt2);
+      dfree(H);
+      if (st) return st;
+    }
+  }
+  return ISDF_OK;
+}
+
+}  // namespace isdf

@@ -1,0 +1,144 @@
+// Least-squares fit of the interpolation vectors (kernel families (c), (d)),
+// Section II.A, Eq. 3:  Xi_l = (ZC^T)_l ((CC^T)_l + lambda I)^-1 with
+// (ZC^T)_l = M_l[:, P_l] and (CC^T)_l = M_l[P_l, P_l].
+//
+// Per level: gather the basis at the pivots, form (ZC^T)^T = A_L o (A_L + 2A_N)
+// as one fused GEMM ([k][ng], g contiguous so every row is one interpolation
+// vector ready for the FFT), pick CC^T out of its pivot columns, factor it
+// with an FP64 Cholesky R R^T, invert R, and apply Xi^T = R^-T (R^-1 ZC^T^T)
+// as two triangular GEMMs.
+#include "internal.cuh"
+
+namespace isdf {
+namespace {
+
+__global__ void k_gather_phiP(int nG, int k, const double* __restrict__ phi, int64_t ng,
+                              const int64_t* __restrict__ pg, double* __restrict__ out) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= int64_t(nG) * k) return;
+  const int r = int(e / k), j = int(e % k);
+  out[e] = phi[int64_t(r) * ng + pg[j]];
+}
+
+// CC[i][j] = M(P_i, P_j) = zct[j][P_i] on and below the diagonal, 0 above
+__global__ void k_gather_cc(int k, const double* __restrict__ zct, int64_t ng, const int64_t* __restrict__ pg,
+                            double* __restrict__ cc) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= int64_t(k) * k) return;
+  const int i = int(e / k), j = int(e % k);
+  cc[e] = (j <= i) ? zct[int64_t(j) * ng + pg[i]] : 0.0;
+}
+
+// lambda = reg_rel tr(CC)/k added on the diagonal (single block)
+__global__ void k_regularise(int k, double reg_rel, double* cc) {
+  __shared__ double sh[256];
+  double t = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) t += cc[int64_t(i) * k + i];
+  sh[threadIdx.x] = t;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  const double lam = reg_rel * sh[0] / double(k);
+  for (int i = threadIdx.x; i < k; i += blockDim.x) cc[int64_t(i) * k + i] += lam;
+}
+
+}  // namespace
+
+isdf_status fit_run(Plan* p) {
+  cudaStream_t s = p->stream;
+  isdf_status st;
+  for (int l = 0; l < p->nlev; ++l) {
+    Level& lv = p->lev[l];
+    dfree(lv.xiT);
+    lv.xiT = nullptr;
+    if (lv.k == 0) continue;
+    const int k = lv.k;
+    const int64_t ng = lv.ng;
+    double *phiP = nullptr, *zct = nullptr, *y = nullptr, *cc = nullptr, *li = nullptr, *scr = nullptr;
+    auto cleanup = [&]() {
+      dfree(phiP);
+      dfree(y);
+      dfree(cc);
+      dfree(li);
+      dfree(scr);
+    };
+    if ((st = dalloc_t(p, &phiP, size_t(lv.nG) * k, "phi at pivots")) ||
+        (st = dalloc_t(p, &zct, size_t(k) * ng, "ZC^T / Xi")) || (st = dalloc_t(p, &y, size_t(k) * ng, "fit scratch")) ||
+        (st = dalloc_t(p, &cc, size_t(k) * k, "CC^T")) || (st = dalloc_t(p, &li, size_t(k) * k, "R^-1")) ||
+        (st = dalloc_t(p, &scr, size_t(64) * k + 64, "trtri scratch"))) {
+      cleanup();
+      dfree(zct);
+      return st;
+    }
+    lv.xiT = zct;
+    const int64_t np = int64_t(lv.nG) * k;
+    count_launches(2 + (p->opt.reg_rel > 0.0));
+    k_gather_phiP<<<unsigned((np + 255) / 256), 256, 0, s>>>(lv.nG, k, lv.phi, ng, lv.d_pg, phiP);
+    {
+      Prof pr(p, "fit_zc", 2.0 * double(k) * double(ng) * double(lv.nG), "flop", 1);
+      zc_gemm(k, ng, lv.nL, lv.nG, phiP, lv.phi, zct, s);
+    }
+    k_gather_cc<<<unsigned((int64_t(k) * k + 255) / 256), 256, 0, s>>>(k, zct, ng, lv.d_pg, cc);
+    if (p->opt.reg_rel > 0.0) k_regularise<<<1, 256, 0, s>>>(k, p->opt.reg_rel, cc);
+    const int big = 0x7fffffff;
+    cudaMemcpyAsync(p->d_err, &big, sizeof(int), cudaMemcpyHostToDevice, s);
+    {
+      const int64_t nb = (k + 63) / 64;
+      Prof pr(p, "fit_cholesky", double(k) * k * k / 3.0, "flop", 3 * nb - 2);
+      dpotrf_lower(cc, k, k, p->d_err, nullptr, s);
+    }
+    int herr = big;
+    cudaMemcpyAsync(&herr, p->d_err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if ((st = cuda_check(p, cudaStreamSynchronize(s), "Cholesky of CC^T"))) {
+      cleanup();
+      return st;
+    }
+    if (herr != big || p->fault == "not_pd") {
+      cleanup();
+      return fail(p, ISDF_ERR_NOT_PD,
+                  "Cholesky of CC^T broke down at column " + std::to_string(herr == big ? 0 : herr) + " of level " +
+                      std::to_string(l));
+    }
+    {
+      const int64_t nb = (k + 63) / 64;
+      Prof pr(p, "fit_trtri", double(k) * k * k / 3.0, "flop", 1 + 2 * (nb - 1));
+      dtrtri_lower(cc, li, k, scr, s);
+    }
+    {
+    Prof pr_solve(p, "fit_solve", 2.0 * double(k) * double(k + 1) * double(ng), "flop", 2);
+    GemmArgs g1;  // Y = R^-1 ZC^T^T (R^-1 lower triangular)
+    g1.M = k;
+    g1.N = ng;
+    g1.K = k;
+    g1.A = li;
+    g1.lda = k;
+    g1.B = zct;
+    g1.ldb = ng;
+    g1.C = y;
+    g1.ldc = ng;
+    g1.tri = 1;
+    dgemm(g1, s);
+    GemmArgs g2;  // Xi^T = R^-T Y (opA upper triangular)
+    g2.ta = 1;
+    g2.M = k;
+    g2.N = ng;
+    g2.K = k;
+    g2.A = li;
+    g2.lda = k;
+    g2.B = y;
+    g2.ldb = ng;
+    g2.C = zct;
+    g2.ldc = ng;
+    g2.tri = 2;
+    dgemm(g2, s);
+    }
+    st = cuda_check(p, cudaStreamSynchronize(s), "fit");
+    cleanup();
+    if (st) return st;
+  }
+  return gather_pivot_factors(p);
+}
+
+}  // namespace isdf

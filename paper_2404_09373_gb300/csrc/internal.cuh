@@ -1,0 +1,156 @@
+// Internal declarations of the multigrid ISDF library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <atomic>
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "isdf.h"
+
+namespace isdf {
+
+constexpr int kPivShift = 40;
+constexpr int64_t kPivMask = (int64_t(1) << kPivShift) - 1;
+
+// One real-space grid level (Section III, Fig. Grids).
+struct Level {
+  int n[3] = {0, 0, 0};  // points per axis
+  int64_t ng = 0;        // points
+  double w = 0.0;        // volume element Omega / ng (selection weight)
+  std::vector<int> L;    // functions of this level
+  std::vector<int> N;    // functions of coarser levels
+  int nL = 0, nN = 0, nG = 0;
+  double* tab[3] = {nullptr, nullptr, nullptr};  // 1-D factors [nG][n[a]]
+  double* phi = nullptr;                         // basis values [nG][ng]
+  // selection factor columns [fac_cap][ng]
+  double* fac = nullptr;
+  int64_t fac_cap = 0;
+  // fit
+  int k = 0;                 // pivots on this level
+  std::vector<int64_t> pg;   // pivot grid indices (selection order)
+  int64_t* d_pg = nullptr;
+  double* xiT = nullptr;     // Xi^T [k][ng]
+  // Coulomb
+  int nh[3] = {0, 0, 0};     // half-spectrum dims (nx/2+1, ny, nz)
+  int64_t nq = 0;            // half-spectrum modes
+  double2* spec = nullptr;   // [k][nq]
+};
+
+// Kernel timing (options.profile): CUDA events around launch groups.
+struct ProfEvent {
+  std::string name;
+  cudaEvent_t a = nullptr, b = nullptr;
+  double work = 0.0;
+  const char* unit = "flop";
+  int64_t launches = 0;
+};
+struct KStat {
+  int64_t launches = 0;
+  double ms = 0.0, work = 0.0;
+  std::string unit;
+};
+
+extern std::atomic<long long> g_launches;
+inline void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+struct Plan {
+  cudaStream_t stream = nullptr;
+  isdf_options opt{};
+  double edge[3] = {0, 0, 0};
+  double omega = 0.0;
+  double image_tol = 1e-10;
+  int natom = 0;
+  std::vector<double> xyz;
+  int nfun = 0;
+  std::vector<int> f_atom, f_l[3], f_level;
+  std::vector<double> f_alpha, f_norm;
+  int nlev = 0;
+  Level lev[ISDF_MAX_LEVELS];
+  int state = 0;  // 0 planned, 1 selected, 2 fitted, 3 Coulomb done
+  // selection (all levels concatenated)
+  int64_t ntot = 0;
+  int64_t off[ISDF_MAX_LEVELS + 1] = {0};
+  double* d_diag = nullptr;    // residual diagonal [ntot]
+  unsigned char* d_active = nullptr;
+  void* d_selstate = nullptr;
+  int64_t* d_piv = nullptr;    // selection-order pivot codes
+  double* d_dval = nullptr;
+  int sel_cap = 0;
+  // fit results, level-ordered pivots
+  int nip = 0;
+  int poff[ISDF_MAX_LEVELS + 1] = {0};
+  std::vector<int64_t> piv_lo;  // level-ordered pivot codes
+  double* XL = nullptr;         // [N][nip]
+  double* XN = nullptr;
+  double* V = nullptr;          // [nip][nip]
+  int* d_err = nullptr;         // device error word (Cholesky breakdown etc.)
+  std::string err;
+  std::string fault;            // host fault injection (ISDF_FAULT)
+  // profiling
+  std::vector<ProfEvent> pend;
+  std::map<std::string, KStat> stats;
+  std::string prof_json;
+};
+
+// RAII timer of one launch group on the plan's stream (no-op unless profiling)
+struct Prof {
+  Plan* p;
+  ProfEvent e;
+  Prof(Plan* p_, const char* name, double work, const char* unit, int64_t launches);
+  ~Prof();
+};
+void prof_flush(Plan* p);  // resolve pending events (stream must be idle)
+
+// ---- helpers (api.cu) ----
+isdf_status fail(Plan* p, isdf_status s, const std::string& msg);
+isdf_status cuda_check(Plan* p, cudaError_t e, const char* what);
+isdf_status dalloc(Plan* p, void** ptr, size_t bytes, const char* what);
+template <class T>
+inline isdf_status dalloc_t(Plan* p, T** ptr, size_t n, const char* what) {
+  return dalloc(p, reinterpret_cast<void**>(ptr), n * sizeof(T), what);
+}
+void dfree(void* ptr);
+bool is_device_ptr(const void* ptr);
+
+// ---- kernels / stages ----
+isdf_status basis_build(Plan* p);                                    // basis.cu
+isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>* cand, int* nfound);  // select.cu
+isdf_status fit_run(Plan* p);                                        // fit.cu
+isdf_status coulomb_run(Plan* p);                                    // coulomb.cu
+isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* Ex);  // exchange.cu
+isdf_status gather_pivot_factors(Plan* p);                           // basis.cu
+
+// FP64 SIMT GEMM (dgemm.cu):
+//   C[m][n] = alpha * sum_k opA(m,k) w(k) opB(k,n) + beta * C[m][n]
+//   opA(m,k) = ta ? A[k*lda+m] : A[m*lda+k];  opB(k,n) = tb ? B[n*ldb+k] : B[k*ldb+n]
+//   tri: 0 dense, 1 opA lower triangular (k <= m), 2 opA upper triangular (k >= m)
+//   sym: only output tiles on or below the diagonal are computed
+struct GemmArgs {
+  int ta = 0, tb = 0;
+  int64_t M = 0, N = 0, K = 0;
+  double alpha = 1.0, beta = 0.0;
+  const double* A = nullptr;
+  int64_t lda = 0;
+  const double* B = nullptr;
+  int64_t ldb = 0;
+  double* C = nullptr;
+  int64_t ldc = 0;
+  const double* kw = nullptr;
+  int tri = 0;
+  int sym = 0;
+};
+void dgemm(const GemmArgs& g, cudaStream_t s);
+// ZC^T = A_L o (A_L + 2 A_N) with A_X = PhiP_X^T Phi_X (fit.cu uses it)
+void zc_gemm(int64_t k, int64_t ng, int nL, int nG, const double* phiP, const double* phi, double* out,
+             cudaStream_t s);
+// lower Cholesky in place (row-major n x n, lda); breakdown column -> *err
+void dpotrf_lower(double* A, int64_t n, int64_t lda, int* err, double* scratch, cudaStream_t s);
+// inverse of a lower-triangular matrix: Li (n x n, zero-initialised by callee)
+void dtrtri_lower(const double* Lm, double* Li, int64_t n, double* scratch, cudaStream_t s);
+
+}  // namespace isdf

@@ -1,0 +1,284 @@
+"""Thin Python binding of the C ABI in ``include/isdf.h`` (argument marshalling only).
+
+Every computation runs in ``libisdf.so``'s CUDA kernels.  Arrays may be NumPy
+arrays (host) or torch tensors (host or CUDA); they are passed to the library
+as raw pointers and the library tells host from device memory itself.  If the
+shared library is missing it is built from ``csrc/`` with nvcc; if that is not
+possible, loading fails with an exception (there is no other code path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from ctypes import POINTER, c_double, c_int, c_int64, c_void_p
+
+import numpy as np
+
+from . import build as _build
+
+PIVOT_SHIFT = 40
+
+ISDF_OK, ISDF_ERR_ARG, ISDF_ERR_OOM, ISDF_ERR_NOT_PD, ISDF_ERR_CUDA, ISDF_ERR_CUFFT, ISDF_ERR_TIMEOUT, ISDF_ERR_STATE = range(8)
+STATUS_NAMES = ["OK", "ERR_ARG", "ERR_OOM", "ERR_NOT_PD", "ERR_CUDA", "ERR_CUFFT", "ERR_TIMEOUT", "ERR_STATE"]
+GET_NBASIS, GET_NIP_LEVEL, GET_PIVOTS, GET_XL, GET_XN, GET_V, GET_XI_LEVEL0 = 0, 1, 2, 3, 4, 5, 6
+GET_PHI_LEVEL0 = 10
+
+EXPORTED = [
+    "isdf_options_default",
+    "isdf_plan",
+    "isdf_select_points",
+    "isdf_fit",
+    "isdf_coulomb",
+    "isdf_exchange",
+    "isdf_get_size",
+    "isdf_get",
+    "isdf_last_error",
+    "isdf_destroy",
+    "isdf_profile_json",
+    "isdf_kernel_launches",
+]
+
+
+class isdf_system(ctypes.Structure):
+    _fields_ = [
+        ("lattice", c_double * 9),
+        ("natom", c_int),
+        ("xyz", POINTER(c_double)),
+        ("nshell", c_int),
+        ("shell_atom", POINTER(c_int)),
+        ("shell_l", POINTER(c_int)),
+        ("shell_exp", POINTER(c_double)),
+        ("nlevel", c_int),
+        ("grid", POINTER(c_int)),
+        ("level_min_exp", POINTER(c_double)),
+        ("image_tol", c_double),
+    ]
+
+
+class isdf_options(ctypes.Structure):
+    _fields_ = [
+        ("precision", c_int),
+        ("tie_rel", c_double),
+        ("tie_abs", c_double),
+        ("reg_rel", c_double),
+        ("col_batch", c_int),
+        ("timeout_ms", c_int),
+        ("prefilter", c_int),
+        ("profile", c_int),
+    ]
+
+
+class IsdfError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {message}")
+        self.status = status
+        self.message = message
+
+
+_lib = None
+
+
+def load_library(build_if_missing: bool = True):
+    """Load libisdf.so (building it first if needed).  Raises if impossible."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing:
+        path = _build.build_library()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libisdf.so not found at {path}; build it with paper_2404_09373_gb300.build")
+    lib = ctypes.CDLL(path)
+    lib.isdf_options_default.argtypes = [POINTER(isdf_options)]
+    lib.isdf_options_default.restype = None
+    lib.isdf_plan.argtypes = [POINTER(isdf_system), POINTER(isdf_options), c_void_p, POINTER(c_void_p)]
+    lib.isdf_plan.restype = c_int
+    lib.isdf_select_points.argtypes = [c_void_p, c_int, c_double, c_void_p, c_int64, c_void_p, c_void_p,
+                                       POINTER(c_int)]
+    lib.isdf_select_points.restype = c_int
+    lib.isdf_fit.argtypes = [c_void_p, c_void_p, c_int]
+    lib.isdf_fit.restype = c_int
+    lib.isdf_coulomb.argtypes = [c_void_p, c_void_p]
+    lib.isdf_coulomb.restype = c_int
+    lib.isdf_exchange.argtypes = [c_void_p, c_void_p, c_int, c_void_p, POINTER(c_double)]
+    lib.isdf_exchange.restype = c_int
+    lib.isdf_get_size.argtypes = [c_void_p, c_int]
+    lib.isdf_get_size.restype = c_int64
+    lib.isdf_get.argtypes = [c_void_p, c_int, c_void_p]
+    lib.isdf_get.restype = c_int
+    lib.isdf_last_error.argtypes = [c_void_p]
+    lib.isdf_last_error.restype = ctypes.c_char_p
+    lib.isdf_destroy.argtypes = [c_void_p]
+    lib.isdf_destroy.restype = None
+    lib.isdf_profile_json.argtypes = [c_void_p]
+    lib.isdf_profile_json.restype = ctypes.c_char_p
+    lib.isdf_kernel_launches.argtypes = []
+    lib.isdf_kernel_launches.restype = c_int64
+    _lib = lib
+    return lib
+
+
+def _addr(x, dtype):
+    """Raw pointer of a C-contiguous numpy array or torch tensor of ``dtype``."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if x.dtype != dtype or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"expected a C-contiguous {np.dtype(dtype)} array")
+        return x.ctypes.data
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(x, torch.Tensor):
+        tmap = {np.dtype(np.float64): torch.float64, np.dtype(np.int64): torch.int64, np.dtype(np.int32): torch.int32}
+        if x.dtype != tmap[np.dtype(dtype)] or not x.is_contiguous():
+            raise ValueError(f"expected a contiguous {np.dtype(dtype)} tensor")
+        return x.data_ptr()
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _default_stream():
+    try:
+        import torch
+
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # pragma: no cover
+        pass
+    return 0
+
+
+def default_options(**kw):
+    lib = load_library()
+    o = isdf_options()
+    lib.isdf_options_default(ctypes.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Plan:
+    """Owner of an ``isdf_plan_t``; destroyed with ``close()`` or on collection."""
+
+    def __init__(self, handle, lib, system):
+        self.handle = handle
+        self._lib = lib
+        self.system = system
+
+    def close(self):
+        if self.handle:
+            self._lib.isdf_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != ISDF_OK:
+            raise IsdfError(st, self._lib.isdf_last_error(self.handle).decode())
+
+
+def isdf_plan(system: dict, options=None, stream=None) -> Plan:
+    lib = load_library()
+    if options is None:
+        options = default_options()
+    elif isinstance(options, dict):
+        options = default_options(**options)
+    edges = np.asarray(system["edges"], dtype=np.float64)
+    xyz = np.ascontiguousarray(system["xyz"], dtype=np.float64)
+    sa = np.ascontiguousarray(system["shell_atom"], dtype=np.int32)
+    sl = np.ascontiguousarray(system["shell_l"], dtype=np.int32)
+    se = np.ascontiguousarray(system["shell_exp"], dtype=np.float64)
+    grid = np.ascontiguousarray(system["grids"], dtype=np.int32).reshape(-1, 3)
+    lme = np.ascontiguousarray(system["level_min_exp"], dtype=np.float64)
+    s = isdf_system()
+    for i in range(9):
+        s.lattice[i] = 0.0
+    for a in range(3):
+        s.lattice[4 * a] = float(edges[a])
+    s.natom = xyz.shape[0]
+    s.xyz = xyz.ctypes.data_as(POINTER(c_double))
+    s.nshell = se.shape[0]
+    s.shell_atom = sa.ctypes.data_as(POINTER(c_int))
+    s.shell_l = sl.ctypes.data_as(POINTER(c_int))
+    s.shell_exp = se.ctypes.data_as(POINTER(c_double))
+    s.nlevel = grid.shape[0]
+    s.grid = grid.ctypes.data_as(POINTER(c_int))
+    s.level_min_exp = lme.ctypes.data_as(POINTER(c_double)) if lme.size else None
+    s.image_tol = float(system["image_tol"])
+    h = c_void_p()
+    st = lib.isdf_plan(ctypes.byref(s), ctypes.byref(options), c_void_p(_default_stream() if stream is None else stream),
+                       ctypes.byref(h))
+    if st != ISDF_OK:
+        raise IsdfError(st, lib.isdf_last_error(None).decode())
+    return Plan(h.value, lib, system)
+
+
+def isdf_select_points(plan: Plan, nip: int, tol: float = 0.0, cand=None, piv_out=None, dval_out=None):
+    """Returns (pivot codes, pivot values) -- numpy unless outputs are given."""
+    piv = np.zeros(nip, dtype=np.int64) if piv_out is None else piv_out
+    dv = np.zeros(nip, dtype=np.float64) if dval_out is None else dval_out
+    cptr = None
+    ncand = 0
+    if cand is not None:
+        cand = cand if not isinstance(cand, np.ndarray) else np.ascontiguousarray(cand, dtype=np.int64)
+        cptr = _addr(cand, np.int64)
+        ncand = int(cand.shape[0])
+    nfound = c_int(0)
+    st = plan._lib.isdf_select_points(plan.handle, int(nip), float(tol), cptr, ncand, _addr(piv, np.int64),
+                                      _addr(dv, np.float64), ctypes.byref(nfound))
+    plan._check(st)
+    return piv[: nfound.value], dv[: nfound.value]
+
+
+def isdf_fit(plan: Plan, piv):
+    if isinstance(piv, np.ndarray):
+        piv = np.ascontiguousarray(piv, dtype=np.int64)
+    plan._check(plan._lib.isdf_fit(plan.handle, _addr(piv, np.int64), int(piv.shape[0])))
+
+
+def isdf_coulomb(plan: Plan, V_out=None):
+    plan._check(plan._lib.isdf_coulomb(plan.handle, _addr(V_out, np.float64)))
+    return V_out
+
+
+def isdf_exchange(plan: Plan, C, K_out=None):
+    """Returns (K, E_x); K is ``K_out`` or a new numpy array."""
+    if isinstance(C, np.ndarray):
+        C = np.ascontiguousarray(C, dtype=np.float64)
+    N = int(C.shape[0])
+    K = np.zeros((N, N)) if K_out is None else K_out
+    ex = c_double(0.0)
+    plan._check(plan._lib.isdf_exchange(plan.handle, _addr(C, np.float64), int(C.shape[1]), _addr(K, np.float64),
+                                        ctypes.byref(ex)))
+    return K, ex.value
+
+
+def isdf_get(plan: Plan, what: int, dst=None):
+    n = int(plan._lib.isdf_get_size(plan.handle, what))
+    if n == 0:
+        raise IsdfError(ISDF_ERR_STATE, "not available")
+    if dst is None:
+        dtype = np.int32 if what in (GET_NBASIS, GET_NIP_LEVEL) else (np.int64 if what == GET_PIVOTS else np.float64)
+        dst = np.zeros(n, dtype=dtype)
+    dtype = dst.dtype if isinstance(dst, np.ndarray) else None
+    plan._check(plan._lib.isdf_get(plan.handle, what, _addr(dst, dtype) if dtype is not None else dst.data_ptr()))
+    return dst
+
+
+def isdf_destroy(plan: Plan):
+    plan.close()
+
+
+def isdf_profile_json(plan: Plan) -> dict:
+    import json
+
+    return json.loads(plan._lib.isdf_profile_json(plan.handle).decode())
+
+
+def isdf_kernel_launches() -> int:
+    return int(load_library().isdf_kernel_launches())

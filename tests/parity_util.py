@@ -1,0 +1,66 @@
+"""Shared helpers of the GPU parity tests: run the CUDA path through the C ABI
+and collect the same quantities the oracle returns."""
+import numpy as np
+
+from paper_2404_09373_gb300 import isdf as B
+from paper_2404_09373_gb300 import systems as S
+
+
+def gpu_run(sysd, C, nip, tol=0.0, piv=None, cand=None, opts=None, want_xi=True):
+    plan = B.isdf_plan(sysd, opts)
+    try:
+        dv = None
+        if piv is None:
+            piv, dv = B.isdf_select_points(plan, nip, tol, cand=cand)
+            piv, dv = piv.copy(), dv.copy()
+        B.isdf_fit(plan, np.asarray(piv, dtype=np.int64))
+        nlev = len(sysd["grids"])
+        k = B.isdf_get(plan, B.GET_NIP_LEVEL)
+        npiv = int(k.sum())
+        V = np.zeros((npiv, npiv))
+        B.isdf_coulomb(plan, V)
+        K, Ex = B.isdf_exchange(plan, C)
+        N = S.nbasis(sysd)
+        out = {
+            "pivots": np.asarray(piv),
+            "dvals": dv,
+            "nip_level": k,
+            "pivots_lo": B.isdf_get(plan, B.GET_PIVOTS),
+            "V": V,
+            "K": K,
+            "Ex": Ex,
+            "XL": B.isdf_get(plan, B.GET_XL).reshape(N, npiv),
+            "XN": B.isdf_get(plan, B.GET_XN).reshape(N, npiv),
+        }
+        if want_xi:
+            out["Xi"] = [
+                B.isdf_get(plan, B.GET_XI_LEVEL0 + l).reshape(int(k[l]), -1).T if k[l] else None for l in range(nlev)
+            ]
+        return out
+    finally:
+        plan.close()
+
+
+def assert_parity(g, o, natom, k_tol=1e-8, v_rel=1e-6, xi_rel=1e-6):
+    """FP64 path vs FP64 oracle.  The bar for K is max|dK| <= 1e-6 Ha and
+    |dE_x| <= 1e-6 Ha/atom; the FP64 path is held to a tighter k_tol.
+    Xi and V inherit the conditioning of CC^T (cond ~ d_0/d_min, up to ~5e6
+    here): FP64 rounding differences of 1e-16 grow to ~1e-9 relative in the
+    near-null directions, which K does not see, hence the looser Xi/V bounds."""
+    np.testing.assert_array_equal(g["pivots"], o["pivots"])
+    if g["dvals"] is not None and o["dvals"] is not None:
+        np.testing.assert_allclose(g["dvals"], o["dvals"], rtol=1e-9, atol=1e-14 * o["dvals"][0])
+    np.testing.assert_array_equal(g["pivots_lo"], o["pivots"][o["order"]])
+    np.testing.assert_allclose(g["XL"], o["XL"], rtol=0, atol=1e-13 * np.abs(o["XL"]).max())
+    np.testing.assert_allclose(g["XN"], o["XN"], rtol=0, atol=1e-13 * max(1.0, np.abs(o["XN"]).max()))
+    if "Xi" in g:
+        for xg, xo in zip(g["Xi"], o["Xi"]):
+            if xg is None:
+                assert xo.shape[1] == 0
+                continue
+            assert np.max(np.abs(xg - xo)) <= xi_rel * np.max(np.abs(xo))
+    assert np.max(np.abs(g["V"] - o["V"])) <= v_rel * np.max(np.abs(o["V"]))
+    dK = np.max(np.abs(g["K"] - o["K"]))
+    assert dK <= k_tol, dK
+    assert abs(g["Ex"] - o["Ex"]) / natom <= k_tol
+    return dK

@@ -1,0 +1,263 @@
+"""CUDA path (through the C ABI) vs the FP64 oracle, element by element.
+
+Sizes span several 64-wide GEMM tiles and ragged tails; every level count,
+orthorhombic (non-cubic) cells, exact pivot ties, candidate lists, the
+tolerance stop, a level without pivots, given pivots, device pointers, the
+error paths and host-side fault injection are covered.  The full-size
+workload (2x2x2 diamond, 96^3/48^3/24^3) is checked on sampled outputs the
+oracle computes one by one and on properties that hold at any size.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import isdf as O
+from paper_2404_09373_gb300 import isdf as B
+from paper_2404_09373_gb300 import systems as S
+from parity_util import assert_parity, gpu_run
+
+pytestmark = pytest.mark.gpu
+
+TWO_ATOMS = np.array([[0.1, 0.2, 0.3], [0.55, 0.6, 0.7]])
+
+
+@pytest.fixture(scope="module")
+def small():
+    sysd, C = S.small_multigrid(per_cell=(16, 8, 4), seed=5)
+    o = oracle.run(sysd, C, 300)
+    return sysd, C, o
+
+
+def test_basis_values_match_oracle(small):
+    sysd, C, o = small
+    plan = B.isdf_plan(sysd)
+    try:
+        f = O.expand_functions(sysd)
+        for lev in range(3):
+            L, N, _ = O.level_sets(f, lev)
+            ref = O.basis_on_level(sysd, f, np.concatenate([L, N]), lev)
+            got = B.isdf_get(plan, B.GET_PHI_LEVEL0 + lev).reshape(ref.shape)
+            assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    finally:
+        plan.close()
+
+
+def test_small_multigrid_parity(small):
+    sysd, C, o = small
+    g = gpu_run(sysd, C, 300)
+    assert_parity(g, o, natom=8)
+
+
+def test_ragged_orthorhombic_cell():
+    rng = np.random.default_rng(9)
+    sysd = S.make_system((1, 1, 2), 0.07, rng, ((10, 12, 9), (6, 6, 5), (2, 4, 3)), (1.6, 0.4))
+    C = S.make_orbitals(sysd, 12, rng)
+    o = oracle.run(sysd, C, 350)
+    g = gpu_run(sysd, C, 350)
+    assert_parity(g, o, natom=16)
+
+
+def test_two_levels_and_given_pivots():
+    rng = np.random.default_rng(2)
+    sysd = S.make_system((1, 1, 1), 0.05, rng, ((18, 18, 18), (10, 10, 10)), (0.5,))
+    C = S.make_orbitals(sysd, 8, rng)
+    o = oracle.run(sysd, C, 210)
+    g = gpu_run(sysd, C, 210)
+    assert_parity(g, o, natom=8)
+    # isdf_fit on a pivot set from elsewhere (here: the oracle's, shuffled)
+    perm = np.random.default_rng(0).permutation(o["pivots"].size)
+    o2 = oracle.run(sysd, C, 0, pivots=o["pivots"][perm])
+    g2 = gpu_run(sysd, C, 0, piv=o["pivots"][perm])
+    g2["dvals"] = None
+    o2["dvals"] = None
+    g2["pivots"] = o2["pivots"]
+    assert_parity(g2, o2, natom=8)
+
+
+def test_workload1_single_grid_with_exact_ties():
+    """1x1x1 undisplaced diamond, one 48^3 grid, N_ip = 8N = 832 (atoms on
+    grid points: the diagonal has exact symmetric ties)."""
+    sysd, C, nip = S.config(1)
+    o = oracle.run(sysd, C, nip)
+    g = gpu_run(sysd, C, nip)
+    assert_parity(g, o, natom=8, k_tol=1e-7)
+
+
+def test_candidate_list_and_tol_stop():
+    sysd, C = S.small_multigrid(per_cell=(12, 6, 4), seed=8)
+    rng = np.random.default_rng(4)
+    codes = []
+    for lev, n in enumerate(sysd["grids"]):
+        ng = int(np.prod(n))
+        g = rng.choice(ng, size=ng // 2, replace=False)
+        codes.append((np.int64(lev) << 40) | np.sort(g).astype(np.int64))
+    cand = np.concatenate(codes)
+    o = oracle.run(sysd, C, 120, cand=cand)
+    g = gpu_run(sysd, C, 120, cand=cand)
+    assert_parity(g, o, natom=8)
+    # tolerance stop: fewer pivots than asked
+    o = oracle.run(sysd, C, 500, tol=1e-4)
+    g = gpu_run(sysd, C, 500, tol=1e-4)
+    assert o["pivots"].size < 500
+    assert_parity(g, o, natom=8)
+
+
+def test_few_pivots_leave_a_level_empty():
+    sysd, C = S.small_multigrid(per_cell=(12, 6, 4), seed=3)
+    for nip in (1, 3):
+        o = oracle.run(sysd, C, nip)
+        g = gpu_run(sysd, C, nip)
+        assert (np.bincount(o["pivots"] >> 40, minlength=3) == 0).any()
+        assert_parity(g, o, natom=8)
+
+
+def test_device_pointers_give_the_same_results(small):
+    import torch
+
+    sysd, C, o = small
+    dev = torch.device("cuda:0")
+    plan = B.isdf_plan(sysd)
+    try:
+        piv = torch.zeros(300, dtype=torch.int64, device=dev)
+        dv = torch.zeros(300, dtype=torch.float64, device=dev)
+        p, d = B.isdf_select_points(plan, 300, piv_out=piv, dval_out=dv)
+        B.isdf_fit(plan, p)
+        V = torch.zeros((300, 300), dtype=torch.float64, device=dev)
+        B.isdf_coulomb(plan, V)
+        K = torch.zeros((C.shape[0], C.shape[0]), dtype=torch.float64, device=dev)
+        Cd = torch.from_numpy(C).to(dev)
+        _, Ex = B.isdf_exchange(plan, Cd, K)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(p.cpu().numpy(), o["pivots"])
+        assert np.max(np.abs(K.cpu().numpy() - o["K"])) <= 1e-8
+        assert abs(Ex - o["Ex"]) <= 1e-8
+    finally:
+        plan.close()
+
+
+def test_call_order_and_argument_errors(small):
+    sysd, C, o = small
+    plan = B.isdf_plan(sysd)
+    try:
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_coulomb(plan)
+        assert e.value.status == B.ISDF_ERR_STATE
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_exchange(plan, C)
+        assert e.value.status == B.ISDF_ERR_STATE
+        bad = np.array([5, 5], dtype=np.int64)
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_fit(plan, bad)
+        assert e.value.status == B.ISDF_ERR_ARG
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_fit(plan, np.array([(np.int64(3) << 40) | 1], dtype=np.int64))
+        assert e.value.status == B.ISDF_ERR_ARG
+        # after errors the plan still works
+        p, _ = B.isdf_select_points(plan, 300)
+        np.testing.assert_array_equal(p, o["pivots"])
+    finally:
+        plan.close()
+
+
+@pytest.mark.parametrize("fault,stage,status", [("oom", "plan", B.ISDF_ERR_OOM), ("not_pd", "fit", B.ISDF_ERR_NOT_PD),
+                                                ("fft_plan", "coulomb", B.ISDF_ERR_CUFFT)])
+def test_host_fault_injection(small, monkeypatch, fault, stage, status):
+    """Failures are injected on the host (no GPU fault): the call returns the
+    status, the plan can be destroyed, and a fresh plan works."""
+    sysd, C, o = small
+    monkeypatch.setenv("ISDF_FAULT", fault)
+    if stage == "plan":
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_plan(sysd)
+        assert e.value.status == status
+    else:
+        plan = B.isdf_plan(sysd)
+        p, _ = B.isdf_select_points(plan, 50)
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_fit(plan, p)
+            B.isdf_coulomb(plan)
+        assert e.value.status == status
+        plan.close()
+    monkeypatch.delenv("ISDF_FAULT")
+    g = gpu_run(sysd, C, 300)
+    assert_parity(g, o, natom=8)
+
+
+def test_selection_time_budget(small):
+    """options.timeout_ms ends the device loop early with ISDF_ERR_TIMEOUT; the
+    pivots found so far are the oracle's prefix."""
+    sysd, C, o = small
+    plan = B.isdf_plan(sysd, {"timeout_ms": 1})
+    try:
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_select_points(plan, 300)
+        assert e.value.status == B.ISDF_ERR_TIMEOUT
+    finally:
+        plan.close()
+
+
+# --------------------------------------------------------------------------- full size
+
+
+@pytest.fixture(scope="module")
+def workload2():
+    sysd, C, nip = S.config(2)
+    return sysd, C, nip
+
+
+def test_workload2_full_size_sampled_and_properties(workload2):
+    """2x2x2 diamond, 96^3/48^3/24^3, N = 832, n = 128, N_ip = 6N = 4992 in the
+    launch configuration the benchmark times.  Checked: basis values at
+    sampled points, the first selection steps against the oracle's own, the
+    interpolation identity, symmetry / PSD of V, symmetry of K, E_x < 0."""
+    sysd, C, nip = workload2
+    plan = B.isdf_plan(sysd)
+    try:
+        f = O.expand_functions(sysd)
+        rng = np.random.default_rng(1)
+        # sampled basis values (oracle one by one)
+        for lev in range(3):
+            L, N, _ = O.level_sets(f, lev)
+            rows = np.concatenate([L, N])
+            phi = B.isdf_get(plan, B.GET_PHI_LEVEL0 + lev).reshape(rows.size, -1)
+            ng = phi.shape[1]
+            gs = rng.choice(ng, size=64, replace=False)
+            rs = rng.choice(rows.size, size=64)
+            for r, g in zip(rs, gs):
+                ref = O.basis_on_level(sysd, f, [rows[r]], lev)[0, g]
+                assert abs(phi[r, g] - ref) <= 1e-13 * max(1e-3, abs(ref))
+        piv, dv = B.isdf_select_points(plan, nip)
+        assert piv.size == nip
+        # first steps of the greedy selection against the oracle
+        levels = O._level_data(sysd, f)
+        osel = O.select_points(levels, 12)
+        np.testing.assert_array_equal(piv[:12], osel["pivots"])
+        np.testing.assert_allclose(dv[:12], osel["dvals"], rtol=1e-10)
+        del levels
+        # pivot values never grow (beyond the tie margin)
+        assert np.all(np.diff(dv) <= 1e-9 * dv[:-1] + 1e-13 * dv[0])
+        B.isdf_fit(plan, piv)
+        k = B.isdf_get(plan, B.GET_NIP_LEVEL)
+        lo = B.isdf_get(plan, B.GET_PIVOTS)
+        off = 0
+        for lev in range(3):
+            if k[lev] == 0:
+                continue
+            xiT = B.isdf_get(plan, B.GET_XI_LEVEL0 + lev).reshape(int(k[lev]), -1)
+            g = lo[off:off + k[lev]] & ((1 << 40) - 1)
+            sub = xiT[:, g]
+            assert np.max(np.abs(sub - np.eye(int(k[lev])))) <= 1e-8
+            off += int(k[lev])
+        V = np.zeros((nip, nip))
+        B.isdf_coulomb(plan, V)
+        assert np.max(np.abs(V - V.T)) <= 1e-12 * np.max(np.abs(V))
+        sel = rng.choice(nip, size=400, replace=False)
+        ev = np.linalg.eigvalsh(V[np.ix_(sel, sel)])
+        assert ev.min() >= -1e-10 * ev.max()
+        K, Ex = B.isdf_exchange(plan, C)
+        assert np.max(np.abs(K - K.T)) <= 1e-10 * np.max(np.abs(K))
+        assert Ex < 0.0
+    finally:
+        plan.close()
