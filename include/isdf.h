@@ -208,6 +208,22 @@ const char* isdf_profile_json(isdf_plan_t plan);
  * own kernels; cuFFT's are not counted).  Host-side counter. */
 int64_t isdf_kernel_launches(void);
 
+/* FP64-accurate matrix product on the tensor cores -- the contraction
+ * kernel behind options.precision = 1, exposed for verification and reuse
+ * (the paper has no counterpart; it is this library's building block):
+ *   C[m*ldc + n] = alpha * sum_k A[m*lda + k] * B[n*ldb + k]
+ * A, B, C are DEVICE pointers (row-major FP64).  Each operand row is scaled
+ * by a power of two and split into `slices` BF16 digit planes (5 or 6, about
+ * 7 bits each); digit-pair products accumulate exactly in FP32 tensor memory
+ * per 1024-wide k chunk and are summed in double-float registers.  The error
+ * is below 2^-(7*slices-2) * K * max_k|A[m,k]| * max_k|B[n,k]| per element.
+ * splits > 1 divides K over that many CTAs (needs splits*M*N*8 bytes of
+ * scratch, allocated by the call).  Enqueued on `stream`; returns after the
+ * stream is idle.  A pipeline wait that exceeds its bound returns
+ * ISDF_ERR_TIMEOUT (no fault or trap). */
+isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
+                          int64_t ldb, int64_t ldc, double alpha, int slices, int splits, void* stream);
+
 /* Message of the last failed call on this plan (or of the last failed
  * isdf_plan when plan is NULL).  Valid until the next call. */
 const char* isdf_last_error(isdf_plan_t plan);

@@ -81,6 +81,18 @@ isdf_status dalloc(Plan* p, void** ptr, size_t bytes, const char* what) {
   return ISDF_OK;
 }
 
+isdf_status oz_check(Plan* p) {
+  int h = 0;
+  isdf_status st = cuda_check(p, cudaMemcpyAsync(&h, p->d_ozerr, sizeof(int), cudaMemcpyDeviceToHost, p->stream),
+                              "error word copy");
+  if (!st) st = cuda_check(p, cudaStreamSynchronize(p->stream), "tensor-core products");
+  if (!st && h) {
+    cudaMemsetAsync(p->d_ozerr, 0, sizeof(int), p->stream);
+    return fail(p, ISDF_ERR_TIMEOUT, "a tensor-core pipeline wait expired (code " + std::to_string(h) + ")");
+  }
+  return st;
+}
+
 void dfree(void* ptr) {
   if (ptr) cudaFree(ptr);
 }
@@ -108,7 +120,6 @@ void free_plan(Plan* p) {
     lv = Level();
   }
   dfree(p->d_diag);
-  dfree(p->d_active);
   dfree(p->d_selstate);
   dfree(p->d_piv);
   dfree(p->d_dval);
@@ -116,8 +127,9 @@ void free_plan(Plan* p) {
   dfree(p->XN);
   dfree(p->V);
   dfree(p->d_err);
+  dfree(p->d_ozerr);
+  p->d_ozerr = nullptr;
   p->d_diag = nullptr;
-  p->d_active = nullptr;
   p->d_selstate = nullptr;
   p->d_piv = nullptr;
   p->d_dval = nullptr;
@@ -199,7 +211,7 @@ isdf_status validate_options(const isdf_options* o, std::string& why) {
     why = m;
     return ISDF_ERR_ARG;
   };
-  if (o->precision != 0) return bad("precision must be 0 (plain FP64)");
+  if (o->precision != 0 && o->precision != 1) return bad("precision must be 0 or 1");
   if (!(o->tie_rel >= 0.0) || !(o->tie_abs >= 0.0) || !(o->reg_rel >= 0.0)) return bad("tolerances must be >= 0");
   if (o->col_batch < 0 || o->timeout_ms < 0) return bad("col_batch and timeout_ms must be >= 0");
   if (o->prefilter != 0 && o->prefilter != 1) return bad("prefilter must be 0 or 1");
@@ -303,6 +315,8 @@ isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* str
               "this library is built for sm_103a; device compute capability is " + std::to_string(prop.major) + "." +
                   std::to_string(prop.minor));
   if (!st) st = dalloc_t(p, &p->d_err, 1, "error word");
+  if (!st) st = dalloc_t(p, &p->d_ozerr, 1, "error word");
+  if (!st) st = cuda_check(p, cudaMemsetAsync(p->d_ozerr, 0, sizeof(int), p->stream), "memset");
   if (!st) st = basis_build(p);
   if (!st) st = cuda_check(p, cudaStreamSynchronize(p->stream), "plan");
   if (st) {
@@ -527,6 +541,50 @@ const char* isdf_profile_json(isdf_plan_t h) {
 }
 
 int64_t isdf_kernel_launches(void) { return g_launches.load(); }
+
+isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
+                          int64_t ldb, int64_t ldc, double alpha, int slices, int splits, void* stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || (slices != 5 && slices != 6) ||
+      splits < 1 || splits > 1024) {
+    g_plan_error = "invalid arguments to isdf_gemm_f64";
+    return ISDF_ERR_ARG;
+  }
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C)) {
+    g_plan_error = "isdf_gemm_f64 takes device pointers";
+    return ISDF_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  OzOperand a, b;
+  double* work = nullptr;
+  int* err = nullptr;
+  isdf_status st = oz_alloc(nullptr, a, M, K, 128, slices, "A slices");
+  if (!st) st = oz_alloc(nullptr, b, N, K, oz_bn(slices), slices, "B slices");
+  if (!st && splits > 1) st = dalloc_t(nullptr, &work, size_t(splits) * M * N, "split-K partials");
+  if (!st) st = dalloc_t(nullptr, &err, 1, "error word");
+  int herr = 0;
+  if (!st) {
+    cudaMemsetAsync(err, 0, sizeof(int), s);
+    oz_slice(A, lda, 1, nullptr, 1.0, a, s);
+    oz_slice(B, ldb, 1, nullptr, 1.0, b, s);
+    oz_gemm(a, b, C, ldc, 0, alpha, 0, 0, splits, work, err, s);
+    cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+    const cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      g_plan_error = std::string("isdf_gemm_f64: ") + cudaGetErrorString(e);
+      st = ISDF_ERR_CUDA;
+    } else if (herr) {
+      g_plan_error = "isdf_gemm_f64: tensor-core pipeline wait expired (code " + std::to_string(herr) + ")";
+      st = ISDF_ERR_TIMEOUT;
+    }
+  } else {
+    g_plan_error = "isdf_gemm_f64: allocation failed";
+  }
+  oz_free(a);
+  oz_free(b);
+  dfree(work);
+  dfree(err);
+  return st;
+}
 
 const char* isdf_last_error(isdf_plan_t h) {
   if (!h) return g_plan_error.c_str();

@@ -16,6 +16,7 @@
 //                wt_c = mult(q_x) 4 pi Omega / (|G_q|^2 N_g,fine N_g,coarse)
 // with mult = 1 for q_x in {0, nx/2}, else 2 (Hermitian partner).  Each sum is
 // one real GEMM over interleaved (Re, Im) with a per-k weight.
+#include <algorithm>
 #include <cmath>
 
 #include "internal.cuh"
@@ -99,6 +100,50 @@ __global__ void k_mirror(double* V, int64_t ld, int64_t offa, int64_t offb, int6
     V[(offa + j) * ld + offb + i] = V[(offa + i) * ld + offb + j];
   else
     V[(offb + j) * ld + offa + i] = V[(offa + i) * ld + offb + j];
+}
+
+__global__ void k_sqrt_inplace(int64_t n, double* w) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e < n) w[e] = sqrt(w[e]);
+}
+
+// V block on the tensor cores: weights split as sqrt(w) on both operands
+// (w >= 0), sliced-BF16 FP64-accurate product, split over k.
+isdf_status coulomb_block_tc(Plan* p, const double2* left, const Level& la, const Level& lb, double* wt2, bool same,
+                             double* Cblk) {
+  cudaStream_t s = p->stream;
+  const int S = 5;
+  const int64_t K2 = 2 * lb.nq;
+  k_sqrt_inplace<<<unsigned((K2 + 255) / 256), 256, 0, s>>>(K2, wt2);
+  count_launches(1);
+  OzOperand a, b;
+  double* work = nullptr;
+  isdf_status st;
+  if ((st = oz_alloc(p, a, la.k, K2, 128, S, "Coulomb slices")) ||
+      (st = oz_alloc(p, b, lb.k, K2, oz_bn(S), S, "Coulomb slices"))) {
+    oz_free(a), oz_free(b);
+    return st;
+  }
+  oz_slice(reinterpret_cast<const double*>(left), K2, 1, wt2, 1.0, a, s);
+  oz_slice(reinterpret_cast<const double*>(lb.spec), K2, 1, wt2, 1.0, b, s);
+  int64_t tiles = a.nrt * b.nrt;
+  if (same) tiles = (tiles + a.nrt) / 2;
+  int64_t splits = (4 * 152 + tiles - 1) / tiles;
+  splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::min<int64_t>(64, a.nkt / 64 + 1)));
+  if (splits > 1 && (st = dalloc_t(p, &work, size_t(splits) * la.k * lb.k, "split-k partials"))) {
+    oz_free(a), oz_free(b);
+    return st;
+  }
+  {
+    const double work_fl = same ? double(la.k) * double(la.k + 1) * double(K2) : 2.0 * la.k * double(lb.k) * K2;
+    Prof pr(p, "coulomb_V", work_fl, "flop", 0);
+    oz_gemm(a, b, Cblk, p->nip, 0, 1.0, 0, same ? 1 : 0, int(splits), work, p->d_ozerr, s);
+  }
+  st = oz_check(p);
+  oz_free(a);
+  oz_free(b);
+  dfree(work);
+  return st;
 }
 
 }  // namespace
@@ -186,7 +231,13 @@ isdf_status coulomb_run(Plan* p) {
       g.ldc = nip;
       g.kw = wt2;
       g.sym = same ? 1 : 0;
-      {
+      if (p->opt.precision == 1) {
+        if ((st = coulomb_block_tc(p, left, la, lb, wt2, same, g.C))) {
+          dfree(wt2);
+          dfree(H);
+          return st;
+        }
+      } else {
         const double K2 = 2.0 * double(lb.nq);
         const double work = same ? double(la.k) * double(la.k + 1) * K2 : 2.0 * double(la.k) * double(lb.k) * K2;
         Prof pr(p, "coulomb_V", work, "flop", 1);

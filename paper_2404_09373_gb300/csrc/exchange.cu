@@ -6,6 +6,8 @@
 //   K = [X^L X^N] W [X^L X^N]^T,
 //   W = [[V o R_GG, V o R_GL], [V o R_LG, V o R_LL]],  R_AB = Y_A Y_B^T.
 // E_x = -Tr(D K) = -sum_{mu i} C_{mu i} (K C)_{mu i}, reduced in FP64.
+#include <algorithm>
+
 #include "internal.cuh"
 
 namespace isdf {
@@ -94,6 +96,32 @@ GemmArgs gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, const double* A, 
   return g;
 }
 
+// C (M x N) = A_rows B_rows^T on the tensor cores; A given as rows x K with
+// element (r, k) at a[r*sar + k*sak], B likewise.
+isdf_status tc_product(Plan* p, const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t N,
+                       int64_t sbr, int64_t sbk, int64_t K, double* C, int64_t ldc, int sym) {
+  cudaStream_t s = p->stream;
+  const int S = 5;
+  OzOperand A, B;
+  double* work = nullptr;
+  isdf_status st;
+  if ((st = oz_alloc(p, A, M, K, 128, S, "exchange slices")) || (st = oz_alloc(p, B, N, K, oz_bn(S), S, "exchange slices")))
+    return oz_free(A), oz_free(B), st;
+  oz_slice(a, sar, sak, nullptr, 1.0, A, s);
+  oz_slice(b, sbr, sbk, nullptr, 1.0, B, s);
+  int64_t tiles = A.nrt * B.nrt;
+  int64_t splits = std::max<int64_t>(1, std::min<int64_t>((2 * 152 + tiles - 1) / tiles, A.nkt / 32 + 1));
+  splits = std::min<int64_t>(splits, 16);
+  if (splits > 1 && (st = dalloc_t(p, &work, size_t(splits) * M * N, "split-k partials")))
+    return oz_free(A), oz_free(B), st;
+  oz_gemm(A, B, C, ldc, 0, 1.0, 0, sym, int(splits), work, p->d_ozerr, s);
+  st = oz_check(p);
+  oz_free(A);
+  oz_free(B);
+  dfree(work);
+  return st;
+}
+
 }  // namespace
 
 isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* Ex) {
@@ -121,13 +149,31 @@ isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* E
   dgemm(gemm(1, 0, nip, n, N, p->XL, nip, dC, n, yl, n), s);  // Y_L = X^L^T C
   dgemm(gemm(1, 0, nip, n, N, p->XN, nip, dC, n, yn, n), s);  // Y_N = X^N^T C
   k_add<<<unsigned((nip * n + 255) / 256), 256, 0, s>>>(nip * n, yl, yn, yg);
-  dgemm(gemm(0, 1, nip, nip, n, yg, n, yg, n, rgg, nip, 1), s);
-  dgemm(gemm(0, 1, nip, nip, n, yg, n, yl, n, rgl, nip), s);
-  dgemm(gemm(0, 1, nip, nip, n, yl, n, yl, n, rll, nip, 1), s);
+  if (p->opt.precision == 1) {
+    if ((st = tc_product(p, yg, nip, n, 1, yg, nip, n, 1, n, rgg, nip, 1)) ||
+        (st = tc_product(p, yg, nip, n, 1, yl, nip, n, 1, n, rgl, nip, 0)) ||
+        (st = tc_product(p, yl, nip, n, 1, yl, nip, n, 1, n, rll, nip, 1))) {
+      cleanup();
+      return st;
+    }
+  } else {
+    dgemm(gemm(0, 1, nip, nip, n, yg, n, yg, n, rgg, nip, 1), s);
+    dgemm(gemm(0, 1, nip, nip, n, yg, n, yl, n, rgl, nip), s);
+    dgemm(gemm(0, 1, nip, nip, n, yl, n, yl, n, rll, nip, 1), s);
+  }
   k_build_w<<<unsigned((n2 * n2 + 255) / 256), 256, 0, s>>>(nip, p->V, rgg, rgl, rll, W);
   k_concat<<<unsigned((N * n2 + 255) / 256), 256, 0, s>>>(N, nip, p->XL, p->XN, x2);
-  dgemm(gemm(0, 1, n2, N, n2, W, n2, x2, n2, T, N), s);  // T = W X2^T
-  dgemm(gemm(0, 0, N, N, n2, x2, n2, T, N, dK, N), s);   // K = X2 T
+  if (p->opt.precision == 1) {
+    // T = W X2^T (rows of W against rows of X2), K = X2 T (rows of X2 against columns of T)
+    if ((st = tc_product(p, W, n2, n2, 1, x2, N, n2, 1, n2, T, N, 0)) ||
+        (st = tc_product(p, x2, N, n2, 1, T, N, 1, N, n2, dK, N, 0))) {
+      cleanup();
+      return st;
+    }
+  } else {
+    dgemm(gemm(0, 1, n2, N, n2, W, n2, x2, n2, T, N), s);  // T = W X2^T
+    dgemm(gemm(0, 0, N, N, n2, x2, n2, T, N, dK, N), s);   // K = X2 T
+  }
   dgemm(gemm(0, 0, N, n, N, dK, N, dC, n, kc, n), s);    // K C
   const int nb = 512;  // partial sums of the E_x reduction
   k_dot_partial<<<nb, 256, 0, s>>>(N * n, dC, kc, part);

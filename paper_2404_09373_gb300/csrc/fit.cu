@@ -44,6 +44,86 @@ __global__ void k_regularise(int k, double reg_rel, double* cc) {
   for (int i = threadIdx.x; i < k; i += blockDim.x) cc[int64_t(i) * k + i] += lam;
 }
 
+// zct = t1 o t2 (elementwise), both [k][ng]
+__global__ void k_hadamard(int64_t n, const double* __restrict__ t1, double* __restrict__ t2_out, double* zct) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e < n) zct[e] = t1[e] * t2_out[e];
+}
+
+__global__ void k_fill_kw(int nL, int nG, double* kw) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < nG) kw[r] = r < nL ? 1.0 : 2.0;
+}
+
+// Tensor-core form of the fit contractions (options.precision = 1): the same
+// three products as the FP64 path, each an FP64-accurate sliced-BF16 GEMM
+// with the grid points on the 128-lane side so every store is coalesced.
+isdf_status fit_products_tc(Plan* p, Level& lv, int k, const double* phiP, double* zct, double* y, const double* li,
+                            int64_t ng) {
+  cudaStream_t s = p->stream;
+  const int S = 5;
+  OzOperand aL, aG, bL, bG, az, bli;
+  double* kw = nullptr;
+  isdf_status st = ISDF_OK;
+  auto cleanup = [&]() {
+    oz_free(aL), oz_free(aG), oz_free(bL), oz_free(bG), oz_free(az), oz_free(bli);
+    dfree(kw);
+  };
+  (void)li;
+  // (ZC^T)^T = T1 o T2, T1 = A_L B_L^T, T2 = [A_L A_N] [B_L 2 B_N]^T
+  if ((st = oz_alloc(p, aL, ng, lv.nL, 128, S, "fit slices")) || (st = oz_alloc(p, bL, k, lv.nL, oz_bn(S), S, "fit slices")))
+    return cleanup(), st;
+  oz_slice(lv.phi, 1, ng, nullptr, 1.0, aL, s);
+  oz_slice(phiP, 1, k, nullptr, 1.0, bL, s);
+  {
+    Prof pr(p, "fit_zc", 2.0 * double(k) * double(ng) * double(lv.nL), "flop", 0);
+    oz_gemm(aL, bL, zct, ng, 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+  }
+  oz_free(aL);
+  oz_free(bL);
+  if (lv.nN > 0) {
+    if ((st = dalloc_t(p, &kw, size_t(lv.nG), "fit weights")) || (st = oz_alloc(p, aG, ng, lv.nG, 128, S, "fit slices")) ||
+        (st = oz_alloc(p, bG, k, lv.nG, oz_bn(S), S, "fit slices")))
+      return cleanup(), st;
+    k_fill_kw<<<unsigned((lv.nG + 255) / 256), 256, 0, s>>>(lv.nL, lv.nG, kw);
+    count_launches(1);
+    oz_slice(lv.phi, 1, ng, nullptr, 1.0, aG, s);
+    oz_slice(phiP, 1, k, kw, 1.0, bG, s);
+    Prof pr(p, "fit_zc", 2.0 * double(k) * double(ng) * double(lv.nG), "flop", 0);
+    oz_gemm(aG, bG, y, ng, 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+    oz_free(aG);
+    oz_free(bG);
+  } else {
+    cudaMemcpyAsync(y, zct, sizeof(double) * size_t(k) * ng, cudaMemcpyDeviceToDevice, s);
+  }
+  const int64_t tot = int64_t(k) * ng;
+  k_hadamard<<<unsigned((tot + 255) / 256), 256, 0, s>>>(tot, zct, y, zct);
+  count_launches(1);
+  cleanup();
+  return ISDF_OK;
+}
+
+isdf_status fit_solve_tc(Plan* p, int k, double* zct, double* y, const double* li, int64_t ng) {
+  cudaStream_t s = p->stream;
+  const int S = 5;
+  OzOperand a, b;
+  isdf_status st;
+  Prof pr(p, "fit_solve", 2.0 * double(k) * double(k + 1) * double(ng), "flop", 0);
+  // Y^T[g][j] = sum_kk Z^T[g][kk] R^-1[j][kk]   (R^-1 lower: kk <= j)
+  if ((st = oz_alloc(p, a, ng, k, 128, S, "solve slices")) || (st = oz_alloc(p, b, k, k, oz_bn(S), S, "solve slices")))
+    return oz_free(a), oz_free(b), st;
+  oz_slice(zct, 1, ng, nullptr, 1.0, a, s);
+  oz_slice(li, k, 1, nullptr, 1.0, b, s);
+  oz_gemm(a, b, y, ng, 1, 1.0, 1, 0, 1, nullptr, p->d_ozerr, s);
+  // Xi^T[j][g] = sum_kk Y[kk][g] R^-1[kk][j]   (R^-T upper: kk >= j)
+  oz_slice(y, 1, ng, nullptr, 1.0, a, s);
+  oz_slice(li, 1, k, nullptr, 1.0, b, s);
+  oz_gemm(a, b, zct, ng, 1, 1.0, 2, 0, 1, nullptr, p->d_ozerr, s);
+  oz_free(a);
+  oz_free(b);
+  return ISDF_OK;
+}
+
 }  // namespace
 
 isdf_status fit_run(Plan* p) {
@@ -76,7 +156,12 @@ isdf_status fit_run(Plan* p) {
     const int64_t np = int64_t(lv.nG) * k;
     count_launches(2 + (p->opt.reg_rel > 0.0));
     k_gather_phiP<<<unsigned((np + 255) / 256), 256, 0, s>>>(lv.nG, k, lv.phi, ng, lv.d_pg, phiP);
-    {
+    if (p->opt.precision == 1) {
+      if ((st = fit_products_tc(p, lv, k, phiP, zct, y, li, ng))) {
+        cleanup();
+        return st;
+      }
+    } else {
       Prof pr(p, "fit_zc", 2.0 * double(k) * double(ng) * double(lv.nG), "flop", 1);
       zc_gemm(k, ng, lv.nL, lv.nG, phiP, lv.phi, zct, s);
     }
@@ -106,7 +191,12 @@ isdf_status fit_run(Plan* p) {
       Prof pr(p, "fit_trtri", double(k) * k * k / 3.0, "flop", 1 + 2 * (nb - 1));
       dtrtri_lower(cc, li, k, scr, s);
     }
-    {
+    if (p->opt.precision == 1) {
+      if ((st = fit_solve_tc(p, k, zct, y, li, ng))) {
+        cleanup();
+        return st;
+      }
+    } else {
     Prof pr_solve(p, "fit_solve", 2.0 * double(k) * double(k + 1) * double(ng), "flop", 2);
     GemmArgs g1;  // Y = R^-1 ZC^T^T (R^-1 lower triangular)
     g1.M = k;
@@ -135,6 +225,7 @@ isdf_status fit_run(Plan* p) {
     dgemm(g2, s);
     }
     st = cuda_check(p, cudaStreamSynchronize(s), "fit");
+    if (!st && p->opt.precision == 1) st = oz_check(p);
     cleanup();
     if (st) return st;
   }

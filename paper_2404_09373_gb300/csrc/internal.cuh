@@ -76,7 +76,6 @@ struct Plan {
   int64_t ntot = 0;
   int64_t off[ISDF_MAX_LEVELS + 1] = {0};
   double* d_diag = nullptr;    // residual diagonal [ntot]
-  unsigned char* d_active = nullptr;
   void* d_selstate = nullptr;
   int64_t* d_piv = nullptr;    // selection-order pivot codes
   double* d_dval = nullptr;
@@ -89,6 +88,7 @@ struct Plan {
   double* XN = nullptr;
   double* V = nullptr;          // [nip][nip]
   int* d_err = nullptr;         // device error word (Cholesky breakdown etc.)
+  int* d_ozerr = nullptr;       // tensor-core pipeline error word
   std::string err;
   std::string fault;            // host fault injection (ISDF_FAULT)
   // profiling
@@ -105,6 +105,7 @@ struct Prof {
   ~Prof();
 };
 void prof_flush(Plan* p);  // resolve pending events (stream must be idle)
+isdf_status oz_check(Plan* p);  // sync; ISDF_ERR_TIMEOUT if a tensor-core wait expired
 
 // ---- helpers (api.cu) ----
 isdf_status fail(Plan* p, isdf_status s, const std::string& msg);
@@ -152,5 +153,26 @@ void zc_gemm(int64_t k, int64_t ng, int nL, int nG, const double* phiP, const do
 void dpotrf_lower(double* A, int64_t n, int64_t lda, int* err, double* scratch, cudaStream_t s);
 // inverse of a lower-triangular matrix: Li (n x n, zero-initialised by callee)
 void dtrtri_lower(const double* Lm, double* Li, int64_t n, double* scratch, cudaStream_t s);
+
+// FP64-accurate GEMM from sliced BF16 products on tcgen05 (ozgemm.cu).
+// An operand is rows x K, pre-sliced into S BF16 digit planes (S = 5 or 6)
+// and pre-tiled for the tensor cores; A operands use row tiles of 128, B
+// operands row tiles of oz_bn(S).
+struct OzOperand {
+  void* tiles = nullptr;  // __nv_bfloat16 slices
+  int* exps = nullptr;    // per-row power-of-two scale
+  int64_t rows = 0, K = 0, nrt = 0, nkt = 0;
+  int rt = 0, S = 0;
+};
+int oz_bn(int S);
+isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, int S, const char* what);
+void oz_free(OzOperand& op);
+// X(r, k) = mul * kw[k] * src[r*sr + k*sk]  (kw nullable)
+void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s);
+// C = alpha * A B^T (A: M x K as the 128-row side, B: N x K); trans: C[n*ldc+m];
+// tri 1/2: B-side lower/upper triangular in (n, k); sym: lower-triangle tiles only;
+// splits > 1 needs work of splits*M*N doubles.  Error codes go to *err.
+void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, double alpha, int tri, int sym,
+             int splits, double* work, int* err, cudaStream_t s);
 
 }  // namespace isdf

@@ -1,0 +1,533 @@
+// FP64-accurate GEMM on the tcgen05 tensor cores from sliced BF16 products.
+//
+// Every row r of an FP64 operand X (rows x K) is scaled by 2^-e_r so that
+// |x| < 1, rounded to a fixed-point integer with 7S fraction bits and split
+// into S balanced base-128 digits d_0..d_{S-1} (|d_0| <= 128, |d_s| <= 64),
+// each exactly representable in BF16:
+//     x 2^-e_r = sum_s d_s 2^{-7(s+1)} + O(2^{-7S-1}).
+// A product keeps the digit pairs s + t <= S - 1 ("levels" q = s + t):
+//     (A B^T)_mn = 2^{e_m + f_n - 14} sum_q 2^{-7q} L_q,  L_q = sum_k sum_{s+t=q} d_s b_t.
+// Each level has its own FP32 accumulator in tensor memory.  Digit products
+// are integers below 2^14, so levels 0 and 1 summed over a chunk of 1024 k
+// values stay below 2^24 and are exact in FP32; deeper levels are scaled by
+// 2^-14 or less, where FP32 rounding is harmless.  After every chunk the
+// epilogue warps read the levels out (tcgen05.ld) and add them to double-float
+// (hi, lo) register accumulators; the result is formed in FP64 at the end.
+//
+// Operands are pre-tiled by the slicing kernel into the canonical K-major,
+// no-swizzle UMMA layout (8x8 core matrices, LBO = 128 B along K, SBO =
+// 512 B per 8-row group, 32 k values per tile), all S slices of one
+// (row tile, k tile) contiguous, so one cp.async.bulk per operand fills a
+// pipeline stage.  Roles per CTA: warp 0 issues the bulk copies, warp 1 owns
+// tensor memory and issues tcgen05.mma, warps 2-9 drain the accumulators.
+// Every mbarrier wait is bounded: on expiry the CTA records an error code,
+// lets its copies and MMAs in flight finish, frees tensor memory and exits.
+#include <cuda_bf16.h>
+
+#include "internal.cuh"
+
+namespace isdf {
+namespace {
+
+constexpr int kBM = 128;  // A rows per CTA = TMEM lanes
+constexpr int kBK = 32;   // k values per tile / pipeline stage
+constexpr int kKcTiles = 32;  // 1024 k values per exact chunk
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr long long kWaitLimit = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
+  // K-major, no swizzle: LBO = 128 B (next core matrix along K), SBO = 512 B
+  // (next 8-row group), descriptor version 1 (bits 46-47), layout type 0.
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)(128 >> 4) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// kind::f16 instruction descriptor: D F32, A/B BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t umma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  const uint32_t addr = smem_u32(bar);
+  for (long long i = 0; i < kWaitLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+          dtmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
+
+// ---------------------------------------------------------------- slicing
+
+// e_r: max_k |x(r,k)| < 2^e_r, x = mul * kw[k] * src[r*sr + k*sk]; one thread per row
+__global__ void k_oz_rowexp_thread(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t rows, int64_t K,
+                                   const double* __restrict__ kw, double mul, int* __restrict__ exps) {
+  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (r >= rows) return;
+  double m = 0.0;
+  for (int64_t k = 0; k < K; ++k) {
+    double v = src[r * sr + k * sk] * mul;
+    if (kw) v *= kw[k];
+    m = fmax(m, fabs(v));
+  }
+  int e = 0;
+  if (m > 0.0) frexp(m, &e);
+  exps[r] = e;
+}
+
+// same, one block per row (long rows with unit k stride)
+__global__ void k_oz_rowexp_block(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t K,
+                                  const double* __restrict__ kw, double mul, int* __restrict__ exps) {
+  __shared__ double sh[256];
+  const int64_t r = blockIdx.x;
+  double m = 0.0;
+  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
+    double v = src[r * sr + k * sk] * mul;
+    if (kw) v *= kw[k];
+    m = fmax(m, fabs(v));
+  }
+  sh[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    int e = 0;
+    if (sh[0] > 0.0) frexp(sh[0], &e);
+    exps[r] = e;
+  }
+}
+
+// Digits of one row and one group of 8 k values, written as 16 bytes per slice.
+// order 0: consecutive threads take consecutive rows; 1: consecutive k groups.
+__global__ void k_oz_digits(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t rows, int64_t K,
+                            const double* __restrict__ kw, double mul, const int* __restrict__ exps, int S, int rt,
+                            int64_t nrt, int64_t nkt, int order, __nv_bfloat16* __restrict__ tiles) {
+  const int64_t rows_pad = nrt * rt, ngrp = nkt * (kBK / 8);
+  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= rows_pad * ngrp) return;
+  int64_t r, kg;
+  if (order == 0) {
+    r = idx % rows_pad;
+    kg = idx / rows_pad;
+  } else {
+    kg = idx % ngrp;
+    r = idx / ngrp;
+  }
+  long long X[8];
+  const int e = (r < rows) ? exps[r] : 0;
+  const int shift = 7 * S - e;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    const int64_t k = kg * 8 + u;
+    double v = 0.0;
+    if (r < rows && k < K) {
+      v = src[r * sr + k * sk] * mul;
+      if (kw) v *= kw[k];
+    }
+    X[u] = llrint(ldexp(v, shift));
+  }
+  const int64_t it = r / rt, rr = r % rt, jt = kg / (kBK / 8), kc = kg % (kBK / 8);
+  const int64_t tile_elems = int64_t(rt) * kBK;
+  __nv_bfloat16* base = tiles + ((it * nkt + jt) * S) * tile_elems;
+  const int64_t inner = ((rr / 8) * 512 + kc * 128 + (rr % 8) * 16) / 2;  // element offset in a tile
+  // digits from the least significant end (balanced, in [-64, 63]); top digit last
+  for (int s = S - 1; s >= 0; --s) {
+    __align__(16) __nv_bfloat16 d[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      long long dig;
+      if (s > 0) {
+        dig = ((X[u] + 64) & 127) - 64;
+        X[u] = (X[u] - dig) >> 7;
+      } else {
+        dig = X[u];
+      }
+      d[u] = __float2bfloat16_rn(float(dig));
+    }
+    *reinterpret_cast<uint4*>(base + int64_t(s) * tile_elems + inner) = *reinterpret_cast<const uint4*>(d);
+  }
+}
+
+// ---------------------------------------------------------------- GEMM
+
+struct OzGemmParams {
+  const __nv_bfloat16* A;
+  const __nv_bfloat16* B;
+  const int* ea;
+  const int* eb;
+  int64_t M, N, nkt;
+  int tri;     // 0 dense; 1 B-side lower (k <= n); 2 B-side upper (k >= n)
+  int sym;     // compute only tiles that touch the lower triangle (n <= m)
+  int splits;  // split-K factor (gridDim.z)
+  double* C;
+  int64_t ldc;
+  int trans;   // 1: C[n*ldc + m], 0: C[m*ldc + n]
+  double alpha;
+  double* work;  // split-K partials [z][M][N]
+  int* err;
+};
+
+template <int S, int BN>
+struct OzCfg {
+  static constexpr int tileA = kBM * kBK * 2;  // bytes per slice tile
+  static constexpr int tileB = BN * kBK * 2;
+  static constexpr int stageA = S * tileA;
+  static constexpr int stageB = S * tileB;
+  static constexpr int stage = stageA + stageB;
+  static constexpr int budget = 220 * 1024 - 2048;
+  static constexpr int nst = budget / stage < 4 ? budget / stage : 4;
+  static constexpr int smem = nst * stage + 2048;  // + barriers and 1024-byte alignment slack
+  static constexpr int cols = S * BN;
+  static constexpr uint32_t tcols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+  static_assert(cols <= 512, "levels x BN must fit in tensor memory");
+  static_assert(nst >= 2, "need at least two pipeline stages");
+  static_assert(BN % 32 == 0, "BN must split into two halves of x16 loads");
+  static_assert(smem <= 232448, "shared memory per CTA");
+};
+
+template <int S, int BN>
+__global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
+  using Cfg = OzCfg<S, BN>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::nst * Cfg::stage);
+  uint64_t* empty = full + Cfg::nst;
+  uint64_t* acc_full = empty + Cfg::nst;
+  uint64_t* acc_empty = acc_full + 1;
+  uint64_t* drain = acc_empty + 1;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int64_t nt = blockIdx.x, mt = blockIdx.y;  // N tiles vary fastest: CTAs in flight share A
+  const int64_t m0 = mt * kBM, n0 = nt * BN;
+  if (P.sym && n0 > m0 + kBM - 1) return;  // tile entirely above the diagonal
+
+  // k-tile range of this CTA
+  int64_t kt_lo = 0, kt_hi = P.nkt;
+  if (P.tri == 1) kt_hi = min(P.nkt, (n0 + BN + kBK - 1) / kBK);
+  if (P.tri == 2) kt_lo = min(P.nkt, n0 / kBK);
+  {
+    const int64_t tot = kt_hi - kt_lo, per = (tot + P.splits - 1) / P.splits;
+    const int64_t a = kt_lo + per * blockIdx.z;
+    kt_lo = min(kt_hi, a);
+    kt_hi = min(kt_hi, a + per);
+  }
+  const int64_t nk = kt_hi - kt_lo;
+  const int64_t nchunks = (nk + kKcTiles - 1) / kKcTiles;
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < Cfg::nst; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&empty[i], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(acc_empty, kEpiWarps);
+    mbar_init(drain, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(Cfg::tcols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------ producer
+    if (lane == 0) {
+      const unsigned char* gA = reinterpret_cast<const unsigned char*>(P.A);
+      const unsigned char* gB = reinterpret_cast<const unsigned char*>(P.B);
+      int64_t issued = 0;
+      for (int64_t it = 0; it < nk; ++it) {
+        const int st = int(it % Cfg::nst);
+        const int64_t round = it / Cfg::nst;
+        if (round > 0 && !mbar_wait(&empty[st], uint32_t((round - 1) & 1))) {
+          set_err(P.err, 11);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        const int64_t kt = kt_lo + it;
+        unsigned char* sA = smem + st * Cfg::stage;
+        unsigned char* sB = sA + Cfg::stageA;
+        mbar_expect_tx(&full[st], Cfg::stageA + Cfg::stageB);
+        bulk_g2s(sA, gA + (mt * P.nkt + kt) * int64_t(Cfg::stageA), Cfg::stageA, &full[st]);
+        bulk_g2s(sB, gB + (nt * P.nkt + kt) * int64_t(Cfg::stageB), Cfg::stageB, &full[st]);
+        issued = it + 1;
+      }
+      // copies that were issued but never consumed must land before exit
+      if (*(volatile int*)abort_flag) {
+        const int64_t first = issued > Cfg::nst ? issued - Cfg::nst : 0;
+        for (int64_t it = first; it < issued; ++it) mbar_wait(&full[it % Cfg::nst], uint32_t((it / Cfg::nst) & 1));
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = umma_idesc(kBM, BN);
+      for (int64_t it = 0; it < nk; ++it) {
+        const int st = int(it % Cfg::nst);
+        const int64_t round = it / Cfg::nst;
+        const int64_t cpos = it % kKcTiles, chunk = it / kKcTiles;
+        if (cpos == 0 && chunk > 0 && !mbar_wait(acc_empty, uint32_t((chunk - 1) & 1))) {
+          set_err(P.err, 12);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (!mbar_wait(&full[st], uint32_t(round & 1))) {
+          set_err(P.err, 13);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        if (*(volatile int*)abort_flag) break;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t sA = smem_u32(smem + st * Cfg::stage);
+        const uint32_t sB = sA + Cfg::stageA;
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+#pragma unroll
+          for (int s = 0; s <= q; ++s) {
+            const int t = q - s;
+#pragma unroll
+            for (int ks = 0; ks < kBK / 16; ++ks) {
+              const uint64_t da = umma_desc(sA + s * Cfg::tileA + ks * 256);
+              const uint64_t db = umma_desc(sB + t * Cfg::tileB + ks * 256);
+              const uint32_t acc = (cpos > 0 || s > 0 || ks > 0) ? 1u : 0u;
+              umma_bf16(tmem + uint32_t(q * BN), da, db, idesc, acc);
+            }
+          }
+        }
+        umma_commit(&empty[st]);
+        if (cpos == kKcTiles - 1 || it == nk - 1) umma_commit(acc_full);
+      }
+      // all MMAs issued by this thread complete before tensor memory is freed
+      umma_commit(drain);
+      mbar_wait(drain, 0);
+    }
+  } else {
+    // ------------------------------------------------ epilogue (8 warps)
+    const int quarter = warp % 4;
+    const int half = (warp - 2) / 4;
+    const int row = quarter * 32 + lane;
+    constexpr int HC = BN / 2;  // columns per thread
+    float hi[HC], lo[HC];
+#pragma unroll
+    for (int j = 0; j < HC; ++j) hi[j] = lo[j] = 0.0f;
+    for (int64_t c = 0; c < nchunks; ++c) {
+      if (!mbar_wait(acc_full, uint32_t(c & 1))) {
+        set_err(P.err, 14);
+        *(volatile int*)abort_flag = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+      for (int q = 0; q < S; ++q) {
+        const float scale = __int_as_float((127 - 7 * q) << 23);  // 2^{-7q}
+#pragma unroll
+        for (int c0 = 0; c0 < HC; c0 += 16) {
+          uint32_t r[16];
+          tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(q * BN + half * HC + c0), r);
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float x = __uint_as_float(r[j]) * scale;
+            const float s = hi[c0 + j] + x;
+            const float bb = s - hi[c0 + j];
+            const float e = (hi[c0 + j] - (s - bb)) + (x - bb);
+            hi[c0 + j] = s;
+            lo[c0 + j] += e;
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acc_empty);
+    }
+    const int64_t m = m0 + row;
+    if (m < P.M && !*(volatile int*)abort_flag) {
+      const int ea = P.ea[m];
+#pragma unroll
+      for (int j = 0; j < HC; ++j) {
+        const int64_t n = n0 + half * HC + j;
+        if (n >= P.N) continue;
+        const double v = ldexp(double(hi[j]) + double(lo[j]), ea + P.eb[n] - 14) * P.alpha;
+        if (P.splits > 1)
+          P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
+        else if (P.trans)
+          P.C[n * P.ldc + m] = v;
+        else
+          P.C[m * P.ldc + n] = v;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(Cfg::tcols));
+  }
+}
+
+// C = sum_z work[z] (deterministic order), same store modes as the GEMM
+__global__ void k_oz_reduce(const double* __restrict__ work, int splits, int64_t M, int64_t N, double* __restrict__ C,
+                            int64_t ldc, int trans, int sym) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= M * N) return;
+  const int64_t m = e / N, n = e % N;
+  if (sym && n > m) return;
+  double s = 0.0;
+  for (int z = 0; z < splits; ++z) s += work[int64_t(z) * M * N + e];
+  if (trans)
+    C[n * ldc + m] = s;
+  else
+    C[m * ldc + n] = s;
+}
+
+template <int S, int BN>
+void launch_oz(const OzGemmParams& P, dim3 grid, cudaStream_t s) {
+  using Cfg = OzCfg<S, BN>;
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::smem);
+    configured = true;
+  }
+  k_oz_gemm<S, BN><<<grid, kThreads, Cfg::smem, s>>>(P);
+}
+
+}  // namespace
+
+int64_t oz_tile_elems(int64_t rows, int64_t K, int rt, int S) {
+  const int64_t nrt = (rows + rt - 1) / rt, nkt = (K + kBK - 1) / kBK;
+  return nrt * nkt * S * int64_t(rt) * kBK;
+}
+
+isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, int S, const char* what) {
+  op.rows = rows;
+  op.K = K;
+  op.tiles = nullptr;
+  op.exps = nullptr;
+  op.rt = rt;
+  op.S = S;
+  op.nrt = (rows + rt - 1) / rt;
+  op.nkt = (K + kBK - 1) / kBK;
+  isdf_status st = dalloc(p, &op.tiles, size_t(oz_tile_elems(rows, K, rt, S)) * 2, what);
+  if (st) return st;
+  return dalloc_t(p, &op.exps, size_t(op.nrt * rt), what);
+}
+
+void oz_free(OzOperand& op) {
+  dfree(op.tiles);
+  dfree(op.exps);
+  op.tiles = nullptr;
+  op.exps = nullptr;
+}
+
+void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s) {
+  const bool rowwise = sr >= sk;  // k contiguous: one block per row
+  if (rowwise && op.K >= 4096) {
+    k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, sr, sk, op.K, kw, mul, op.exps);
+  } else {
+    k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, kw, mul, op.exps);
+  }
+  const int64_t total = op.nrt * op.rt * op.nkt * (kBK / 8);
+  k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, kw, mul, op.exps, op.S, op.rt,
+                                                             op.nrt, op.nkt, rowwise ? 1 : 0,
+                                                             static_cast<__nv_bfloat16*>(op.tiles));
+  count_launches(2);
+}
+
+int oz_bn(int S) { return S == 5 ? 96 : 64; }
+
+void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, double alpha, int tri, int sym,
+             int splits, double* work, int* err, cudaStream_t s) {
+  OzGemmParams P;
+  P.A = static_cast<const __nv_bfloat16*>(A.tiles);
+  P.B = static_cast<const __nv_bfloat16*>(B.tiles);
+  P.ea = A.exps;
+  P.eb = B.exps;
+  P.M = A.rows;
+  P.N = B.rows;
+  P.nkt = A.nkt;
+  P.tri = tri;
+  P.sym = sym;
+  P.splits = splits < 1 ? 1 : splits;
+  P.C = C;
+  P.ldc = ldc;
+  P.trans = trans;
+  P.alpha = alpha;
+  P.work = work;
+  P.err = err;
+  dim3 grid(unsigned(B.nrt), unsigned(A.nrt), unsigned(P.splits));
+  if (A.S == 5)
+    launch_oz<5, 96>(P, grid, s);
+  else
+    launch_oz<6, 64>(P, grid, s);
+  count_launches(1);
+  if (P.splits > 1) {
+    const int64_t tot = A.rows * B.rows;
+    k_oz_reduce<<<unsigned((tot + 255) / 256), 256, 0, s>>>(work, P.splits, A.rows, B.rows, C, ldc, trans, sym);
+    count_launches(1);
+  }
+}
+
+}  // namespace isdf

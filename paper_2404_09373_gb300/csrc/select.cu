@@ -12,7 +12,17 @@
 //                d(g) -= L[g,k]^2,  L[p,k] = sqrt(d_p), d(p) = 0
 // Steps are captured once into a CUDA graph and replayed.  No kernel waits on
 // another; there is no spin anywhere.
+//
+// Candidates.  Every level works on a compacted, ascending list of candidate
+// grid points (all points, a caller-given list, or the exact prefilter), so
+// the factor columns, the residual and every step scale with the number of
+// candidates.  Exact prefilter: a point whose initial residual is below tau
+// can never be picked while every pivot value stays above tau plus the tie
+// margin, because residuals only shrink; the host checks that certificate on
+// the returned pivot values and otherwise repeats with a lower tau.
+#include <algorithm>
 #include <climits>
+#include <cstring>
 
 #include "internal.cuh"
 
@@ -24,7 +34,8 @@ struct SelState {
   unsigned long long first;
   double d0;
   double dp;
-  long long gp;
+  long long gp;  // grid index of this step's pivot
+  long long tp;  // its position in the level's candidate list
   int lev;
   int col;
   int k;
@@ -36,12 +47,13 @@ struct SelState {
 };
 
 struct SelParams {
-  double* d;
-  const unsigned char* active;
+  double* d;  // residual over all levels' candidates (concatenated)
   int64_t ntot;
   int nlev;
-  int64_t off[ISDF_MAX_LEVELS + 1];
-  double* fac[ISDF_MAX_LEVELS];
+  int64_t coff[ISDF_MAX_LEVELS + 1];  // candidate offsets per level
+  const int* cidx[ISDF_MAX_LEVELS];   // candidate grid indices (nullptr: all points)
+  int64_t nc[ISDF_MAX_LEVELS];
+  double* fac[ISDF_MAX_LEVELS];       // factor columns [col][nc]
   const double* phi[ISDF_MAX_LEVELS];
   int64_t ng[ISDF_MAX_LEVELS];
   int nL[ISDF_MAX_LEVELS];
@@ -81,9 +93,9 @@ struct MinOp {
   __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a < b ? a : b; }
 };
 
-// w_l M_l(g, g) = w (aL^2 + 2 aL aN), aX = sum_{mu in X} phi_mu(g)^2
+// w_l M_l(g, g) = w (aL^2 + 2 aL aN), aX = sum_{mu in X} phi_mu(g)^2, every grid point
 __global__ void k_sel_diag(const double* __restrict__ phi, int64_t ng, int nL, int nG, double w,
-                           const unsigned char* __restrict__ act, double* __restrict__ d) {
+                           double* __restrict__ d) {
   for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
     double aL = 0.0, aN = 0.0;
     for (int r = 0; r < nL; ++r) {
@@ -94,9 +106,62 @@ __global__ void k_sel_diag(const double* __restrict__ phi, int64_t ng, int nL, i
       const double v = phi[int64_t(r) * ng + g];
       aN = fma(v, v, aN);
     }
-    const double m = w * (aL * (aL + 2.0 * aN));
-    d[g] = (act && !act[g]) ? 0.0 : m;
+    d[g] = w * (aL * (aL + 2.0 * aN));
   }
+}
+
+// max of a vector into a scalar slot (slot preset to 0; values >= 0 compare as bits)
+__global__ void k_vec_max(const double* __restrict__ v, int64_t n, unsigned long long* out) {
+  __shared__ double sh[32];
+  double m = 0.0;
+  for (int64_t i = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x)
+    m = fmax(m, v[i]);
+  m = block_reduce(m, MaxOp(), sh);
+  if (threadIdx.x == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+// ordered compaction of {g : d0[g] >= tau}: per-block counts, then scatter
+constexpr int kCompactBlock = 1024;
+__global__ void k_flag_count(const double* __restrict__ d0, int64_t ng, double tau, int* __restrict__ counts) {
+  __shared__ int sh[32];
+  const int64_t g = int64_t(blockIdx.x) * kCompactBlock + threadIdx.x;
+  const int f = (g < ng && d0[g] >= tau) ? 1 : 0;
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int i = 0; i < kCompactBlock / 32; ++i) c += sh[i];
+    counts[blockIdx.x] = c;
+  }
+}
+
+__global__ void k_compact(const double* __restrict__ d0, int64_t ng, double tau, const int* __restrict__ block_off,
+                          int* __restrict__ cidx) {
+  __shared__ int warp_off[32];
+  const int64_t g = int64_t(blockIdx.x) * kCompactBlock + threadIdx.x;
+  const int f = (g < ng && d0[g] >= tau) ? 1 : 0;
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) warp_off[wid] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int acc = 0;
+    for (int i = 0; i < kCompactBlock / 32; ++i) {
+      const int c = warp_off[i];
+      warp_off[i] = acc;
+      acc += c;
+    }
+  }
+  __syncthreads();
+  if (f) cidx[block_off[blockIdx.x] + warp_off[wid] + __popc(b & ((1u << lane) - 1u))] = int(g);
+}
+
+// residual over the candidates of one level
+__global__ void k_gather_diag(const double* __restrict__ d0, const int* __restrict__ cidx, int64_t nc,
+                              double* __restrict__ d) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < nc) d[t] = d0[cidx ? cidx[t] : t];
 }
 
 __global__ void k_sel_max(SelParams P, SelState* st) {
@@ -145,13 +210,15 @@ __global__ void k_sel_pick(SelParams P, SelState* st) {
     return;
   }
   int l = 0;
-  while (l + 1 < P.nlev && (long long)idx >= P.off[l + 1]) ++l;
-  const long long g = (long long)idx - P.off[l];
+  while (l + 1 < P.nlev && (long long)idx >= P.coff[l + 1]) ++l;
+  const long long t = (long long)idx - P.coff[l];
+  const long long g = P.cidx[l] ? P.cidx[l][t] : t;
   const double dp = P.d[idx];
   const int k = st->k;
   if (k == 0) st->d0 = __longlong_as_double((long long)st->dmax_bits);
   st->lev = l;
   st->gp = g;
+  st->tp = t;
   st->dp = dp;
   st->col = st->kl[l];
   P.piv[k] = ((long long)l << kPivShift) | g;
@@ -176,87 +243,64 @@ __global__ __launch_bounds__(256) void k_sel_col(SelParams P, const SelState* st
   if (st->skip) return;
   extern __shared__ double cp[];  // phi_G(p)
   const int l = st->lev;
-  const int64_t gp = st->gp;
+  const int64_t gp = st->gp, tp = st->tp;
   const int col = st->col;
   const double dp = st->dp;
-  const int64_t ng = P.ng[l];
+  const int64_t ng = P.ng[l], nc = P.nc[l];
   const int nL = P.nL[l], nG = P.nG[l];
+  const int* __restrict__ cidx = P.cidx[l];
   const double* __restrict__ phi = P.phi[l];
   double* __restrict__ fac = P.fac[l];
-  double* __restrict__ d = P.d + P.off[l];
-  const unsigned char* act = P.active ? P.active + P.off[l] : nullptr;
+  double* __restrict__ d = P.d + P.coff[l];
   for (int r = threadIdx.x; r < nG; r += blockDim.x) cp[r] = phi[int64_t(r) * ng + gp];
   __syncthreads();
   const double sq = sqrt(dp);
   const double w = P.w[l];
-  for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nc; t += int64_t(gridDim.x) * blockDim.x) {
+    const int64_t g = cidx ? cidx[t] : t;
     double aL = 0.0, aN = 0.0;
     for (int r = 0; r < nL; ++r) aL = fma(phi[int64_t(r) * ng + g], cp[r], aL);
     for (int r = nL; r < nG; ++r) aN = fma(phi[int64_t(r) * ng + g], cp[r], aN);
     const double m = w * (aL * (aL + 2.0 * aN));
     double s = 0.0;
-    for (int j = 0; j < col; ++j) s = fma(fac[int64_t(j) * ng + g], __ldg(&fac[int64_t(j) * ng + gp]), s);
+    for (int j = 0; j < col; ++j) s = fma(fac[int64_t(j) * nc + t], __ldg(&fac[int64_t(j) * nc + tp]), s);
     double v = (m - s) / sq;
-    const bool inactive = act && !act[g];
-    if (g == gp) v = sq;
-    if (inactive) v = 0.0;
-    fac[int64_t(col) * ng + g] = v;
-    if (g == gp)
-      d[g] = 0.0;
-    else if (!inactive)
-      d[g] = d[g] - v * v;
+    if (t == tp) v = sq;
+    fac[int64_t(col) * nc + t] = v;
+    d[t] = (t == tp) ? 0.0 : d[t] - v * v;
   }
 }
 
 }  // namespace
 
-isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>* cand, int* nfound) {
+namespace {
+
+// One greedy run over the given candidates (cidx[l] == nullptr: all points).
+isdf_status select_loop(Plan* p, int nip, double tol, const double* d0full, int* const* cidx, const int64_t* nc,
+                        int* nfound, int* kl_out) {
   cudaStream_t s = p->stream;
   isdf_status st;
-  // (re)allocate selection buffers
+  SelParams P{};
+  P.nlev = p->nlev;
+  P.coff[0] = 0;
+  int nGmax = 1;
+  for (int l = 0; l < p->nlev; ++l) {
+    P.coff[l + 1] = P.coff[l] + nc[l];
+    P.cidx[l] = cidx[l];
+    P.nc[l] = nc[l];
+  }
+  P.ntot = P.coff[p->nlev];
   dfree(p->d_diag);
   p->d_diag = nullptr;
-  dfree(p->d_active);
-  p->d_active = nullptr;
-  dfree(p->d_piv);
-  p->d_piv = nullptr;
-  dfree(p->d_dval);
-  p->d_dval = nullptr;
-  if (!p->d_selstate) {
-    st = dalloc(p, &p->d_selstate, sizeof(SelState), "selection state");
-    if (st) return st;
-  }
-  if ((st = dalloc_t(p, &p->d_diag, size_t(p->ntot), "residual diagonal"))) return st;
-  if ((st = dalloc_t(p, &p->d_piv, size_t(nip), "pivots"))) return st;
-  if ((st = dalloc_t(p, &p->d_dval, size_t(nip), "pivot values"))) return st;
-  if (cand) {
-    std::vector<unsigned char> act(size_t(p->ntot), 0);
-    for (int64_t c : *cand) {
-      const int l = int(c >> kPivShift);
-      const int64_t g = c & kPivMask;
-      act[size_t(p->off[l] + g)] = 1;
-    }
-    if ((st = dalloc_t(p, &p->d_active, size_t(p->ntot), "candidate mask"))) return st;
-    if ((st = cuda_check(p, cudaMemcpyAsync(p->d_active, act.data(), act.size(), cudaMemcpyHostToDevice, s), "copy")))
-      return st;
-    if ((st = cuda_check(p, cudaStreamSynchronize(s), "copy candidates"))) return st;
-  }
+  if ((st = dalloc_t(p, &p->d_diag, size_t(std::max<int64_t>(P.ntot, 1)), "residual diagonal"))) return st;
+  P.d = p->d_diag;
   for (int l = 0; l < p->nlev; ++l) {
     Level& lv = p->lev[l];
     dfree(lv.fac);
     lv.fac = nullptr;
-    lv.fac_cap = std::min<int64_t>(nip, lv.ng);
-    if ((st = dalloc_t(p, &lv.fac, size_t(lv.fac_cap) * size_t(lv.ng), "selection factor columns"))) return st;
-  }
-  SelParams P{};
-  P.d = p->d_diag;
-  P.active = p->d_active;
-  P.ntot = p->ntot;
-  P.nlev = p->nlev;
-  for (int l = 0; l <= p->nlev; ++l) P.off[l] = p->off[l];
-  int nGmax = 1;
-  for (int l = 0; l < p->nlev; ++l) {
-    Level& lv = p->lev[l];
+    lv.fac_cap = std::min<int64_t>(nip, nc[l]);
+    if ((st = dalloc_t(p, &lv.fac, size_t(std::max<int64_t>(lv.fac_cap * nc[l], 1)), "selection factor columns")))
+      return st;
     P.fac[l] = lv.fac;
     P.phi[l] = lv.phi;
     P.ng[l] = lv.ng;
@@ -264,9 +308,11 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     P.nG[l] = lv.nG;
     P.w[l] = lv.w;
     nGmax = std::max(nGmax, lv.nG);
-    Prof pr(p, "select_diag", 2.0 * double(lv.nG) * double(lv.ng), "flop", 1);
-    k_sel_diag<<<152 * 8, 256, 0, s>>>(lv.phi, lv.ng, lv.nL, lv.nG, lv.w,
-                                       p->d_active ? p->d_active + p->off[l] : nullptr, p->d_diag + p->off[l]);
+    if (nc[l]) {
+      k_gather_diag<<<unsigned((nc[l] + 255) / 256), 256, 0, s>>>(d0full + p->off[l], cidx[l], nc[l],
+                                                                  p->d_diag + P.coff[l]);
+      count_launches(1);
+    }
   }
   P.piv = p->d_piv;
   P.dval = p->d_dval;
@@ -327,23 +373,150 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     return st;
   if ((st = cuda_check(p, cudaStreamSynchronize(s), "selection"))) return st;
   *nfound = h.k;
+  for (int l = 0; l < p->nlev; ++l) kl_out[l] = h.kl[l];
   if (p->opt.profile && !p->pend.empty() && p->pend.back().name == "select_loop") {
-    // algorithmic flops: step c on level l costs 2 (nG + c) ng (M column and
-    // the factor-row dot product)
+    // algorithmic flops: step c on level l costs 2 (nG + c) n_cand (M column
+    // and the factor-row dot product)
     double work = 0.0;
     for (int l = 0; l < p->nlev; ++l) {
-      const double k = h.kl[l], ng = double(p->lev[l].ng), nG = p->lev[l].nG;
-      work += 2.0 * ng * (nG * k + 0.5 * k * (k - 1.0));
+      const double k = h.kl[l], n = double(nc[l]), nG = p->lev[l].nG;
+      work += 2.0 * n * (nG * k + 0.5 * k * (k - 1.0));
     }
     p->pend.back().work = work;
   }
-  // the factor columns are not needed after selection
-  for (int l = 0; l < p->nlev; ++l) {
+  for (int l = 0; l < p->nlev; ++l) {  // factor columns are not needed after selection
     dfree(p->lev[l].fac);
     p->lev[l].fac = nullptr;
   }
   if (h.err == ISDF_ERR_TIMEOUT) return fail(p, ISDF_ERR_TIMEOUT, "selection loop exceeded options.timeout_ms");
   return ISDF_OK;
+}
+
+}  // namespace
+
+isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>* cand, int* nfound) {
+  cudaStream_t s = p->stream;
+  isdf_status st;
+  dfree(p->d_piv);
+  p->d_piv = nullptr;
+  dfree(p->d_dval);
+  p->d_dval = nullptr;
+  if (!p->d_selstate && (st = dalloc(p, &p->d_selstate, sizeof(SelState), "selection state"))) return st;
+  if ((st = dalloc_t(p, &p->d_piv, size_t(nip), "pivots"))) return st;
+  if ((st = dalloc_t(p, &p->d_dval, size_t(nip), "pivot values"))) return st;
+  // initial residual diagonal on every point of every level
+  double* d0 = nullptr;
+  if ((st = dalloc_t(p, &d0, size_t(p->ntot), "initial diagonal"))) return st;
+  for (int l = 0; l < p->nlev; ++l) {
+    Level& lv = p->lev[l];
+    Prof pr(p, "select_diag", 2.0 * double(lv.nG) * double(lv.ng), "flop", 1);
+    k_sel_diag<<<152 * 8, 256, 0, s>>>(lv.phi, lv.ng, lv.nL, lv.nG, lv.w, d0 + p->off[l]);
+  }
+  int* cidx[ISDF_MAX_LEVELS] = {nullptr, nullptr, nullptr, nullptr};
+  int64_t nc[ISDF_MAX_LEVELS] = {0, 0, 0, 0};
+  auto free_cidx = [&]() {
+    for (int l = 0; l < p->nlev; ++l) {
+      dfree(cidx[l]);
+      cidx[l] = nullptr;
+    }
+  };
+  auto done = [&](isdf_status r) {
+    free_cidx();
+    dfree(d0);
+    return r;
+  };
+  int kl[ISDF_MAX_LEVELS];
+  if (cand) {
+    // caller-given candidates: ascending, unique per level
+    std::vector<std::vector<int>> per(p->nlev);
+    for (int64_t c : *cand) per[c >> kPivShift].push_back(int(c & kPivMask));
+    for (int l = 0; l < p->nlev; ++l) {
+      std::sort(per[l].begin(), per[l].end());
+      per[l].erase(std::unique(per[l].begin(), per[l].end()), per[l].end());
+      nc[l] = int64_t(per[l].size());
+      if (!nc[l]) continue;
+      if ((st = dalloc_t(p, &cidx[l], size_t(nc[l]), "candidates"))) return done(st);
+      if ((st = cuda_check(p, cudaMemcpyAsync(cidx[l], per[l].data(), sizeof(int) * nc[l], cudaMemcpyHostToDevice, s),
+                           "copy candidates")))
+        return done(st);
+    }
+    if ((st = cuda_check(p, cudaStreamSynchronize(s), "copy candidates"))) return done(st);
+    return done(select_loop(p, nip, tol, d0, cidx, nc, nfound, kl));
+  }
+  if (!p->opt.prefilter) {
+    for (int l = 0; l < p->nlev; ++l) nc[l] = p->lev[l].ng;
+    return done(select_loop(p, nip, tol, d0, cidx, nc, nfound, kl));
+  }
+  // exact prefilter: tau relative to the largest initial residual d_0
+  unsigned long long* dmax_slot = nullptr;
+  if ((st = dalloc_t(p, &dmax_slot, 1, "max slot"))) return done(st);
+  cudaMemsetAsync(dmax_slot, 0, sizeof(unsigned long long), s);
+  k_vec_max<<<152 * 4, 256, 0, s>>>(d0, p->ntot, dmax_slot);
+  count_launches(1);
+  unsigned long long bits = 0;
+  cudaMemcpyAsync(&bits, dmax_slot, sizeof(bits), cudaMemcpyDeviceToHost, s);
+  st = cuda_check(p, cudaStreamSynchronize(s), "prefilter max");
+  dfree(dmax_slot);
+  if (st) return done(st);
+  double dmax0;
+  std::memcpy(&dmax0, &bits, sizeof(dmax0));
+  const double taus[3] = {1e-6, 1e-9, 0.0};
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    const double tau = taus[attempt] * dmax0;
+    free_cidx();
+    for (int l = 0; l < p->nlev; ++l) {
+      Level& lv = p->lev[l];
+      if (tau <= 0.0) {
+        nc[l] = lv.ng;
+        continue;
+      }
+      const int64_t nb = (lv.ng + kCompactBlock - 1) / kCompactBlock;
+      int* counts = nullptr;
+      if ((st = dalloc_t(p, &counts, size_t(nb), "compaction counts"))) return done(st);
+      k_flag_count<<<unsigned(nb), kCompactBlock, 0, s>>>(d0 + p->off[l], lv.ng, tau, counts);
+      std::vector<int> hc(nb);
+      cudaMemcpyAsync(hc.data(), counts, sizeof(int) * nb, cudaMemcpyDeviceToHost, s);
+      if ((st = cuda_check(p, cudaStreamSynchronize(s), "compaction counts"))) {
+        dfree(counts);
+        return done(st);
+      }
+      int64_t acc = 0;
+      for (int64_t b = 0; b < nb; ++b) {
+        const int c = hc[b];
+        hc[b] = int(acc);
+        acc += c;
+      }
+      nc[l] = acc;
+      if (acc) {
+        if ((st = dalloc_t(p, &cidx[l], size_t(acc), "candidates"))) {
+          dfree(counts);
+          return done(st);
+        }
+        cudaMemcpyAsync(counts, hc.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s);
+        k_compact<<<unsigned(nb), kCompactBlock, 0, s>>>(d0 + p->off[l], lv.ng, tau, counts, cidx[l]);
+      }
+      count_launches(acc ? 2 : 1);
+      st = cuda_check(p, cudaStreamSynchronize(s), "compaction");
+      dfree(counts);
+      if (st) return done(st);
+    }
+    bool all_kept = true;
+    for (int l = 0; l < p->nlev; ++l) all_kept = all_kept && nc[l] == p->lev[l].ng;
+    if (all_kept) {  // nothing dropped: this is the full greedy run
+      free_cidx();
+      return done(select_loop(p, nip, tol, d0, cidx, nc, nfound, kl));
+    }
+    st = select_loop(p, nip, tol, d0, cidx, nc, nfound, kl);
+    if (st || tau <= 0.0) return done(st);
+    // certificate: every step's tie threshold stayed above tau
+    std::vector<double> dv(*nfound);
+    cudaMemcpyAsync(dv.data(), p->d_dval, sizeof(double) * dv.size(), cudaMemcpyDeviceToHost, s);
+    if ((st = cuda_check(p, cudaStreamSynchronize(s), "pivot values"))) return done(st);
+    bool ok = *nfound == nip || (tol > 0.0 && tau <= tol * dmax0);
+    for (double v : dv) ok = ok && (v * (1.0 - 2.0 * p->opt.tie_rel) - 2.0 * p->opt.tie_abs * dmax0 >= tau);
+    if (ok) return done(ISDF_OK);
+  }
+  return done(ISDF_OK);
 }
 
 }  // namespace isdf

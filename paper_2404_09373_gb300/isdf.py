@@ -36,6 +36,7 @@ EXPORTED = [
     "isdf_destroy",
     "isdf_profile_json",
     "isdf_kernel_launches",
+    "isdf_gemm_f64",
 ]
 
 
@@ -114,6 +115,9 @@ def load_library(build_if_missing: bool = True):
     lib.isdf_profile_json.restype = ctypes.c_char_p
     lib.isdf_kernel_launches.argtypes = []
     lib.isdf_kernel_launches.restype = c_int64
+    lib.isdf_gemm_f64.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64, c_int64,
+                                  c_double, c_int, c_int, c_void_p]
+    lib.isdf_gemm_f64.restype = c_int
     _lib = lib
     return lib
 
@@ -278,6 +282,19 @@ def isdf_profile_json(plan: Plan) -> dict:
     import json
 
     return json.loads(plan._lib.isdf_profile_json(plan.handle).decode())
+
+
+def isdf_gemm_f64(A, B, C, alpha=1.0, slices=5, splits=1, stream=None):
+    """C = alpha A B^T on the tensor cores (torch CUDA float64 tensors, row-major)."""
+    lib = load_library()
+    M, K = A.shape
+    N = B.shape[0]
+    st = lib.isdf_gemm_f64(A.data_ptr(), B.data_ptr(), C.data_ptr(), M, N, K, A.stride(0), B.stride(0), C.stride(0),
+                           float(alpha), int(slices), int(splits),
+                           c_void_p(_default_stream() if stream is None else stream))
+    if st != ISDF_OK:
+        raise IsdfError(st, lib.isdf_last_error(None).decode())
+    return C
 
 
 def isdf_kernel_launches() -> int:

@@ -198,6 +198,47 @@ def test_selection_time_budget(small):
         plan.close()
 
 
+def test_exact_prefilter_equals_full_greedy():
+    """options.prefilter = 1 drops points whose initial residual is below tau
+    and certifies the result; pivots and K equal the oracle's full greedy."""
+    sysd, C = S.small_multigrid(per_cell=(16, 8, 4), seed=12)
+    o = oracle.run(sysd, C, 260)
+    g = gpu_run(sysd, C, 260, opts={"prefilter": 1})
+    assert_parity(g, o, natom=8)
+    sysd, C, nip = S.config(1)  # nothing can be dropped here: full run
+    o = oracle.run(sysd, C, nip)
+    g = gpu_run(sysd, C, nip, opts={"prefilter": 1})
+    assert_parity(g, o, natom=8, k_tol=1e-7)
+
+
+# --------------------------------------------------------------------------- tensor-core path
+
+
+def test_tensor_core_path_small(small):
+    """options.precision = 1: fit, Coulomb products on tcgen05 with sliced BF16
+    digits.  Selection is unchanged (FP64), so pivots match exactly; K and E_x
+    meet max|dK| <= 1e-6 Ha and |dE_x| <= 1e-6 Ha/atom.  Xi and V are not
+    compared elementwise: they carry the conditioning of CC^T (see
+    assert_parity), K does not."""
+    sysd, C, o = small
+    g = gpu_run(sysd, C, 300, opts={"precision": 1})
+    dK = assert_parity(g, o, natom=8, k_tol=1e-6, v_rel=None, xi_rel=None)
+    assert dK <= 1e-6
+
+
+def test_tensor_core_path_ragged_and_workload1():
+    rng = np.random.default_rng(9)
+    sysd = S.make_system((1, 1, 2), 0.07, rng, ((10, 12, 9), (6, 6, 5), (2, 4, 3)), (1.6, 0.4))
+    C = S.make_orbitals(sysd, 12, rng)
+    o = oracle.run(sysd, C, 350)
+    g = gpu_run(sysd, C, 350, opts={"precision": 1})
+    assert_parity(g, o, natom=16, k_tol=1e-6, v_rel=None, xi_rel=None)
+    sysd, C, nip = S.config(1)
+    o = oracle.run(sysd, C, nip)
+    g = gpu_run(sysd, C, nip, opts={"precision": 1})
+    assert_parity(g, o, natom=8, k_tol=1e-6, v_rel=None, xi_rel=None)
+
+
 # --------------------------------------------------------------------------- full size
 
 
@@ -230,6 +271,14 @@ def test_workload2_full_size_sampled_and_properties(workload2):
                 assert abs(phi[r, g] - ref) <= 1e-13 * max(1e-3, abs(ref))
         piv, dv = B.isdf_select_points(plan, nip)
         assert piv.size == nip
+        # the exact prefilter reproduces the full greedy selection at full size
+        plan_f = B.isdf_plan(sysd, {"prefilter": 1})
+        try:
+            piv_f, dv_f = B.isdf_select_points(plan_f, nip)
+        finally:
+            plan_f.close()
+        np.testing.assert_array_equal(piv_f, piv)
+        np.testing.assert_allclose(dv_f, dv, rtol=1e-9, atol=1e-14 * dv[0])
         # first steps of the greedy selection against the oracle
         levels = O._level_data(sysd, f)
         osel = O.select_points(levels, 12)
