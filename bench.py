@@ -41,8 +41,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--precision", type=int, default=0, help="1: tensor-core products, 0: plain FP64")
-    ap.add_argument("--prefilter", type=int, default=0, help="exact candidate prefilter in the selection")
+    ap.add_argument("--precision", type=int, default=1, help="1: tensor-core products, 0: plain FP64")
+    ap.add_argument("--prefilter", type=int, default=1, help="exact candidate prefilter in the selection")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 comparison step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")

@@ -174,5 +174,6 @@ void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, doubl
 // splits > 1 needs work of splits*M*N doubles.  Error codes go to *err.
 void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, double alpha, int tri, int sym,
              int splits, double* work, int* err, cudaStream_t s);
+int64_t oz_tile_elems(int64_t rows, int64_t K, int rt, int S);
 
 }  // namespace isdf

@@ -34,7 +34,8 @@ constexpr int kBK = 32;   // k values per tile / pipeline stage
 constexpr int kKcTiles = 32;  // 1024 k values per exact chunk
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 32 * (2 + kEpiWarps);
-constexpr long long kWaitLimit = 1ll << 26;
+constexpr long long kWaitLimit = 1ll << 30;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s of device time per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -58,8 +59,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Bounded wait: gives up after kWaitNs of device time, after kWaitLimit polls,
+// or as soon as any CTA of the launch has recorded an error in *err.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, const int* err) {
   const uint32_t addr = smem_u32(bar);
+  unsigned long long t0 = 0;
   for (long long i = 0; i < kWaitLimit; ++i) {
     uint32_t done;
     asm volatile(
@@ -68,6 +78,12 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
         : "r"(addr), "r"(phase)
         : "memory");
     if (done) return true;
+    if ((i & 255) == 0) {
+      const unsigned long long now = globaltimer_ns();
+      if (i == 0) t0 = now;
+      else if (now - t0 > kWaitNs) return false;
+      if (err && *(volatile const int*)err) return false;
+    }
   }
   return false;
 }
@@ -257,6 +273,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
   const int64_t nt = blockIdx.x, mt = blockIdx.y;  // N tiles vary fastest: CTAs in flight share A
   const int64_t m0 = mt * kBM, n0 = nt * BN;
   if (P.sym && n0 > m0 + kBM - 1) return;  // tile entirely above the diagonal
+  // an earlier CTA failed: do nothing (one read, made uniform across the CTA)
+  if (__syncthreads_or(threadIdx.x == 0 ? *(volatile const int*)P.err : 0)) return;
 
   // k-tile range of this CTA
   int64_t kt_lo = 0, kt_hi = P.nkt;
@@ -301,7 +319,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
       for (int64_t it = 0; it < nk; ++it) {
         const int st = int(it % Cfg::nst);
         const int64_t round = it / Cfg::nst;
-        if (round > 0 && !mbar_wait(&empty[st], uint32_t((round - 1) & 1))) {
+        if (round > 0 && !mbar_wait(&empty[st], uint32_t((round - 1) & 1), P.err)) {
           set_err(P.err, 11);
           *(volatile int*)abort_flag = 1;
           break;
@@ -318,7 +336,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
       // copies that were issued but never consumed must land before exit
       if (*(volatile int*)abort_flag) {
         const int64_t first = issued > Cfg::nst ? issued - Cfg::nst : 0;
-        for (int64_t it = first; it < issued; ++it) mbar_wait(&full[it % Cfg::nst], uint32_t((it / Cfg::nst) & 1));
+        for (int64_t it = first; it < issued; ++it) mbar_wait(&full[it % Cfg::nst], uint32_t((it / Cfg::nst) & 1), nullptr);
       }
     }
   } else if (warp == 1) {
@@ -329,12 +347,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
         const int st = int(it % Cfg::nst);
         const int64_t round = it / Cfg::nst;
         const int64_t cpos = it % kKcTiles, chunk = it / kKcTiles;
-        if (cpos == 0 && chunk > 0 && !mbar_wait(acc_empty, uint32_t((chunk - 1) & 1))) {
+        if (cpos == 0 && chunk > 0 && !mbar_wait(acc_empty, uint32_t((chunk - 1) & 1), P.err)) {
           set_err(P.err, 12);
           *(volatile int*)abort_flag = 1;
           break;
         }
-        if (!mbar_wait(&full[st], uint32_t(round & 1))) {
+        if (!mbar_wait(&full[st], uint32_t(round & 1), P.err)) {
           set_err(P.err, 13);
           *(volatile int*)abort_flag = 1;
           break;
@@ -362,7 +380,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
       }
       // all MMAs issued by this thread complete before tensor memory is freed
       umma_commit(drain);
-      mbar_wait(drain, 0);
+      mbar_wait(drain, 0, nullptr);
     }
   } else {
     // ------------------------------------------------ epilogue (8 warps)
@@ -374,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
 #pragma unroll
     for (int j = 0; j < HC; ++j) hi[j] = lo[j] = 0.0f;
     for (int64_t c = 0; c < nchunks; ++c) {
-      if (!mbar_wait(acc_full, uint32_t(c & 1))) {
+      if (!mbar_wait(acc_full, uint32_t(c & 1), P.err)) {
         set_err(P.err, 14);
         *(volatile int*)abort_flag = 1;
         break;
