@@ -224,6 +224,29 @@ int64_t isdf_kernel_launches(void);
 isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
                           int64_t ldb, int64_t ldc, double alpha, int slices, int splits, void* stream);
 
+/* The same product as isdf_gemm_f64 for callers that cannot allocate device
+ * memory: code running while a stream capture is open, inside a framework
+ * whose allocator owns the device's memory, or on a path where the implicit
+ * synchronisation of cudaMalloc/cudaFree is not acceptable.  (The paper has
+ * no counterpart; this is an interface of this library only.)
+ * All scratch -- the BF16 digit planes of both operands, their row scales and
+ * an error word -- lives in one static device array of
+ * isdf_gemm_f64_noalloc_capacity() bytes (32 MiB), which every GPU that loads
+ * the library holds until the process exits.  The call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.  Operands whose
+ * digit planes need more than the array (about 10 (M + N) K bytes plus
+ * padding) are rejected with ISDF_ERR_ARG and a message giving both sizes;
+ * there is no k splitting here.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress, with that device current) and
+ * caches it; make that first call before any stream capture starts.  Every
+ * call on a device shares the one array, so calls whose GPU work overlaps
+ * (different streams or host threads) race and corrupt each other: serialise
+ * them.  A, B, C are device pointers, same layout, slices and error behaviour
+ * as isdf_gemm_f64; returns after `stream` is idle. */
+isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K,
+                                  int64_t lda, int64_t ldb, int64_t ldc, double alpha, int slices, void* stream);
+int64_t isdf_gemm_f64_noalloc_capacity(void);
+
 /* Message of the last failed call on this plan (or of the last failed
  * isdf_plan when plan is NULL).  Valid until the next call. */
 const char* isdf_last_error(isdf_plan_t plan);

@@ -586,6 +586,21 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
   return st;
 }
 
+isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K,
+                                  int64_t lda, int64_t ldb, int64_t ldc, double alpha, int slices, void* stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || (slices != 5 && slices != 6)) {
+    g_plan_error = "invalid arguments to isdf_gemm_f64_noalloc";
+    return ISDF_ERR_ARG;
+  }
+  std::string why;
+  const isdf_status st = gemm_noalloc(A, B, C, M, N, K, lda, ldb, ldc, alpha, slices,
+                                      static_cast<cudaStream_t>(stream), why);
+  if (st) g_plan_error = why;
+  return st;
+}
+
+int64_t isdf_gemm_f64_noalloc_capacity(void) { return int64_t(gemm_noalloc_capacity()); }
+
 const char* isdf_last_error(isdf_plan_t h) {
   if (!h) return g_plan_error.c_str();
   return h->p.err.c_str();

@@ -175,5 +175,9 @@ void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, doubl
 void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, double alpha, int tri, int sym,
              int splits, double* work, int* err, cudaStream_t s);
 int64_t oz_tile_elems(int64_t rows, int64_t K, int rt, int S);
+// the same product with its scratch in a fixed static device array (no allocation)
+size_t gemm_noalloc_capacity();
+isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
+                         int64_t ldb, int64_t ldc, double alpha, int slices, cudaStream_t s, std::string& why);
 
 }  // namespace isdf

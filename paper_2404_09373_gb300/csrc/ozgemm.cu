@@ -24,6 +24,9 @@
 // lets its copies and MMAs in flight finish, frees tensor memory and exits.
 #include <cuda_bf16.h>
 
+#include <mutex>
+#include <string>
+
 #include "internal.cuh"
 
 namespace isdf {
@@ -546,6 +549,93 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
     k_oz_reduce<<<unsigned((tot + 255) / 256), 256, 0, s>>>(work, P.splits, A.rows, B.rows, C, ldc, trans, sym);
     count_launches(1);
   }
+}
+
+// ---------------------------------------------------------------- fixed scratch
+//
+// The variant below runs the same slicing and GEMM kernels, but its scratch
+// lives in one file-scope device array instead of memory from cudaMalloc.
+// Every GPU that loads the library holds this array until the process exits.
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;
+static __device__ __align__(256) unsigned char g_gemm_static_scratch[kStaticScratchBytes];
+
+namespace {
+
+std::mutex g_static_mu;
+void* g_static_addr[64] = {nullptr};
+
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+}  // namespace
+
+size_t gemm_noalloc_capacity() { return kStaticScratchBytes; }
+
+isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
+                         int64_t ldb, int64_t ldc, double alpha, int slices, cudaStream_t s, std::string& why) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    why = "no current CUDA device";
+    return ISDF_ERR_CUDA;
+  }
+  unsigned char* base = nullptr;
+  {
+    // set-up once per device, with that device current: the array's name is
+    // a host-side stand-in, its device address comes from the runtime
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_addr[dev]) {
+      void* ptr = nullptr;
+      const cudaError_t e = cudaGetSymbolAddress(&ptr, g_gemm_static_scratch);
+      if (e != cudaSuccess || !ptr) {
+        cudaGetLastError();
+        why = std::string("cudaGetSymbolAddress of the static scratch failed: ") + cudaGetErrorString(e);
+        return ISDF_ERR_CUDA;
+      }
+      g_static_addr[dev] = ptr;
+    }
+    base = static_cast<unsigned char*>(g_static_addr[dev]);
+  }
+  OzOperand a, b;
+  a.rows = M, a.K = K, a.rt = 128, a.S = slices, a.nrt = (M + 127) / 128, a.nkt = (K + kBK - 1) / kBK;
+  b.rows = N, b.K = K, b.rt = oz_bn(slices), b.S = slices, b.nrt = (N + b.rt - 1) / b.rt, b.nkt = a.nkt;
+  const size_t ta = round256(size_t(oz_tile_elems(M, K, a.rt, slices)) * 2);
+  const size_t ea = round256(sizeof(int) * size_t(a.nrt * a.rt));
+  const size_t tb = round256(size_t(oz_tile_elems(N, K, b.rt, slices)) * 2);
+  const size_t eb = round256(sizeof(int) * size_t(b.nrt * b.rt));
+  const size_t need = ta + ea + tb + eb + 256;
+  if (need > kStaticScratchBytes) {
+    why = "isdf_gemm_f64_noalloc needs " + std::to_string(need) + " bytes of scratch; the static array holds " +
+          std::to_string(kStaticScratchBytes);
+    return ISDF_ERR_ARG;
+  }
+  a.tiles = base;
+  a.exps = reinterpret_cast<int*>(base + ta);
+  b.tiles = base + ta + ea;
+  b.exps = reinterpret_cast<int*>(base + ta + ea + tb);
+  int* err = reinterpret_cast<int*>(base + ta + ea + tb + eb);
+  // the array keeps the previous call's contents: the error word must start at
+  // zero; every slice byte and every scale read below is rewritten first
+  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) {
+    cudaGetLastError();
+    why = "cudaMemsetAsync of the error word failed";
+    return ISDF_ERR_CUDA;
+  }
+  oz_slice(A, lda, 1, nullptr, 1.0, a, s);
+  oz_slice(B, ldb, 1, nullptr, 1.0, b, s);
+  oz_gemm(a, b, C, ldc, 0, alpha, 0, 0, 1, nullptr, err, s);
+  int herr = 0;
+  cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    why = std::string("isdf_gemm_f64_noalloc: ") + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  }
+  if (herr) {
+    why = "isdf_gemm_f64_noalloc: tensor-core pipeline wait expired (code " + std::to_string(herr) + ")";
+    return ISDF_ERR_TIMEOUT;
+  }
+  return ISDF_OK;
 }
 
 }  // namespace isdf

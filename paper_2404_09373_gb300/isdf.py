@@ -37,6 +37,8 @@ EXPORTED = [
     "isdf_profile_json",
     "isdf_kernel_launches",
     "isdf_gemm_f64",
+    "isdf_gemm_f64_noalloc",
+    "isdf_gemm_f64_noalloc_capacity",
 ]
 
 
@@ -118,6 +120,11 @@ def load_library(build_if_missing: bool = True):
     lib.isdf_gemm_f64.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64, c_int64,
                                   c_double, c_int, c_int, c_void_p]
     lib.isdf_gemm_f64.restype = c_int
+    lib.isdf_gemm_f64_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64,
+                                          c_int64, c_double, c_int, c_void_p]
+    lib.isdf_gemm_f64_noalloc.restype = c_int
+    lib.isdf_gemm_f64_noalloc_capacity.argtypes = []
+    lib.isdf_gemm_f64_noalloc_capacity.restype = c_int64
     _lib = lib
     return lib
 
