@@ -44,6 +44,12 @@ def parse():
     ap.add_argument("--precision", type=int, default=1, help="1: tensor-core products, 0: plain FP64")
     ap.add_argument("--prefilter", type=int, default=1, help="exact candidate prefilter in the selection")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 comparison step")
+    ap.add_argument("--batch", action="store_true",
+                    help="also run the 24-cell batch (6 each of 1x1x1, 1x1x2, 1x2x2, 2x2x2, sigma 0.1) on "
+                         "concurrent streams and one stream")
+    ap.add_argument("--learned", type=int, default=0,
+                    help="train the point proposer on this many seeded 1x1x1/2x2x1 cells, then time the "
+                         "learned selection (4 N_ip candidates, fallback check) on the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip the separately profiled step")
@@ -139,6 +145,20 @@ def cpu_baseline_sample():
             "sample": "FP64 NumPy/SciPy oracle, 1x1x1 cell of the same family (8 C, N=104, n=16, grids "
                       "48^3/24^3/12^3, N_ip=624), 1/8 of the workload's atoms; BLAS threads = host cores",
             "T_isdf_s": t1 - t0, "T_exchange_s": t2 - t1}
+
+
+def aggregate_over_ranks(s_iter, ms_step, world, device):
+    """Max over ranks of the per-rank step times; the whole-job value is the
+    time per processed cell: `world` independent cells per max step time.
+    Returns (value, max s_iter, max ms_step)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        t = torch.tensor([s_iter, ms_step], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        s_iter, ms_step = float(t[0]), float(t[1])
+    return s_iter / world, s_iter, ms_step
 
 
 def dist_env():
@@ -291,12 +311,7 @@ def main():
     sx = [r["exchange"] for r in res]
     s_iter = statistics.mean(a / SCF_CHARGE + b for a, b in zip(per, sx))
     ms_step = 1e3 * statistics.mean(a + b for a, b in zip(per, sx))
-    if world > 1:
-        t = torch.tensor([s_iter, ms_step], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        s_iter, ms_step = float(t[0]), float(t[1])
-    # whole job: `world` independent cells per max-over-ranks step time
-    value = s_iter / world
+    value, s_iter, ms_step = aggregate_over_ranks(s_iter, ms_step, world, dev)
 
     # ---- the plain FP64 GPU form on the same workload (the metric's denominator)
     plain = None
@@ -308,6 +323,58 @@ def main():
             "plan", "select", "fit", "coulomb", "exchange")},
                  "max_abs_dK_vs_fast_Ha": float((K_dev - K_fast).abs().max()),
                  "dEx_per_atom_vs_fast_Ha": abs(r0["Ex"] - res[-1]["Ex"]) / sysd["xyz"].shape[0]}
+
+    # ---- learned point proposal (trained here; reported beside the main number)
+    learned = None
+    if args.learned > 0:
+        from paper_2404_09373_gb300 import learn as Lr
+
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            cells = Lr.training_cells(args.learned)
+            stats = {}
+            X, y, w = Lr.collect(cells, neg_per_pos=20, stats=stats)
+            params, losses = Lr.train(X, y, w, epochs=30, batch=65536, lr=3e-3, stream=stream.cuda_stream)
+        t_train = time.perf_counter() - t0
+        K_full = K_dev.clone()
+        with torch.cuda.stream(stream):
+            plan = B.isdf_plan(sysd, opts, stream=stream.cuda_stream)
+            te = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            te[0].record(stream)
+            piv_l, info = Lr.select_learned(plan, params, nip, stats["level_density"], factor=4)
+            te[1].record(stream)
+            B.isdf_coulomb(plan)
+            te[2].record(stream)
+            _, ex_l = B.isdf_exchange(plan, C_dev, K_dev)
+            te[3].record(stream)
+        stream.synchronize()
+        plan.close()
+        tl = [te[i].elapsed_time(te[i + 1]) / 1e3 for i in range(3)]
+        full_sel = statistics.mean(r["select"] for r in res)
+        learned = {"train_cells": args.learned, "train_samples": int(X.shape[0]), "train_s": t_train,
+                   "final_loss": losses[-1], "ncand": info["ncand"], "fallback": info["fallback"],
+                   "residual_ratio": info["residual_ratio"], "t_select_s": info["t_select_s"],
+                   "quota": info["quota"], "pivots_per_level": info["pivots_per_level"],
+                   "residual_ratio_per_level": info["residual_ratio_per_level"],
+                   "level_density_train": stats["level_density"],
+                   "t_select_full_s": full_sel, "select_speedup": full_sel / info["t_select_s"],
+                   "s_iter": (statistics.mean(r["plan"] for r in res) + tl[0] + tl[1]) / SCF_CHARGE + tl[2],
+                   "max_abs_dK_vs_full_Ha": float((K_dev - K_full).abs().max()),
+                   "dEx_per_atom_vs_full_Ha": abs(ex_l - res[-1]["Ex"]) / sysd["xyz"].shape[0]}
+
+    # ---- batched workload: 24 uneven cells, concurrent streams vs one stream
+    batch = None
+    if args.batch:
+        from paper_2404_09373_gb300 import batch as Bt
+
+        cells = S.batch_cells()
+        res_c, wall_c = Bt.run_batch(cells, opts, n_streams=4)
+        res_s, wall_s = Bt.run_batch(cells, opts, n_streams=1)
+        same = all(np.array_equal(a["K"], b["K"]) for a, b in zip(res_c, res_s))
+        batch = {"cells": len(cells), "wall_s_concurrent": wall_c, "wall_s_one_stream": wall_s,
+                 "speedup": wall_s / wall_c, "identical_results": bool(same),
+                 "s_iter_per_cell_concurrent": (sum(r["t_isdf_s"] for r in res_s) / SCF_CHARGE +
+                                                sum(r["t_exchange_s"] for r in res_s)) / len(cells) * wall_c / wall_s}
 
     # ---- per-kernel timing (separate profiled step, not part of the timed region)
     kern, roof = {}, None
@@ -355,7 +422,7 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "stages_s": {k: statistics.mean(r[k] for r in res) for k in ("plan", "select", "fit", "coulomb", "exchange")},
         "Ex_per_atom": res[-1]["Ex"] / sysd["xyz"].shape[0],
-        "plain_fp64_gpu": plain,
+        "plain_fp64_gpu": plain, "learned": learned, "batch": batch,
         "speedup_vs_plain_fp64_gpu": (plain["s_iter"] / s_iter) if plain else None,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk, "wall_s_timed": wall, "kernels": kern,

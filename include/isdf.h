@@ -190,6 +190,13 @@ enum {
   ISDF_GET_V = 5,          /* double[nip x nip]                            */
   ISDF_GET_XI_LEVEL0 = 6,  /* double[k_l x N_g,l] Xi^T of level 0; add the
                               level index for the others                   */
+  ISDF_GET_NPOINTS = 4 + 16,  /* int64[1]: grid points of all levels       */
+  ISDF_GET_FIT_RESIDUAL = 5 + 16, /* double[2 nlevel]: per level the largest
+                              and the summed residual w (M(g,g) - M(g,P)
+                              M_PP^-1 M(P,g)) over all grid points after
+                              isdf_fit, i.e. the Schur complement left by the
+                              pivots (sum = weighted fit error^2); -1 for a
+                              level without pivots                         */
   ISDF_GET_PHI_LEVEL0 = 10 /* double[|G_l| x N_g,l] basis values of level
                               0 (rows: functions of the level in index order,
                               then coarser ones); add the level index      */
@@ -207,6 +214,44 @@ const char* isdf_profile_json(isdf_plan_t plan);
 /* Number of kernels this library has launched in this process so far (its
  * own kernels; cuFFT's are not counted).  Host-side counter. */
 int64_t isdf_kernel_launches(void);
+
+/* ---- Learned point proposer (not in the paper: an extension of this
+ * library).  A small network (8 inputs, two hidden layers of 64 with ReLU,
+ * one logistic output; 4801 FP32 parameters in the order W1 8x64, b1, W2
+ * 64x64, b2, W3 64, b3) scores grid points so that isdf_select_points can
+ * run on a short candidate list.  The full selection stays the reference. */
+
+int isdf_mlp_num_params(void);
+
+/* Eight FP32 features per grid point, all levels concatenated (level 0
+ * first, grid order g within a level; isdf_get_size(plan, ISDF_GET_NPOINTS)
+ * points): log10 of the initial residual relative to the largest, log10 of
+ * sum_L phi^2 and of sum_N phi^2, log10 |grad (sum_G phi^2)|, distances to
+ * the nearest and second-nearest atom (bohr / 4), the L share of the basis
+ * weight, level / (nlevel-1).  feat_out: host or device, npoints x 8. */
+isdf_status isdf_features(isdf_plan_t plan, float* feat_out);
+
+/* One training step on n samples (DEVICE pointers): class-weighted binary
+ * cross entropy L = -sum_i w_i [y_i log p_i + (1-y_i) log(1-p_i)] / sum_i w_i,
+ * gradient by the library's fused forward/backward kernel, then an Adam
+ * update (step counts from 1; lr = 0 skips the update).  adam_m/adam_v are
+ * the moment vectors (nullable when lr = 0).  loss_out: host float of the
+ * loss before the update (nullable); grad_out: device copy of the gradient
+ * (nullable).  X is n x 8 row-major, y and w length n. */
+isdf_status isdf_mlp_train_step(float* params, float* adam_m, float* adam_v, int step, float lr, const float* X,
+                                const float* y, const float* w, int64_t n, float* loss_out, float* grad_out,
+                                void* stream);
+
+/* Logits of n samples with BF16 weights and activations (FP32 sums);
+ * DEVICE pointers. */
+isdf_status isdf_mlp_score(const float* params, const float* X, int64_t n, float* scores, void* stream);
+
+/* Candidate list for isdf_select_points: on every level l the quota[l]
+ * highest-scoring grid points of that level (ties to the smallest g), as
+ * pivot codes in ascending (level, g) order.  quota: host, nlevel entries,
+ * 0 <= quota[l] <= N_g,l.  params: device.  cand_out: host or device, sum of
+ * the quotas int64. */
+isdf_status isdf_propose(isdf_plan_t plan, const float* params, const int64_t* quota, int64_t* cand_out);
 
 /* FP64-accurate matrix product on the tensor cores -- the contraction
  * kernel behind options.precision = 1, exposed for verification and reuse

@@ -465,6 +465,10 @@ int64_t isdf_get_size(isdf_plan_t h, int what) {
       return p->state >= 2 ? int64_t(p->nfun) * p->nip : 0;
     case ISDF_GET_V:
       return p->state >= 3 ? int64_t(p->nip) * p->nip : 0;
+    case ISDF_GET_NPOINTS:
+      return 1;
+    case ISDF_GET_FIT_RESIDUAL:
+      return p->state >= 2 ? 2 * p->nlev : 0;
     default:
       break;
   }
@@ -510,6 +514,12 @@ isdf_status isdf_get(isdf_plan_t h, int what, void* dst) {
       return from_device(p, static_cast<double*>(dst), p->XN, size_t(n), true);
     case ISDF_GET_V:
       return from_device(p, static_cast<double*>(dst), p->V, size_t(n), true);
+    case ISDF_GET_NPOINTS: {
+      const int64_t v = p->ntot;
+      return put_host(&v, sizeof(v));
+    }
+    case ISDF_GET_FIT_RESIDUAL:
+      return put_host(p->fit_resid, sizeof(double) * 2 * p->nlev);
     default:
       break;
   }
@@ -541,6 +551,82 @@ const char* isdf_profile_json(isdf_plan_t h) {
 }
 
 int64_t isdf_kernel_launches(void) { return g_launches.load(); }
+
+int isdf_mlp_num_params(void) { return mlp_num_params(); }
+
+isdf_status isdf_features(isdf_plan_t h, float* feat_out) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (!feat_out) return fail(p, ISDF_ERR_ARG, "feat_out is NULL");
+  const size_t n = size_t(p->ntot) * 8;
+  float* d = feat_out;
+  float* stage = nullptr;
+  const bool dev = is_device_ptr(feat_out);
+  isdf_status st = ISDF_OK;
+  if (!dev && (st = dalloc_t(p, &stage, n, "features"))) return st;
+  if (!dev) d = stage;
+  st = learn_features(p, d);
+  if (!st && !dev) st = from_device(p, feat_out, stage, n, true);
+  dfree(stage);
+  return st;
+}
+
+isdf_status isdf_mlp_train_step(float* params, float* adam_m, float* adam_v, int step, float lr, const float* X,
+                                const float* y, const float* w, int64_t n, float* loss_out, float* grad_out,
+                                void* stream) {
+  if (!params || !X || !y || !w || n < 1 || step < 1 || !(lr >= 0.0f) || (lr > 0.0f && (!adam_m || !adam_v))) {
+    g_plan_error = "invalid arguments to isdf_mlp_train_step";
+    return ISDF_ERR_ARG;
+  }
+  if (!is_device_ptr(params) || !is_device_ptr(X) || !is_device_ptr(y) || !is_device_ptr(w)) {
+    g_plan_error = "isdf_mlp_train_step takes device pointers";
+    return ISDF_ERR_ARG;
+  }
+  std::string why;
+  const isdf_status st = mlp_grad_step(params, adam_m, adam_v, step, lr, X, y, w, n, loss_out, grad_out,
+                                       static_cast<cudaStream_t>(stream), why);
+  if (st) g_plan_error = why;
+  return st;
+}
+
+isdf_status isdf_mlp_score(const float* params, const float* X, int64_t n, float* scores, void* stream) {
+  if (!params || !X || !scores || n < 1) {
+    g_plan_error = "invalid arguments to isdf_mlp_score";
+    return ISDF_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  mlp_score(params, X, n, scores, s);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    g_plan_error = std::string("isdf_mlp_score: ") + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  }
+  return ISDF_OK;
+}
+
+isdf_status isdf_propose(isdf_plan_t h, const float* params, const int64_t* quota, int64_t* cand_out) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (!params || !quota || !cand_out) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_propose");
+  std::vector<int64_t> q(p->nlev);
+  int64_t ncand = 0;
+  for (int l = 0; l < p->nlev; ++l) {
+    if (quota[l] < 0 || quota[l] > p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "quota out of range");
+    q[l] = quota[l];
+    ncand += q[l];
+  }
+  if (ncand < 1) return fail(p, ISDF_ERR_ARG, "empty candidate quota");
+  int64_t* d = cand_out;
+  int64_t* stage = nullptr;
+  const bool dev = is_device_ptr(cand_out);
+  isdf_status st = ISDF_OK;
+  if (!dev && (st = dalloc_t(p, &stage, size_t(ncand), "candidates"))) return st;
+  if (!dev) d = stage;
+  st = learn_propose(p, params, q.data(), d);
+  if (!st && !dev) st = from_device(p, cand_out, stage, size_t(ncand), true);
+  dfree(stage);
+  return st;
+}
 
 isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
                           int64_t ldb, int64_t ldc, double alpha, int slices, int splits, void* stream) {

@@ -124,6 +124,31 @@ isdf_status fit_solve_tc(Plan* p, int k, double* zct, double* y, const double* l
   return ISDF_OK;
 }
 
+// residual of the pair fit at every grid point, r(g) = w (M(g,g) - |Y[:,g]|^2)
+// with Y = R^-1 (ZC^T)^T: the Schur complement left after the pivots; max and
+// sum (= the weighted Frobenius fit error^2) go to out[0], out[1]
+__global__ void k_fit_residual(const double* __restrict__ phi, int64_t ng, int nL, int nG, double w,
+                               const double* __restrict__ y, int k, unsigned long long* out_max, double* out_sum) {
+  double mx = 0.0, sm = 0.0;
+  for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
+    double aL = 0.0, aN = 0.0, q = 0.0;
+    for (int r = 0; r < nL; ++r) aL = fma(phi[int64_t(r) * ng + g], phi[int64_t(r) * ng + g], aL);
+    for (int r = nL; r < nG; ++r) aN = fma(phi[int64_t(r) * ng + g], phi[int64_t(r) * ng + g], aN);
+    for (int j = 0; j < k; ++j) q = fma(y[int64_t(j) * ng + g], y[int64_t(j) * ng + g], q);
+    const double res = w * (aL * (aL + 2.0 * aN) - q);
+    mx = fmax(mx, res);
+    sm += res;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    sm += __shfl_xor_sync(0xffffffffu, sm, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out_max, (unsigned long long)__double_as_longlong(fmax(mx, 0.0)));
+    atomicAdd(out_sum, sm);
+  }
+}
+
 }  // namespace
 
 isdf_status fit_run(Plan* p) {
@@ -133,6 +158,7 @@ isdf_status fit_run(Plan* p) {
     Level& lv = p->lev[l];
     dfree(lv.xiT);
     lv.xiT = nullptr;
+    p->fit_resid[2 * l] = p->fit_resid[2 * l + 1] = -1.0;  // not computed (no pivots on the level)
     if (lv.k == 0) continue;
     const int k = lv.k;
     const int64_t ng = lv.ng;
@@ -223,6 +249,15 @@ isdf_status fit_run(Plan* p) {
     g2.ldc = ng;
     g2.tri = 2;
     dgemm(g2, s);
+    }
+    {
+      // y still holds R^-1 (ZC^T)^T: residual statistics of this level
+      unsigned long long* rmax = reinterpret_cast<unsigned long long*>(scr);
+      double* rsum = scr + 1;
+      cudaMemsetAsync(scr, 0, 2 * sizeof(double), s);
+      k_fit_residual<<<152 * 4, 256, 0, s>>>(lv.phi, ng, lv.nL, lv.nG, lv.w, y, k, rmax, rsum);
+      count_launches(1);
+      cudaMemcpyAsync(&p->fit_resid[2 * l], scr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     }
     st = cuda_check(p, cudaStreamSynchronize(s), "fit");
     if (!st && p->opt.precision == 1) st = oz_check(p);

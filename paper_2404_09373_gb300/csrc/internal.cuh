@@ -89,6 +89,7 @@ struct Plan {
   double* V = nullptr;          // [nip][nip]
   int* d_err = nullptr;         // device error word (Cholesky breakdown etc.)
   int* d_ozerr = nullptr;       // tensor-core pipeline error word
+  double fit_resid[2 * ISDF_MAX_LEVELS] = {0};  // per level: max and sum of the fit residual
   std::string err;
   std::string fault;            // host fault injection (ISDF_FAULT)
   // profiling
@@ -179,5 +180,14 @@ int64_t oz_tile_elems(int64_t rows, int64_t K, int rt, int S);
 size_t gemm_noalloc_capacity();
 isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
                          int64_t ldb, int64_t ldc, double alpha, int slices, cudaStream_t s, std::string& why);
+
+// learned point proposer (learn.cu)
+int mlp_num_params();
+isdf_status learn_features(Plan* p, float* dfeat);
+isdf_status mlp_grad_step(float* params, float* m, float* v, int step, float lr, const float* X, const float* y,
+                          const float* w, int64_t n, float* loss_host, float* grad_dev, cudaStream_t s,
+                          std::string& why);
+void mlp_score(const float* params, const float* X, int64_t n, float* out, cudaStream_t s);
+isdf_status learn_propose(Plan* p, const float* params, const int64_t* quota, int64_t* dcand);
 
 }  // namespace isdf

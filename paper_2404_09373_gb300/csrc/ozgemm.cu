@@ -129,46 +129,92 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
 
+// f * 2^e as a double, built with integer operations (exact; the narrow FP64
+// pipe is left alone).  Subnormal or out-of-range cases take the FP64 route.
+__device__ __forceinline__ double scaled_to_double(float f, int e) {
+  const uint32_t b = __float_as_uint(f);
+  if ((b << 1) == 0u) return __longlong_as_double((long long)(uint64_t(b >> 31) << 63));  // +-0
+  const int ef = int((b >> 23) & 0xFF);
+  const int ed = ef - 127 + 1023 + e;
+  if (ef == 0 || ef == 0xFF || ed <= 0 || ed >= 0x7FF) return ldexp(double(f), e);
+  const uint64_t bits = (uint64_t(b >> 31) << 63) | (uint64_t(ed) << 52) | (uint64_t(b & 0x7FFFFF) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
 // ---------------------------------------------------------------- slicing
+
+// |x| as an order-preserving integer key (finite doubles)
+__device__ __forceinline__ uint64_t abs_key(double x) { return uint64_t(__double_as_longlong(x)) & 0x7FFFFFFFFFFFFFFFull; }
+
+// exponent e with |x| < 2^e from the key of the largest |x| of a row
+__device__ __forceinline__ int exp_of_key(uint64_t key) {
+  if (key == 0) return 0;
+  int e;
+  frexp(__longlong_as_double((long long)key), &e);
+  return e;
+}
+
+// round(x * 2^shift) to the nearest integer (ties to even) with integer
+// operations only; |result| < 2^62 is guaranteed by the caller's scaling
+__device__ __forceinline__ long long round_scaled(double x, int shift) {
+  const uint64_t b = uint64_t(__double_as_longlong(x));
+  const int E = int((b >> 52) & 0x7FF);
+  if (E == 0 && (b << 1) == 0) return 0;
+  uint64_t m = b & 0xFFFFFFFFFFFFFull;
+  int ee = E;
+  if (E == 0) ee = 1; else m |= 1ull << 52;
+  const int sh = ee - 1075 + shift;  // value = m * 2^sh
+  long long q;
+  if (sh >= 0) {
+    q = (long long)(m << sh);
+  } else if (sh <= -64) {
+    q = 0;
+  } else {
+    const int r = -sh;
+    const uint64_t qq = m >> r;
+    const uint64_t rem = m & ((1ull << r) - 1ull);
+    const uint64_t half = 1ull << (r - 1);
+    q = (long long)(qq + ((rem > half || (rem == half && (qq & 1ull))) ? 1ull : 0ull));
+  }
+  return (b >> 63) ? -q : q;
+}
 
 // e_r: max_k |x(r,k)| < 2^e_r, x = mul * kw[k] * src[r*sr + k*sk]; one thread per row
 __global__ void k_oz_rowexp_thread(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t rows, int64_t K,
                                    const double* __restrict__ kw, double mul, int* __restrict__ exps) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= rows) return;
-  double m = 0.0;
+  uint64_t m = 0;
   for (int64_t k = 0; k < K; ++k) {
-    double v = src[r * sr + k * sk] * mul;
+    double v = src[r * sr + k * sk];
+    if (mul != 1.0) v *= mul;
     if (kw) v *= kw[k];
-    m = fmax(m, fabs(v));
+    const uint64_t key = abs_key(v);
+    m = key > m ? key : m;
   }
-  int e = 0;
-  if (m > 0.0) frexp(m, &e);
-  exps[r] = e;
+  exps[r] = exp_of_key(m);
 }
 
 // same, one block per row (long rows with unit k stride)
 __global__ void k_oz_rowexp_block(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t K,
                                   const double* __restrict__ kw, double mul, int* __restrict__ exps) {
-  __shared__ double sh[256];
+  __shared__ unsigned long long sh[256];
   const int64_t r = blockIdx.x;
-  double m = 0.0;
+  uint64_t m = 0;
   for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-    double v = src[r * sr + k * sk] * mul;
+    double v = src[r * sr + k * sk];
+    if (mul != 1.0) v *= mul;
     if (kw) v *= kw[k];
-    m = fmax(m, fabs(v));
+    const uint64_t key = abs_key(v);
+    m = key > m ? key : m;
   }
   sh[threadIdx.x] = m;
   __syncthreads();
   for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-    if (threadIdx.x < o) sh[threadIdx.x] = fmax(sh[threadIdx.x], sh[threadIdx.x + o]);
+    if (threadIdx.x < o) sh[threadIdx.x] = sh[threadIdx.x] > sh[threadIdx.x + o] ? sh[threadIdx.x] : sh[threadIdx.x + o];
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    int e = 0;
-    if (sh[0] > 0.0) frexp(sh[0], &e);
-    exps[r] = e;
-  }
+  if (threadIdx.x == 0) exps[r] = exp_of_key(sh[0]);
 }
 
 // Digits of one row and one group of 8 k values, written as 16 bytes per slice.
@@ -195,10 +241,11 @@ __global__ void k_oz_digits(const double* __restrict__ src, int64_t sr, int64_t 
     const int64_t k = kg * 8 + u;
     double v = 0.0;
     if (r < rows && k < K) {
-      v = src[r * sr + k * sk] * mul;
+      v = src[r * sr + k * sk];
+      if (mul != 1.0) v *= mul;
       if (kw) v *= kw[k];
     }
-    X[u] = llrint(ldexp(v, shift));
+    X[u] = round_scaled(v, shift);
   }
   const int64_t it = r / rt, rr = r % rt, jt = kg / (kBK / 8), kc = kg % (kBK / 8);
   const int64_t tile_elems = int64_t(rt) * kBK;
@@ -431,7 +478,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
       for (int j = 0; j < HC; ++j) {
         const int64_t n = n0 + half * HC + j;
         if (n >= P.N) continue;
-        const double v = ldexp(double(hi[j]) + double(lo[j]), ea + P.eb[n] - 14) * P.alpha;
+        const int e = ea + P.eb[n] - 14;
+        double v = scaled_to_double(hi[j], e) + scaled_to_double(lo[j], e);  // one FP64 add
+        if (P.alpha != 1.0) v *= P.alpha;
         if (P.splits > 1)
           P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
         else if (P.trans)

@@ -22,6 +22,7 @@
 // the returned pivot values and otherwise repeats with a lower tau.
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <cstring>
 
 #include "internal.cuh"
@@ -239,15 +240,23 @@ __global__ void k_sel_pick(SelParams P, SelState* st) {
   }
 }
 
-__global__ __launch_bounds__(256) void k_sel_col(SelParams P, const SelState* st) {
+// One block works on 32 candidate points at a time (one point per lane, so
+// every load is a coalesced row segment); its 8 warps split the basis
+// functions and factor columns 8 ways and the partial dot products are added
+// in shared memory in a fixed order.  Grid-striding over 32-point groups keeps
+// every SM equally busy whatever the number of candidates.
+constexpr int kColWarps = 8;
+__global__ __launch_bounds__(32 * kColWarps) void k_sel_col(SelParams P, const SelState* st) {
   if (st->skip) return;
-  extern __shared__ double cp[];  // phi_G(p)
+  extern __shared__ double sm[];
   const int l = st->lev;
+  const int nL = P.nL[l], nG = P.nG[l];
+  double* cp = sm;                                 // phi_G(p)
+  double* part = sm + ((nG + 1) & ~1);             // [3][kColWarps][32]
   const int64_t gp = st->gp, tp = st->tp;
   const int col = st->col;
   const double dp = st->dp;
   const int64_t ng = P.ng[l], nc = P.nc[l];
-  const int nL = P.nL[l], nG = P.nG[l];
   const int* __restrict__ cidx = P.cidx[l];
   const double* __restrict__ phi = P.phi[l];
   double* __restrict__ fac = P.fac[l];
@@ -256,24 +265,69 @@ __global__ __launch_bounds__(256) void k_sel_col(SelParams P, const SelState* st
   __syncthreads();
   const double sq = sqrt(dp);
   const double w = P.w[l];
-  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nc; t += int64_t(gridDim.x) * blockDim.x) {
-    const int64_t g = cidx ? cidx[t] : t;
-    double aL = 0.0, aN = 0.0;
-    for (int r = 0; r < nL; ++r) aL = fma(phi[int64_t(r) * ng + g], cp[r], aL);
-    for (int r = nL; r < nG; ++r) aN = fma(phi[int64_t(r) * ng + g], cp[r], aN);
-    const double m = w * (aL * (aL + 2.0 * aN));
-    double s = 0.0;
-    for (int j = 0; j < col; ++j) s = fma(fac[int64_t(j) * nc + t], __ldg(&fac[int64_t(j) * nc + tp]), s);
-    double v = (m - s) / sq;
-    if (t == tp) v = sq;
-    fac[int64_t(col) * nc + t] = v;
-    d[t] = (t == tp) ? 0.0 : d[t] - v * v;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t ngroups = (nc + 31) / 32;
+  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int64_t t = grp * 32 + lane;
+    const bool valid = t < nc;
+    double aL = 0.0, aN = 0.0, s = 0.0;
+    if (valid) {
+      const int64_t g = cidx ? cidx[t] : t;
+      // independent partial sums keep several loads and FMAs in flight
+      double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+      int r = warp;
+      for (; r + kColWarps < nL; r += 2 * kColWarps) {
+        a0 = fma(phi[int64_t(r) * ng + g], cp[r], a0);
+        a1 = fma(phi[int64_t(r + kColWarps) * ng + g], cp[r + kColWarps], a1);
+      }
+      if (r < nL) a0 = fma(phi[int64_t(r) * ng + g], cp[r], a0);
+      r = nL + warp;
+      for (; r + kColWarps < nG; r += 2 * kColWarps) {
+        b0 = fma(phi[int64_t(r) * ng + g], cp[r], b0);
+        b1 = fma(phi[int64_t(r + kColWarps) * ng + g], cp[r + kColWarps], b1);
+      }
+      if (r < nG) b0 = fma(phi[int64_t(r) * ng + g], cp[r], b0);
+      aL = a0 + a1;
+      aN = b0 + b1;
+      double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      const double* fp = fac + tp;
+      const double* ft = fac + t;
+      int j = warp;
+      for (; j + 3 * kColWarps < col; j += 4 * kColWarps) {
+        s0 = fma(ft[int64_t(j) * nc], fp[int64_t(j) * nc], s0);
+        s1 = fma(ft[int64_t(j + kColWarps) * nc], fp[int64_t(j + kColWarps) * nc], s1);
+        s2 = fma(ft[int64_t(j + 2 * kColWarps) * nc], fp[int64_t(j + 2 * kColWarps) * nc], s2);
+        s3 = fma(ft[int64_t(j + 3 * kColWarps) * nc], fp[int64_t(j + 3 * kColWarps) * nc], s3);
+      }
+      for (; j < col; j += kColWarps) s0 = fma(ft[int64_t(j) * nc], fp[int64_t(j) * nc], s0);
+      s = (s0 + s1) + (s2 + s3);
+    }
+    part[(0 * kColWarps + warp) * 32 + lane] = aL;
+    part[(1 * kColWarps + warp) * 32 + lane] = aN;
+    part[(2 * kColWarps + warp) * 32 + lane] = s;
+    __syncthreads();
+    if (warp == 0 && valid) {
+      aL = aN = s = 0.0;
+      for (int q = 0; q < kColWarps; ++q) {
+        aL += part[(0 * kColWarps + q) * 32 + lane];
+        aN += part[(1 * kColWarps + q) * 32 + lane];
+        s += part[(2 * kColWarps + q) * 32 + lane];
+      }
+      const double m = w * (aL * (aL + 2.0 * aN));
+      double v = (m - s) / sq;
+      if (t == tp) v = sq;
+      fac[int64_t(col) * nc + t] = v;
+      d[t] = (t == tp) ? 0.0 : d[t] - v * v;
+    }
+    __syncthreads();
   }
 }
 
 }  // namespace
 
 namespace {
+
+constexpr unsigned kColBlocks = 152 * 6;  // fallback grid if the occupancy query fails
 
 // One greedy run over the given candidates (cidx[l] == nullptr: all points).
 isdf_status select_loop(Plan* p, int nip, double tol, const double* d0full, int* const* cidx, const int64_t* nc,
@@ -328,13 +382,19 @@ isdf_status select_loop(Plan* p, int nip, double tol, const double* d0full, int*
   if ((st = cuda_check(p, cudaMemcpyAsync(p->d_selstate, &h, sizeof(h), cudaMemcpyHostToDevice, s), "state init")))
     return st;
   SelState* dst = static_cast<SelState*>(p->d_selstate);
-  const size_t smem = sizeof(double) * size_t(nGmax);
+  const size_t smem = sizeof(double) * (size_t((nGmax + 1) & ~1) + 3 * kColWarps * 32);
   if (smem > 48 * 1024) {
     if ((st = cuda_check(p, cudaFuncSetAttribute(k_sel_col, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
                          "smem attribute")))
       return st;
   }
-  const unsigned red_blocks = 152 * 4, col_blocks = 152 * 8;
+  // one wave of resident blocks: grid-striding then splits the groups evenly
+  int dev = 0, nsm = 152, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sel_col, 32 * kColWarps, smem);
+  const unsigned red_blocks = unsigned(nsm) * 4;
+  const unsigned col_blocks = per_sm > 0 ? unsigned(per_sm * nsm) : kColBlocks;
   auto one_step = [&]() {
     k_sel_max<<<red_blocks, 256, 0, s>>>(P, dst);
     k_sel_first<<<red_blocks, 256, 0, s>>>(P, dst);

@@ -22,6 +22,9 @@ ISDF_OK, ISDF_ERR_ARG, ISDF_ERR_OOM, ISDF_ERR_NOT_PD, ISDF_ERR_CUDA, ISDF_ERR_CU
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_OOM", "ERR_NOT_PD", "ERR_CUDA", "ERR_CUFFT", "ERR_TIMEOUT", "ERR_STATE"]
 GET_NBASIS, GET_NIP_LEVEL, GET_PIVOTS, GET_XL, GET_XN, GET_V, GET_XI_LEVEL0 = 0, 1, 2, 3, 4, 5, 6
 GET_PHI_LEVEL0 = 10
+GET_NPOINTS, GET_FIT_RESIDUAL = 20, 21
+# element type written by isdf_get for each selector (float64 otherwise)
+_GET_DTYPE = {GET_NBASIS: np.int32, GET_NIP_LEVEL: np.int32, GET_PIVOTS: np.int64, GET_NPOINTS: np.int64}
 
 EXPORTED = [
     "isdf_options_default",
@@ -37,6 +40,11 @@ EXPORTED = [
     "isdf_profile_json",
     "isdf_kernel_launches",
     "isdf_gemm_f64",
+    "isdf_mlp_num_params",
+    "isdf_features",
+    "isdf_mlp_train_step",
+    "isdf_mlp_score",
+    "isdf_propose",
     "isdf_gemm_f64_noalloc",
     "isdf_gemm_f64_noalloc_capacity",
 ]
@@ -120,6 +128,17 @@ def load_library(build_if_missing: bool = True):
     lib.isdf_gemm_f64.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64, c_int64,
                                   c_double, c_int, c_int, c_void_p]
     lib.isdf_gemm_f64.restype = c_int
+    lib.isdf_mlp_num_params.argtypes = []
+    lib.isdf_mlp_num_params.restype = c_int
+    lib.isdf_features.argtypes = [c_void_p, c_void_p]
+    lib.isdf_features.restype = c_int
+    lib.isdf_mlp_train_step.argtypes = [c_void_p, c_void_p, c_void_p, c_int, ctypes.c_float, c_void_p, c_void_p,
+                                        c_void_p, c_int64, POINTER(ctypes.c_float), c_void_p, c_void_p]
+    lib.isdf_mlp_train_step.restype = c_int
+    lib.isdf_mlp_score.argtypes = [c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
+    lib.isdf_mlp_score.restype = c_int
+    lib.isdf_propose.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.isdf_propose.restype = c_int
     lib.isdf_gemm_f64_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64,
                                           c_int64, c_double, c_int, c_void_p]
     lib.isdf_gemm_f64_noalloc.restype = c_int
@@ -273,9 +292,14 @@ def isdf_get(plan: Plan, what: int, dst=None):
     n = int(plan._lib.isdf_get_size(plan.handle, what))
     if n == 0:
         raise IsdfError(ISDF_ERR_STATE, "not available")
+    dtype = _GET_DTYPE.get(what, np.float64)
     if dst is None:
-        dtype = np.int32 if what in (GET_NBASIS, GET_NIP_LEVEL) else (np.int64 if what == GET_PIVOTS else np.float64)
         dst = np.zeros(n, dtype=dtype)
+    if isinstance(dst, np.ndarray):
+        if dst.dtype != dtype or dst.size < n:
+            raise ValueError(f"isdf_get({what}) needs {n} elements of {np.dtype(dtype)}")
+    elif dst.numel() < n:
+        raise ValueError(f"isdf_get({what}) needs {n} elements")
     dtype = dst.dtype if isinstance(dst, np.ndarray) else None
     plan._check(plan._lib.isdf_get(plan.handle, what, _addr(dst, dtype) if dtype is not None else dst.data_ptr()))
     return dst
@@ -302,6 +326,52 @@ def isdf_gemm_f64(A, B, C, alpha=1.0, slices=5, splits=1, stream=None):
     if st != ISDF_OK:
         raise IsdfError(st, lib.isdf_last_error(None).decode())
     return C
+
+
+def _dptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def isdf_features(plan: Plan, out=None):
+    """Features (npoints x 8 float32): numpy unless a torch CUDA tensor is given."""
+    n = int(isdf_get(plan, GET_NPOINTS)[0])
+    if out is None:
+        out = np.zeros((n, 8), dtype=np.float32)
+        plan._check(plan._lib.isdf_features(plan.handle, out.ctypes.data))
+    else:
+        if out.numel() < 8 * n:
+            raise ValueError(f"features need {n} x 8 floats")
+        plan._check(plan._lib.isdf_features(plan.handle, out.data_ptr()))
+    return out
+
+
+def isdf_mlp_train_step(params, m, v, step, lr, X, y, w, grad_out=None, stream=None):
+    """One Adam step (torch CUDA float32 tensors).  Returns the loss before the step."""
+    lib = load_library()
+    loss = ctypes.c_float(0.0)
+    st = lib.isdf_mlp_train_step(params.data_ptr(), _dptr(m), _dptr(v), int(step), float(lr), X.data_ptr(),
+                                 y.data_ptr(), w.data_ptr(), int(X.shape[0]), ctypes.byref(loss), _dptr(grad_out),
+                                 c_void_p(_default_stream() if stream is None else stream))
+    if st != ISDF_OK:
+        raise IsdfError(st, lib.isdf_last_error(None).decode())
+    return loss.value
+
+
+def isdf_mlp_score(params, X, out, stream=None):
+    lib = load_library()
+    st = lib.isdf_mlp_score(params.data_ptr(), X.data_ptr(), int(X.shape[0]), out.data_ptr(),
+                            c_void_p(_default_stream() if stream is None else stream))
+    if st != ISDF_OK:
+        raise IsdfError(st, lib.isdf_last_error(None).decode())
+    return out
+
+
+def isdf_propose(plan: Plan, params, quota):
+    """Per-level quotas (sequence of nlevel ints) -> candidate pivot codes."""
+    q = np.ascontiguousarray(quota, dtype=np.int64)
+    out = np.zeros(int(q.sum()), dtype=np.int64)
+    plan._check(plan._lib.isdf_propose(plan.handle, params.data_ptr(), q.ctypes.data, out.ctypes.data))
+    return out
 
 
 def isdf_kernel_launches() -> int:

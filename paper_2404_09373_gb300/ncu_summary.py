@@ -1,6 +1,6 @@
 """Summarise an ncu launch list (gpu__time_duration.sum per launch, --csv) by kernel.
 
-Usage: python profiles/summarize_launches.py launches.csv
+Usage: python -m paper_2404_09373_gb300.ncu_summary launches.csv
 Prints per kernel: launches, total device time, share of the total.
 """
 import collections

@@ -203,6 +203,23 @@ def config(k: int):
     return sysd, C, nip_per_n * nbasis(sysd)
 
 
+def batch_cells(sigma=0.1, n_each=6, per_cell=(48, 24, 12)):
+    """The batched workload: n_each cells each of 1x1x1, 1x1x2, 1x2x2 and 2x2x2
+    diamond supercells (24 by default), seeded displacements, three grid
+    levels scaled with the cell, N_ip = 6N, n = 2 per atom.  Cell j of the
+    batch uses numpy default_rng(20240409 + 3 + 1000 j)."""
+    out = []
+    j = 0
+    for reps in ((1, 1, 1), (1, 1, 2), (1, 2, 2), (2, 2, 2)):
+        for _ in range(n_each):
+            rng = np.random.default_rng(SEED_BASE + 3 + 1000 * j)
+            sysd = make_system(reps, sigma, rng, tuple((p, p, p) for p in per_cell), LEVEL_EDGES_3)
+            C = make_orbitals(sysd, 2 * sysd["xyz"].shape[0], rng)
+            out.append((sysd, C, 6 * nbasis(sysd)))
+            j += 1
+    return out
+
+
 def small_multigrid(reps=(1, 1, 1), sigma=0.05, seed=7, per_cell=(16, 8, 4), n_occ=None, sites=DIAMOND_SITES,
                     a=A_DIAMOND):
     """A small 3-level cell for parity tests (same basis, coarser grids)."""

@@ -357,3 +357,45 @@ def test_planted_mistake_in_eq8_breaks_brute_agreement(monkeypatch):
     monkeypatch.setattr(O, "exchange", wrong)
     r = oracle.run(sysd, C, 200, tol=1e-14, reg_rel=0.0)
     assert np.max(np.abs(r["K"] - Kn)) > 1e-6
+
+
+# --------------------------------------------------------------------------- learned proposer network
+
+
+def test_mlp_gradient_matches_finite_differences():
+    from oracle import mlp
+
+    rng = np.random.default_rng(0)
+    theta = mlp.init_params(rng)
+    X = rng.standard_normal((40, mlp.N_IN))
+    y = (rng.random(40) < 0.2).astype(float)
+    w = np.where(y > 0, 4.0, 1.0)
+    L, g = mlp.loss_and_grad(theta, X, y, w)
+    h = 1e-6
+    idx = rng.choice(mlp.N_PARAMS, size=60, replace=False)
+    for i in idx:
+        e = np.zeros_like(theta)
+        e[i] = h
+        fd = (mlp.loss_and_grad(theta + e, X, y, w)[0] - mlp.loss_and_grad(theta - e, X, y, w)[0]) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_mlp_closed_form_with_zero_hidden_weights():
+    """With W1 = W2 = 0 and biases b1 = b2 = 1, every hidden unit is 1, so
+    z = sum(W3) + b3 for every sample: dL/db3 = sum_i w_i (p - y_i) / sum w."""
+    from oracle import mlp
+
+    P = {"W1": np.zeros((8, 64)), "b1": np.ones(64), "W2": np.zeros((64, 64)), "b2": np.ones(64),
+         "W3": np.full(64, 0.01), "b3": np.array([-0.3])}
+    theta = mlp.pack(P)
+    rng = np.random.default_rng(1)
+    X = rng.standard_normal((10, 8))
+    y = np.array([1, 0, 0, 1, 0, 0, 0, 1, 0, 0], dtype=float)
+    w = np.where(y > 0, 2.0, 1.0)
+    L, g = mlp.loss_and_grad(theta, X, y, w)
+    z = 0.64 - 0.3
+    p = 1 / (1 + np.exp(-z))
+    ref_b3 = np.sum(w * (p - y)) / np.sum(w)
+    assert abs(g[-1] - ref_b3) <= 1e-14
+    ref_L = -np.sum(w * (y * np.log(p) + (1 - y) * np.log(1 - p))) / np.sum(w)
+    assert abs(L - ref_L) <= 1e-14
