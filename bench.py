@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", type=int, default=1, help="1: tensor-core products, 0: plain FP64")
     ap.add_argument("--prefilter", type=int, default=1, help="exact candidate prefilter in the selection")
+    ap.add_argument("--select-block", type=int, default=64,
+                    help="speculative block size of the selection (0: one FP64 step at a time)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 comparison step")
     ap.add_argument("--batch", action="store_true",
                     help="also run the 24-cell batch (6 each of 1x1x1, 1x1x2, 1x2x2, 2x2x2, sigma 0.1) on "
@@ -199,8 +201,9 @@ def run_reference(args):
 TRAFFIC = {}
 
 
-TC_KERNELS = ("fit_zc", "fit_solve", "coulomb_V", "exchange")
-DIGIT_PRODUCTS = 15  # BF16 digit-pair products per FP64-accurate product (5 digits, s + t <= 4)
+# BF16 digit-pair products per FP64-equivalent flop: 5 digits (s + t <= 4) in
+# the fit, Coulomb and exchange products, 8 digits (s + t <= 7) in the selection
+TC_KERNELS = {"fit_zc": 15, "fit_solve": 15, "coulomb_V": 15, "exchange": 15, "select_gemm": 36}
 
 
 def roofline(kern, precision):
@@ -211,14 +214,15 @@ def roofline(kern, precision):
     launches = max(1, st["launches"])
     per_launch = st["work"] / launches
     avg_s = st["ms"] / 1e3 / launches
-    if st["unit"] == "flop" and precision == 1 and name in TC_KERNELS:
+    if st["unit"] == "flop" and name in TC_KERNELS and (precision == 1 or name == "select_gemm"):
+        dp = TC_KERNELS[name]
         achieved = per_launch / avg_s / 1e12
         peak = pk.get("bf16_tflops", 1900.0)
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst, of measured)",
                 "note": "achieved counts FP64-equivalent algorithmic flops; the tensor cores execute "
-                        f"{DIGIT_PRODUCTS} BF16 digit-pair products per flop",
-                "tensor_issue_frac": achieved * DIGIT_PRODUCTS / peak}
+                        f"{dp} BF16 digit-pair products per flop",
+                "tensor_issue_frac": achieved * dp / peak}
     elif st["unit"] == "flop":
         achieved = per_launch / avg_s / 1e12
         # FP64 SIMT contraction: ALU-bound against the nominal FP64 rate
@@ -267,7 +271,7 @@ def main():
     K_dev = torch.empty((N, N), dtype=torch.float64, device=dev)
     V_dev = torch.empty((nip, nip), dtype=torch.float64, device=dev)
     piv_dev = torch.empty(nip, dtype=torch.int64, device=dev)
-    opts = {"precision": args.precision, "prefilter": args.prefilter}
+    opts = {"precision": args.precision, "prefilter": args.prefilter, "select_block": args.select_block}
 
     def step(profile=False, o=None):
         o = opts if o is None else o
@@ -317,10 +321,12 @@ def main():
     plain = None
     if not args.no_plain and args.precision != 0:
         K_fast = K_dev.clone()
+        piv_fast = piv_dev.clone()
         r0 = step(o={"precision": 0, "prefilter": 0})
         t_isdf = r0["plan"] + r0["select"] + r0["fit"] + r0["coulomb"]
         plain = {"s_iter": t_isdf / SCF_CHARGE + r0["exchange"], "stages_s": {k: r0[k] for k in (
             "plan", "select", "fit", "coulomb", "exchange")},
+                 "pivots_equal_to_fast": bool(torch.equal(piv_dev, piv_fast)),
                  "max_abs_dK_vs_fast_Ha": float((K_dev - K_fast).abs().max()),
                  "dEx_per_atom_vs_fast_Ha": abs(r0["Ex"] - res[-1]["Ex"]) / sysd["xyz"].shape[0]}
 
@@ -417,7 +423,8 @@ def main():
         "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "bf16-sliced(f64-accurate)",
         "data": "synthetic",
         "config": {"workload": workload, "precision": "plain FP64" if args.precision == 0 else
-                   "tensor-core sliced BF16 (FP64-accurate), FP64 selection/Cholesky/E_x", "prefilter": args.prefilter,
+                   "tensor-core sliced BF16 (FP64-accurate) contractions, FP64 pivot decisions/Cholesky/E_x",
+                   "prefilter": args.prefilter, "select_block": args.select_block,
                    "l2": "inputs larger than L2 (basis values 6.4 GB, interpolation vectors > 15 GB)",
                    "parallelism": f"replicas x{world}"},
         "stages_s": {k: statistics.mean(r[k] for r in res) for k in ("plan", "select", "fit", "coulomb", "exchange")},

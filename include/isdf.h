@@ -114,7 +114,17 @@ typedef struct {
  *               full greedy one, residuals never grow) and otherwise repeats
  *               the selection with a lower tau
  *   profile     1: time every kernel family with CUDA events on the plan's
- *               stream and count its algorithmic work (isdf_profile_json)  */
+ *               stream and count its algorithmic work (isdf_profile_json)
+ *   select_block  0: the selection takes one step at a time (FP64 column of
+ *               M and factor-row products per step).  s in [1, 256]:
+ *               speculative blocks -- the s largest local maxima of the
+ *               residual on the grids form a set S, the columns that S would
+ *               produce are computed for all candidates by FP64-grade
+ *               tensor-core products (8 BF16 digits, exact level sums), and
+ *               greedy steps finish them until a pivot falls outside S.  The
+ *               pivots are the same greedy ones (every decision is the argmax
+ *               over all candidates' residuals with the same tie rule); only
+ *               the rounding of the factor columns differs.  Default 0. */
 typedef struct {
   int precision;
   double tie_rel;
@@ -124,6 +134,7 @@ typedef struct {
   int timeout_ms;
   int prefilter;
   int profile;
+  int select_block;
 } isdf_options;
 
 void isdf_options_default(isdf_options* opt);
@@ -197,9 +208,12 @@ enum {
                               isdf_fit, i.e. the Schur complement left by the
                               pivots (sum = weighted fit error^2); -1 for a
                               level without pivots                         */
-  ISDF_GET_PHI_LEVEL0 = 10 /* double[|G_l| x N_g,l] basis values of level
+  ISDF_GET_PHI_LEVEL0 = 10, /* double[|G_l| x N_g,l] basis values of level
                               0 (rows: functions of the level in index order,
                               then coarser ones); add the level index      */
+  ISDF_GET_SELECT_STATS = 6 + 16 /* int64[2]: speculative blocks and
+                              single steps of the last selection (0, 0 when
+                              options.select_block = 0)                    */
 };
 int64_t isdf_get_size(isdf_plan_t plan, int what);
 isdf_status isdf_get(isdf_plan_t plan, int what, void* dst);
@@ -258,10 +272,13 @@ isdf_status isdf_propose(isdf_plan_t plan, const float* params, const int64_t* q
  * (the paper has no counterpart; it is this library's building block):
  *   C[m*ldc + n] = alpha * sum_k A[m*lda + k] * B[n*ldb + k]
  * A, B, C are DEVICE pointers (row-major FP64).  Each operand row is scaled
- * by a power of two and split into `slices` BF16 digit planes (5 or 6, about
- * 7 bits each); digit-pair products accumulate exactly in FP32 tensor memory
- * per 1024-wide k chunk and are summed in double-float registers.  The error
- * is below 2^-(7*slices-2) * K * max_k|A[m,k]| * max_k|B[n,k]| per element.
+ * by a power of two and split into `slices` BF16 digit planes (5, 6 or 8,
+ * about 7 bits each).  With 5 or 6, digit-pair products accumulate in FP32
+ * tensor memory per 1024-wide k chunk and are summed in double-float
+ * registers; the error is below 2^-(7*slices-2) * K * max_k|A[m,k]| *
+ * max_k|B[n,k]| per element.  With 8 (FP64-grade), every digit level is
+ * summed exactly (256-wide chunks, 64-bit integer accumulation); the error is
+ * below 2^-52 * K * max_k|A[m,k]| * max_k|B[n,k]| + 2^-53 |C[m,n]|.
  * splits > 1 divides K over that many CTAs (needs splits*M*N*8 bytes of
  * scratch, allocated by the call).  Enqueued on `stream`; returns after the
  * stream is idle.  A pipeline wait that exceeds its bound returns

@@ -216,6 +216,7 @@ isdf_status validate_options(const isdf_options* o, std::string& why) {
   if (o->col_batch < 0 || o->timeout_ms < 0) return bad("col_batch and timeout_ms must be >= 0");
   if (o->prefilter != 0 && o->prefilter != 1) return bad("prefilter must be 0 or 1");
   if (o->profile != 0 && o->profile != 1) return bad("profile must be 0 or 1");
+  if (o->select_block < 0 || o->select_block > 256) return bad("select_block must be in [0, 256]");
   return ISDF_OK;
 }
 
@@ -236,6 +237,7 @@ void isdf_options_default(isdf_options* o) {
   o->timeout_ms = 0;
   o->prefilter = 0;
   o->profile = 0;
+  o->select_block = 0;
 }
 
 isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* stream, isdf_plan_t* out) {
@@ -469,6 +471,8 @@ int64_t isdf_get_size(isdf_plan_t h, int what) {
       return 1;
     case ISDF_GET_FIT_RESIDUAL:
       return p->state >= 2 ? 2 * p->nlev : 0;
+    case ISDF_GET_SELECT_STATS:
+      return p->state >= 1 ? 2 : 0;
     default:
       break;
   }
@@ -520,6 +524,10 @@ isdf_status isdf_get(isdf_plan_t h, int what, void* dst) {
     }
     case ISDF_GET_FIT_RESIDUAL:
       return put_host(p->fit_resid, sizeof(double) * 2 * p->nlev);
+    case ISDF_GET_SELECT_STATS: {
+      const int64_t v[2] = {p->sel_blocks, p->sel_plain_steps};
+      return put_host(v, sizeof(v));
+    }
     default:
       break;
   }
@@ -630,8 +638,8 @@ isdf_status isdf_propose(isdf_plan_t h, const float* params, const int64_t* quot
 
 isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
                           int64_t ldb, int64_t ldc, double alpha, int slices, int splits, void* stream) {
-  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || (slices != 5 && slices != 6) ||
-      splits < 1 || splits > 1024) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N ||
+      (slices != 5 && slices != 6 && slices != 8) || splits < 1 || splits > 1024) {
     g_plan_error = "invalid arguments to isdf_gemm_f64";
     return ISDF_ERR_ARG;
   }
@@ -674,7 +682,7 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
 
 isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K,
                                   int64_t lda, int64_t ldb, int64_t ldc, double alpha, int slices, void* stream) {
-  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || (slices != 5 && slices != 6)) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || (slices != 5 && slices != 6 && slices != 8)) {
     g_plan_error = "invalid arguments to isdf_gemm_f64_noalloc";
     return ISDF_ERR_ARG;
   }

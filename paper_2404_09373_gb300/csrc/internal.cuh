@@ -80,6 +80,7 @@ struct Plan {
   int64_t* d_piv = nullptr;    // selection-order pivot codes
   double* d_dval = nullptr;
   int sel_cap = 0;
+  int64_t sel_blocks = 0, sel_plain_steps = 0;  // speculative-block statistics of the last selection
   // fit results, level-ordered pivots
   int nip = 0;
   int poff[ISDF_MAX_LEVELS + 1] = {0};
@@ -163,6 +164,7 @@ struct OzOperand {
   void* tiles = nullptr;  // __nv_bfloat16 slices
   int* exps = nullptr;    // per-row power-of-two scale
   int64_t rows = 0, K = 0, nrt = 0, nkt = 0;
+  int64_t kst = 0;        // k-tile stride of the tile array (capacity in k tiles)
   int rt = 0, S = 0;
 };
 int oz_bn(int S);
@@ -170,6 +172,12 @@ isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, in
 void oz_free(OzOperand& op);
 // X(r, k) = mul * kw[k] * src[r*sr + k*sk]  (kw nullable)
 void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s);
+// Gathered rows (row r = source row ridx[r], ridx nullable) and a k-tile
+// window [kt0, kt1) of an operand allocated for op.kst k tiles; op.K is the
+// current K (entries at k >= op.K are zero).  exps_ready: the row scales are
+// already in op.exps (they must bound every |x| the operand will ever hold).
+void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzOperand& op, int64_t kt0, int64_t kt1,
+                 bool exps_ready, cudaStream_t s);
 // C = alpha * A B^T (A: M x K as the 128-row side, B: N x K); trans: C[n*ldc+m];
 // tri 1/2: B-side lower/upper triangular in (n, k); sym: lower-triangle tiles only;
 // splits > 1 needs work of splits*M*N doubles.  Error codes go to *err.

@@ -13,6 +13,11 @@
 // 2^-14 or less, where FP32 rounding is harmless.  After every chunk the
 // epilogue warps read the levels out (tcgen05.ld) and add them to double-float
 // (hi, lo) register accumulators; the result is formed in FP64 at the end.
+// With S = 8 (FP64-grade: 56 fraction bits per operand) the chunk is 256 k, so
+// every level's sum is an exact integer below 2^24, and the epilogue adds the
+// levels into two 64-bit integer accumulators: the product of the rounded
+// operands is then exact up to the dropped levels (below 2^-56 relative per
+// term) and one final FP64 rounding.
 //
 // Operands are pre-tiled by the slicing kernel into the canonical K-major,
 // no-swizzle UMMA layout (8x8 core matrices, LBO = 128 B along K, SBO =
@@ -127,6 +132,10 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&r)[2]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+}
+
 __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
 
 // f * 2^e as a double, built with integer operations (exact; the narrow FP64
@@ -180,13 +189,16 @@ __device__ __forceinline__ long long round_scaled(double x, int shift) {
 }
 
 // e_r: max_k |x(r,k)| < 2^e_r, x = mul * kw[k] * src[r*sr + k*sk]; one thread per row
+// (ridx: row r of the operand is source row ridx[r])
 __global__ void k_oz_rowexp_thread(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t rows, int64_t K,
-                                   const double* __restrict__ kw, double mul, int* __restrict__ exps) {
+                                   const double* __restrict__ kw, double mul, const int* __restrict__ ridx,
+                                   int* __restrict__ exps) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= rows) return;
+  const int64_t rs = ridx ? int64_t(ridx[r]) : r;
   uint64_t m = 0;
   for (int64_t k = 0; k < K; ++k) {
-    double v = src[r * sr + k * sk];
+    double v = src[rs * sr + k * sk];
     if (mul != 1.0) v *= mul;
     if (kw) v *= kw[k];
     const uint64_t key = abs_key(v);
@@ -197,12 +209,14 @@ __global__ void k_oz_rowexp_thread(const double* __restrict__ src, int64_t sr, i
 
 // same, one block per row (long rows with unit k stride)
 __global__ void k_oz_rowexp_block(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t K,
-                                  const double* __restrict__ kw, double mul, int* __restrict__ exps) {
+                                  const double* __restrict__ kw, double mul, const int* __restrict__ ridx,
+                                  int* __restrict__ exps) {
   __shared__ unsigned long long sh[256];
   const int64_t r = blockIdx.x;
+  const int64_t rs = ridx ? int64_t(ridx[r]) : r;
   uint64_t m = 0;
   for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-    double v = src[r * sr + k * sk];
+    double v = src[rs * sr + k * sk];
     if (mul != 1.0) v *= mul;
     if (kw) v *= kw[k];
     const uint64_t key = abs_key(v);
@@ -219,9 +233,13 @@ __global__ void k_oz_rowexp_block(const double* __restrict__ src, int64_t sr, in
 
 // Digits of one row and one group of 8 k values, written as 16 bytes per slice.
 // order 0: consecutive threads take consecutive rows; 1: consecutive k groups.
+// Only k tiles [kt0, kt0 + nkt) are written; tile (row tile i, k tile j) sits
+// at position i * kst + j, so an operand whose K grows can be extended in
+// place.  ridx: row r is source row ridx[r].
 __global__ void k_oz_digits(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t rows, int64_t K,
                             const double* __restrict__ kw, double mul, const int* __restrict__ exps, int S, int rt,
-                            int64_t nrt, int64_t nkt, int order, __nv_bfloat16* __restrict__ tiles) {
+                            int64_t nrt, int64_t kt0, int64_t nkt, int64_t kst, int order,
+                            const int* __restrict__ ridx, __nv_bfloat16* __restrict__ tiles) {
   const int64_t rows_pad = nrt * rt, ngrp = nkt * (kBK / 8);
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= rows_pad * ngrp) return;
@@ -233,15 +251,17 @@ __global__ void k_oz_digits(const double* __restrict__ src, int64_t sr, int64_t 
     kg = idx % ngrp;
     r = idx / ngrp;
   }
+  kg += kt0 * (kBK / 8);
   long long X[8];
   const int e = (r < rows) ? exps[r] : 0;
   const int shift = 7 * S - e;
+  const int64_t rs = (r < rows && ridx) ? int64_t(ridx[r]) : r;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int64_t k = kg * 8 + u;
     double v = 0.0;
     if (r < rows && k < K) {
-      v = src[r * sr + k * sk];
+      v = src[rs * sr + k * sk];
       if (mul != 1.0) v *= mul;
       if (kw) v *= kw[k];
     }
@@ -249,7 +269,7 @@ __global__ void k_oz_digits(const double* __restrict__ src, int64_t sr, int64_t 
   }
   const int64_t it = r / rt, rr = r % rt, jt = kg / (kBK / 8), kc = kg % (kBK / 8);
   const int64_t tile_elems = int64_t(rt) * kBK;
-  __nv_bfloat16* base = tiles + ((it * nkt + jt) * S) * tile_elems;
+  __nv_bfloat16* base = tiles + ((it * kst + jt) * S) * tile_elems;
   const int64_t inner = ((rr / 8) * 512 + kc * 128 + (rr % 8) * 16) / 2;  // element offset in a tile
   // digits from the least significant end (balanced, in [-64, 63]); top digit last
   for (int s = S - 1; s >= 0; --s) {
@@ -277,6 +297,7 @@ struct OzGemmParams {
   const int* ea;
   const int* eb;
   int64_t M, N, nkt;
+  int64_t akst, bkst;  // k-tile strides of the A and B tile arrays (>= nkt)
   int tri;     // 0 dense; 1 B-side lower (k <= n); 2 B-side upper (k >= n)
   int sym;     // compute only tiles that touch the lower triangle (n <= m)
   int splits;  // split-K factor (gridDim.z)
@@ -300,6 +321,11 @@ struct OzCfg {
   static constexpr int smem = nst * stage + 2048;  // + barriers and 1024-byte alignment slack
   static constexpr int cols = S * BN;
   static constexpr uint32_t tcols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
+  // S >= 7: every level is kept exact (chunks of 256 k keep each level's
+  // integer sum below 2^24) and summed in 64-bit integers; else double-float
+  static constexpr bool exact = S >= 7;
+  static constexpr int kc = exact ? 8 : kKcTiles;  // k tiles per chunk
+  static_assert(!exact || S == 8, "the integer epilogue splits the levels of exactly 8 digits");
   static_assert(cols <= 512, "levels x BN must fit in tensor memory");
   static_assert(nst >= 2, "need at least two pipeline stages");
   static_assert(BN % 32 == 0, "BN must split into two halves of x16 loads");
@@ -337,7 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
     kt_hi = min(kt_hi, a + per);
   }
   const int64_t nk = kt_hi - kt_lo;
-  const int64_t nchunks = (nk + kKcTiles - 1) / kKcTiles;
+  const int64_t nchunks = (nk + Cfg::kc - 1) / Cfg::kc;
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < Cfg::nst; ++i) {
@@ -379,8 +405,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
         unsigned char* sA = smem + st * Cfg::stage;
         unsigned char* sB = sA + Cfg::stageA;
         mbar_expect_tx(&full[st], Cfg::stageA + Cfg::stageB);
-        bulk_g2s(sA, gA + (mt * P.nkt + kt) * int64_t(Cfg::stageA), Cfg::stageA, &full[st]);
-        bulk_g2s(sB, gB + (nt * P.nkt + kt) * int64_t(Cfg::stageB), Cfg::stageB, &full[st]);
+        bulk_g2s(sA, gA + (mt * P.akst + kt) * int64_t(Cfg::stageA), Cfg::stageA, &full[st]);
+        bulk_g2s(sB, gB + (nt * P.bkst + kt) * int64_t(Cfg::stageB), Cfg::stageB, &full[st]);
         issued = it + 1;
       }
       // copies that were issued but never consumed must land before exit
@@ -396,7 +422,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
       for (int64_t it = 0; it < nk; ++it) {
         const int st = int(it % Cfg::nst);
         const int64_t round = it / Cfg::nst;
-        const int64_t cpos = it % kKcTiles, chunk = it / kKcTiles;
+        const int64_t cpos = it % Cfg::kc, chunk = it / Cfg::kc;
         if (cpos == 0 && chunk > 0 && !mbar_wait(acc_empty, uint32_t((chunk - 1) & 1), P.err)) {
           set_err(P.err, 12);
           *(volatile int*)abort_flag = 1;
@@ -426,7 +452,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
           }
         }
         umma_commit(&empty[st]);
-        if (cpos == kKcTiles - 1 || it == nk - 1) umma_commit(acc_full);
+        if (cpos == Cfg::kc - 1 || it == nk - 1) umma_commit(acc_full);
       }
       // all MMAs issued by this thread complete before tensor memory is freed
       umma_commit(drain);
@@ -438,55 +464,120 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
     const int half = (warp - 2) / 4;
     const int row = quarter * 32 + lane;
     constexpr int HC = BN / 2;  // columns per thread
-    float hi[HC], lo[HC];
+    const int64_t m = m0 + row;
+    if constexpr (Cfg::exact) {
+      // Per column and chunk: hi = sum_{q<4} L_q 2^{7(3-q)}, lo = sum_{q>=4}
+      // L_q 2^{7(S-1-q)} (64-bit, exact).  th accumulates hi plus the part of
+      // lo above 2^28; rem keeps lo's low 28 bits (carried into th whenever
+      // it passes 2^28), so value = th + rem 2^-28 in units of 2^-21.
+      long long th[HC];
+      uint32_t rem[HC];
 #pragma unroll
-    for (int j = 0; j < HC; ++j) hi[j] = lo[j] = 0.0f;
-    for (int64_t c = 0; c < nchunks; ++c) {
-      if (!mbar_wait(acc_full, uint32_t(c & 1), P.err)) {
-        set_err(P.err, 14);
-        *(volatile int*)abort_flag = 1;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;");
+      for (int j = 0; j < HC; ++j) th[j] = 0, rem[j] = 0u;
+      for (int64_t c = 0; c < nchunks; ++c) {
+        if (!mbar_wait(acc_full, uint32_t(c & 1), P.err)) {
+          set_err(P.err, 14);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-      for (int q = 0; q < S; ++q) {
-        const float scale = __int_as_float((127 - 7 * q) << 23);  // 2^{-7q}
+        for (int c0 = 0; c0 < HC; c0 += 2) {
+          uint32_t r[S][2];
 #pragma unroll
-        for (int c0 = 0; c0 < HC; c0 += 16) {
-          uint32_t r[16];
-          tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(q * BN + half * HC + c0), r);
+          for (int q = 0; q < S; ++q)
+            tmem_ld2(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(q * BN + half * HC + c0), r[q]);
           asm volatile("tcgen05.wait::ld.sync.aligned;");
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const float x = __uint_as_float(r[j]) * scale;
-            const float s = hi[c0 + j] + x;
-            const float bb = s - hi[c0 + j];
-            const float e = (hi[c0 + j] - (s - bb)) + (x - bb);
-            hi[c0 + j] = s;
-            lo[c0 + j] += e;
+          for (int j = 0; j < 2; ++j) {
+            long long hi = 0, lo = 0;
+#pragma unroll
+            for (int q = 0; q < S; ++q) {
+              const long long v = (long long)__float2int_rn(__uint_as_float(r[q][j]));  // exact: |v| < 2^24
+              if (q < 4)
+                hi += v * (1ll << (7 * (3 - q)));
+              else
+                lo += v * (1ll << (7 * (S - 1 - q)));
+            }
+            const long long carry = lo >> 28;  // floor; lo - carry 2^28 in [0, 2^28)
+            const uint32_t low = uint32_t(lo - carry * (1ll << 28));
+            uint32_t rr = rem[c0 + j] + low;  // < 2^29
+            th[c0 + j] += hi + carry + (long long)(rr >> 28);
+            rem[c0 + j] = rr & 0x0FFFFFFFu;
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acc_empty);
-    }
-    const int64_t m = m0 + row;
-    if (m < P.M && !*(volatile int*)abort_flag) {
-      const int ea = P.ea[m];
+      if (m < P.M && !*(volatile int*)abort_flag) {
+        const int ea = P.ea[m];
 #pragma unroll
-      for (int j = 0; j < HC; ++j) {
-        const int64_t n = n0 + half * HC + j;
-        if (n >= P.N) continue;
-        const int e = ea + P.eb[n] - 14;
-        double v = scaled_to_double(hi[j], e) + scaled_to_double(lo[j], e);  // one FP64 add
-        if (P.alpha != 1.0) v *= P.alpha;
-        if (P.splits > 1)
-          P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
-        else if (P.trans)
-          P.C[n * P.ldc + m] = v;
-        else
-          P.C[m * P.ldc + n] = v;
+        for (int j = 0; j < HC; ++j) {
+          const int64_t n = n0 + half * HC + j;
+          if (n >= P.N) continue;
+          const int e = ea + P.eb[n] - 14 - 21;
+          const double t = double(th[j]) + ldexp(double(rem[j]), -28);  // one rounding
+          double v = ldexp(t, e);
+          if (P.alpha != 1.0) v *= P.alpha;
+          if (P.splits > 1)
+            P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
+          else if (P.trans)
+            P.C[n * P.ldc + m] = v;
+          else
+            P.C[m * P.ldc + n] = v;
+        }
+      }
+    } else {
+      float hi[HC], lo[HC];
+#pragma unroll
+      for (int j = 0; j < HC; ++j) hi[j] = lo[j] = 0.0f;
+      for (int64_t c = 0; c < nchunks; ++c) {
+        if (!mbar_wait(acc_full, uint32_t(c & 1), P.err)) {
+          set_err(P.err, 14);
+          *(volatile int*)abort_flag = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          const float scale = __int_as_float((127 - 7 * q) << 23);  // 2^{-7q}
+#pragma unroll
+          for (int c0 = 0; c0 < HC; c0 += 16) {
+            uint32_t r[16];
+            tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(q * BN + half * HC + c0), r);
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              const float x = __uint_as_float(r[j]) * scale;
+              const float s = hi[c0 + j] + x;
+              const float bb = s - hi[c0 + j];
+              const float e = (hi[c0 + j] - (s - bb)) + (x - bb);
+              hi[c0 + j] = s;
+              lo[c0 + j] += e;
+            }
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(acc_empty);
+      }
+      if (m < P.M && !*(volatile int*)abort_flag) {
+        const int ea = P.ea[m];
+#pragma unroll
+        for (int j = 0; j < HC; ++j) {
+          const int64_t n = n0 + half * HC + j;
+          if (n >= P.N) continue;
+          const int e = ea + P.eb[n] - 14;
+          double v = scaled_to_double(hi[j], e) + scaled_to_double(lo[j], e);  // one FP64 add
+          if (P.alpha != 1.0) v *= P.alpha;
+          if (P.splits > 1)
+            P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
+          else if (P.trans)
+            P.C[n * P.ldc + m] = v;
+          else
+            P.C[m * P.ldc + n] = v;
+        }
       }
     }
   }
@@ -540,6 +631,7 @@ isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, in
   op.S = S;
   op.nrt = (rows + rt - 1) / rt;
   op.nkt = (K + kBK - 1) / kBK;
+  op.kst = op.nkt;
   isdf_status st = dalloc(p, &op.tiles, size_t(oz_tile_elems(rows, K, rt, S)) * 2, what);
   if (st) return st;
   return dalloc_t(p, &op.exps, size_t(op.nrt * rt), what);
@@ -555,18 +647,38 @@ void oz_free(OzOperand& op) {
 void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s) {
   const bool rowwise = sr >= sk;  // k contiguous: one block per row
   if (rowwise && op.K >= 4096) {
-    k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, sr, sk, op.K, kw, mul, op.exps);
+    k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, sr, sk, op.K, kw, mul, nullptr, op.exps);
   } else {
-    k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, kw, mul, op.exps);
+    k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, kw, mul, nullptr,
+                                                                        op.exps);
   }
   const int64_t total = op.nrt * op.rt * op.nkt * (kBK / 8);
   k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, kw, mul, op.exps, op.S, op.rt,
-                                                             op.nrt, op.nkt, rowwise ? 1 : 0,
+                                                             op.nrt, 0, op.nkt, op.kst, rowwise ? 1 : 0, nullptr,
                                                              static_cast<__nv_bfloat16*>(op.tiles));
   count_launches(2);
 }
 
-int oz_bn(int S) { return S == 5 ? 96 : 64; }
+void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzOperand& op, int64_t kt0, int64_t kt1,
+                 bool exps_ready, cudaStream_t s) {
+  if (op.rows <= 0 || kt1 <= kt0) return;
+  const bool rowwise = sr >= sk;
+  if (!exps_ready) {
+    if (rowwise && op.K >= 4096)
+      k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, sr, sk, op.K, nullptr, 1.0, ridx, op.exps);
+    else
+      k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, nullptr, 1.0,
+                                                                          ridx, op.exps);
+    count_launches(1);
+  }
+  const int64_t total = op.nrt * op.rt * (kt1 - kt0) * (kBK / 8);
+  k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, nullptr, 1.0, op.exps, op.S,
+                                                             op.rt, op.nrt, kt0, kt1 - kt0, op.kst, rowwise ? 1 : 0,
+                                                             ridx, static_cast<__nv_bfloat16*>(op.tiles));
+  count_launches(1);
+}
+
+int oz_bn(int S) { return S == 5 ? 96 : 64; }  // S levels x BN columns fill at most 512 of tensor memory
 
 void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, double alpha, int tri, int sym,
              int splits, double* work, int* err, cudaStream_t s) {
@@ -578,6 +690,8 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   P.M = A.rows;
   P.N = B.rows;
   P.nkt = A.nkt;
+  P.akst = A.kst > 0 ? A.kst : A.nkt;
+  P.bkst = B.kst > 0 ? B.kst : B.nkt;
   P.tri = tri;
   P.sym = sym;
   P.splits = splits < 1 ? 1 : splits;
@@ -590,6 +704,8 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   dim3 grid(unsigned(B.nrt), unsigned(A.nrt), unsigned(P.splits));
   if (A.S == 5)
     launch_oz<5, 96>(P, grid, s);
+  else if (A.S == 8)
+    launch_oz<8, 64>(P, grid, s);
   else
     launch_oz<6, 64>(P, grid, s);
   count_launches(1);
@@ -646,8 +762,8 @@ isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M,
     base = static_cast<unsigned char*>(g_static_addr[dev]);
   }
   OzOperand a, b;
-  a.rows = M, a.K = K, a.rt = 128, a.S = slices, a.nrt = (M + 127) / 128, a.nkt = (K + kBK - 1) / kBK;
-  b.rows = N, b.K = K, b.rt = oz_bn(slices), b.S = slices, b.nrt = (N + b.rt - 1) / b.rt, b.nkt = a.nkt;
+  a.rows = M, a.K = K, a.rt = 128, a.S = slices, a.nrt = (M + 127) / 128, a.nkt = (K + kBK - 1) / kBK, a.kst = a.nkt;
+  b.rows = N, b.K = K, b.rt = oz_bn(slices), b.S = slices, b.nrt = (N + b.rt - 1) / b.rt, b.nkt = a.nkt, b.kst = b.nkt;
   const size_t ta = round256(size_t(oz_tile_elems(M, K, a.rt, slices)) * 2);
   const size_t ea = round256(sizeof(int) * size_t(a.nrt * a.rt));
   const size_t tb = round256(size_t(oz_tile_elems(N, K, b.rt, slices)) * 2);

@@ -45,6 +45,11 @@ struct SelState {
   int err;
   int kl[ISDF_MAX_LEVELS];
   unsigned long long t0;
+  // speculative blocks
+  int final_;                // a stop rule ended the selection
+  int jpos;                  // this step's pivot: its position in the block's set S
+  int bsteps;                // steps taken in the current block
+  int kb[ISDF_MAX_LEVELS];   // factor columns per level when the block began
 };
 
 struct SelParams {
@@ -186,6 +191,7 @@ __global__ void k_sel_first(SelParams P, SelState* st) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->done = 1;
       st->skip = 1;
+      st->final_ = 1;
     }
     return;
   }
@@ -323,6 +329,373 @@ __global__ __launch_bounds__(32 * kColWarps) void k_sel_col(SelParams P, const S
   }
 }
 
+// ---------------------------------------------------------------- speculative blocks
+//
+// A block of the greedy loop first guesses a set S of up to s points that are
+// likely to be the next pivots (the largest local maxima of the residual on
+// the grids), computes the factor columns they would produce with
+// tensor-core products over all candidates,
+//   B[j][t] = w M(t, S_j) - sum_{k < kb} L[t,k] L[S_j,k]        (kb = columns so far)
+// and then takes ordinary greedy steps, each finishing its column from B with
+// the few columns added inside the block:
+//   L[t,col] = (B[pos(p)][t] - sum_{kb <= k < col} L[t,k] L[p,k]) / sqrt(d_p).
+// The pivot of every step is still the argmax over ALL candidates' exact
+// residuals (same tie rule); the block ends at the first pivot outside S.  S
+// only decides how many steps one block covers, never which point is chosen.
+
+struct BlkParams {
+  SelParams P;
+  const int* spos;                      // [ntot] position of a candidate in S's range of its level, -1 if not in S
+  const double* bm[ISDF_MAX_LEVELS];    // [s_l][nc_l]
+};
+
+struct LmParams {
+  const double* d;
+  int64_t ntot;
+  int nlev;
+  int64_t coff[ISDF_MAX_LEVELS + 1];
+  const int* cidx[ISDF_MAX_LEVELS];  // candidate -> grid index (nullptr: identity)
+  const int* gpos[ISDF_MAX_LEVELS];  // grid index -> candidate (-1: none; nullptr: identity)
+  int n[ISDF_MAX_LEVELS][3];
+};
+
+// d at the 6 periodic grid neighbours of candidate i (non-candidates count 0)
+__device__ __forceinline__ bool is_local_max(const LmParams& Q, int64_t i) {
+  const double v = Q.d[i];
+  if (!(v > 0.0)) return false;
+  int l = 0;
+  while (l + 1 < Q.nlev && i >= Q.coff[l + 1]) ++l;
+  const int64_t t = i - Q.coff[l];
+  const int64_t g = Q.cidx[l] ? Q.cidx[l][t] : t;
+  const int nx = Q.n[l][0], ny = Q.n[l][1], nz = Q.n[l][2];
+  const int x = int(g % nx), y = int((g / nx) % ny), z = int(g / (int64_t(nx) * ny));
+  const double* dl = Q.d + Q.coff[l];
+#pragma unroll
+  for (int a = 0; a < 6; ++a) {
+    int xx = x, yy = y, zz = z;
+    if (a == 0) xx = x + 1 == nx ? 0 : x + 1;
+    if (a == 1) xx = x == 0 ? nx - 1 : x - 1;
+    if (a == 2) yy = y + 1 == ny ? 0 : y + 1;
+    if (a == 3) yy = y == 0 ? ny - 1 : y - 1;
+    if (a == 4) zz = z + 1 == nz ? 0 : z + 1;
+    if (a == 5) zz = z == 0 ? nz - 1 : z - 1;
+    const int64_t gg = xx + int64_t(nx) * (yy + int64_t(ny) * zz);
+    const int64_t tt = Q.gpos[l] ? int64_t(Q.gpos[l][gg]) : gg;
+    if (tt >= 0 && dl[tt] > v) return false;
+  }
+  return true;
+}
+
+// ordered compaction of the local maxima: per-block counts, one-block scan, scatter
+__global__ void k_lm_count(LmParams Q, int* __restrict__ counts) {
+  __shared__ int sh[32];
+  const int64_t i = int64_t(blockIdx.x) * kCompactBlock + threadIdx.x;
+  const int f = (i < Q.ntot && is_local_max(Q, i)) ? 1 : 0;
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int c = 0;
+    for (int w = 0; w < kCompactBlock / 32; ++w) c += sh[w];
+    counts[blockIdx.x] = c;
+  }
+}
+
+// exclusive scan of nb counts in place; total into *total (one block of 1024)
+__global__ void k_scan_counts(int* __restrict__ counts, int64_t nb, int* __restrict__ total) {
+  __shared__ int sh[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t b0 = 0; b0 < nb; b0 += 1024) {
+    const int64_t b = b0 + threadIdx.x;
+    const int v = b < nb ? counts[b] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int add = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += add;
+      __syncthreads();
+    }
+    if (b < nb) counts[b] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_lm_write(LmParams Q, const int* __restrict__ offs, int* __restrict__ list) {
+  __shared__ int woff[32];
+  const int64_t i = int64_t(blockIdx.x) * kCompactBlock + threadIdx.x;
+  const int f = (i < Q.ntot && is_local_max(Q, i)) ? 1 : 0;
+  const unsigned b = __ballot_sync(0xffffffffu, f);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) woff[wid] = __popc(b);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0;
+    for (int w = 0; w < kCompactBlock / 32; ++w) {
+      const int c = woff[w];
+      woff[w] = a;
+      a += c;
+    }
+  }
+  __syncthreads();
+  if (f) list[offs[blockIdx.x] + woff[wid] + __popc(b & ((1u << lane) - 1u))] = int(i);
+}
+
+// The s largest residuals of the list (ties to the smallest index), by an
+// 8-bit radix select on the bit patterns (d > 0 orders like its bits).
+// Writes S in ascending candidate order: sidx (concatenated index), sg (grid
+// index), st (position in its level), per-level counts and offsets, spos.
+struct TopSOut {
+  int* sidx;
+  int* sg;
+  int* st;
+  int* scount;  // [ISDF_MAX_LEVELS + 1]: per-level counts, then the total
+  int* spos;    // [ntot]
+};
+__global__ void __launch_bounds__(1024) k_top_s(LmParams Q, const int* __restrict__ list, const int* __restrict__ nlist,
+                                                int smax, TopSOut O) {
+  __shared__ int hist[256];
+  __shared__ unsigned long long prefix, pmask;
+  __shared__ int need, take_gt;
+  __shared__ int wsum[32];
+  __shared__ int base;
+  __shared__ int lcount[ISDF_MAX_LEVELS];
+  const int n = *nlist;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    prefix = 0ull;
+    pmask = 0ull;
+    need = n < smax ? n : smax;
+    take_gt = 0;
+    base = 0;
+  }
+  if (tid < ISDF_MAX_LEVELS) lcount[tid] = 0;
+  __syncthreads();
+  const int want = need;
+  // find the threshold key T: count(key > T) < want <= count(key >= T)
+  if (want > 0 && want < n) {
+    int above = 0;  // keys above the current prefix range (already counted)
+    for (int shift = 56; shift >= 0; shift -= 8) {
+      for (int b = tid; b < 256; b += blockDim.x) hist[b] = 0;
+      __syncthreads();
+      for (int i = tid; i < n; i += blockDim.x) {
+        const unsigned long long key = (unsigned long long)__double_as_longlong(Q.d[list[i]]);
+        if ((key & pmask) == prefix) atomicAdd(&hist[(key >> shift) & 255], 1);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int acc = above, b = 255;
+        for (; b > 0; --b) {
+          if (acc + hist[b] >= want) break;
+          acc += hist[b];
+        }
+        above = acc;
+        prefix |= (unsigned long long)b << shift;
+        pmask |= 255ull << shift;
+        take_gt = acc;
+      }
+      __syncthreads();
+      above = take_gt;
+    }
+  }
+  const unsigned long long T = prefix;
+  const bool all = !(want > 0 && want < n);
+  const int n_eq_needed = all ? 0 : want - take_gt;
+  // ordered pass: keep key > T, and key == T while the equal quota lasts
+  __shared__ int eq_base;
+  if (tid == 0) eq_base = 0;
+  __syncthreads();
+  for (int i0 = 0; i0 < n; i0 += blockDim.x) {
+    const int i = i0 + tid;
+    bool gt = false, eq = false;
+    int idx = 0;
+    if (i < n) {
+      idx = list[i];
+      const unsigned long long key = (unsigned long long)__double_as_longlong(Q.d[idx]);
+      gt = all || key > T;
+      eq = !all && key == T;
+    }
+    // rank of the equals in list order
+    const unsigned be = __ballot_sync(0xffffffffu, eq);
+    const int lane = tid & 31, wid = tid >> 5;
+    if (lane == 0) wsum[wid] = __popc(be);
+    __syncthreads();
+    if (tid == 0) {
+      int a = eq_base;
+      for (int w = 0; w < 32; ++w) {
+        const int c = wsum[w];
+        wsum[w] = a;
+        a += c;
+      }
+      eq_base = a;
+    }
+    __syncthreads();
+    const int eq_rank = wsum[wid] + __popc(be & ((1u << lane) - 1u));
+    const bool sel = gt || (eq && eq_rank < n_eq_needed);
+    __syncthreads();
+    const unsigned bs = __ballot_sync(0xffffffffu, sel);
+    if (lane == 0) wsum[wid] = __popc(bs);
+    __syncthreads();
+    if (tid == 0) {
+      int a = base;
+      for (int w = 0; w < 32; ++w) {
+        const int c = wsum[w];
+        wsum[w] = a;
+        a += c;
+      }
+      base = a;
+    }
+    __syncthreads();
+    if (sel) {
+      const int pos = wsum[wid] + __popc(bs & ((1u << lane) - 1u));
+      int l = 0;
+      while (l + 1 < Q.nlev && idx >= Q.coff[l + 1]) ++l;
+      const int64_t t = idx - Q.coff[l];
+      O.sidx[pos] = idx;
+      O.st[pos] = int(t);
+      O.sg[pos] = Q.cidx[l] ? Q.cidx[l][t] : int(t);
+      atomicAdd(&lcount[l], 1);
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int l = 0; l < Q.nlev; ++l) {
+      O.scount[l] = lcount[l];
+      acc += lcount[l];
+    }
+    O.scount[ISDF_MAX_LEVELS] = acc;
+  }
+  __syncthreads();
+  // positions within each level's range
+  const int total = base;
+  for (int j = tid; j < total; j += blockDim.x) {
+    const int idx = O.sidx[j];
+    int l = 0;
+    while (l + 1 < Q.nlev && idx >= Q.coff[l + 1]) ++l;
+    int first = 0;
+    for (int q = 0; q < l; ++q) first += lcount[q];
+    O.spos[idx] = j - first;
+  }
+}
+
+__global__ void k_spos_clear(const int* __restrict__ sidx, const int* __restrict__ scount, int* __restrict__ spos) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < scount[ISDF_MAX_LEVELS]) spos[sidx[j]] = -1;
+}
+
+// B = w * aL (aL + 2 aN) - F over [s_l][nc]; in place in aL
+__global__ void k_blk_combine(double* __restrict__ aL, const double* __restrict__ aN, const double* __restrict__ F,
+                              int64_t n, double w) {
+  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < n; e += int64_t(gridDim.x) * blockDim.x) {
+    const double a = aL[e];
+    const double b = aN ? aN[e] : 0.0;
+    double v = w * (a * (a + 2.0 * b));
+    if (F) v -= F[e];
+    aL[e] = v;
+  }
+}
+
+// per-candidate power-of-two bound of the factor rows: sum_k L[t,k]^2 <= d0(t)
+__global__ void k_fac_exps(const double* __restrict__ d0c, int64_t nc, int64_t npad, int* __restrict__ exps) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t >= npad) return;
+  int e = 0;
+  if (t < nc && d0c[t] > 0.0) frexp(sqrt(d0c[t]) * (1.0 + 0x1p-20), &e);
+  exps[t] = e;
+}
+
+__global__ void k_blk_begin(SelState* st) {
+  if (threadIdx.x != 0) return;
+  st->done = st->final_ ? 1 : 0;
+  st->skip = 1;
+  st->bsteps = 0;
+  st->dmax_bits = 0ull;
+  st->first = ULLONG_MAX;
+  for (int l = 0; l < ISDF_MAX_LEVELS; ++l) st->kb[l] = st->kl[l];
+}
+
+__global__ void k_blk_pick(BlkParams B, SelState* st) {
+  const SelParams& P = B.P;
+  if (threadIdx.x != 0 || st->done) return;
+  const unsigned long long idx = st->first;
+  if (idx == ULLONG_MAX) {
+    st->done = 1;
+    st->skip = 1;
+    st->final_ = 1;
+    return;
+  }
+  const int pos = B.spos[idx];
+  if (pos < 0) {  // the greedy pivot is outside S: the block ends here
+    st->done = 1;
+    st->skip = 1;
+    return;
+  }
+  int l = 0;
+  while (l + 1 < P.nlev && (long long)idx >= P.coff[l + 1]) ++l;
+  const long long t = (long long)idx - P.coff[l];
+  const long long g = P.cidx[l] ? P.cidx[l][t] : t;
+  const double dp = P.d[idx];
+  const int k = st->k;
+  if (k == 0) st->d0 = __longlong_as_double((long long)st->dmax_bits);
+  st->lev = l;
+  st->gp = g;
+  st->tp = t;
+  st->dp = dp;
+  st->jpos = pos;
+  st->col = st->kl[l];
+  P.piv[k] = ((long long)l << kPivShift) | g;
+  P.dval[k] = dp;
+  st->kl[l] += 1;
+  st->k = k + 1;
+  st->bsteps += 1;
+  st->skip = 0;
+  st->dmax_bits = 0ull;
+  st->first = ULLONG_MAX;
+  if (P.timeout_ns) {
+    const unsigned long long now = globaltimer();
+    if (k == 0) {
+      st->t0 = now;
+    } else if (now - st->t0 > P.timeout_ns) {
+      st->err = ISDF_ERR_TIMEOUT;
+      st->done = 1;
+      st->final_ = 1;
+    }
+  }
+}
+
+// column of this step from B and the block's earlier columns; residual update
+__global__ void __launch_bounds__(256) k_blk_col(BlkParams B, const SelState* st) {
+  if (st->skip) return;
+  __shared__ double lp[256];  // L[p, kb..col) (a block has at most 256 steps)
+  const SelParams& P = B.P;
+  const int l = st->lev;
+  const int col = st->col, kb = st->kb[l];
+  const int nb = col - kb;
+  const int64_t nc = P.nc[l], tp = st->tp;
+  const double* __restrict__ fac = P.fac[l];
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) lp[i] = fac[int64_t(kb + i) * nc + tp];
+  __syncthreads();
+  const double sq = sqrt(st->dp);
+  const double* __restrict__ bcol = B.bm[l] + int64_t(st->jpos) * nc;
+  double* __restrict__ facw = P.fac[l];
+  double* __restrict__ d = P.d + P.coff[l];
+  for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nc; t += int64_t(gridDim.x) * blockDim.x) {
+    double s0 = 0.0;
+    for (int i = 0; i < nb; ++i) s0 = fma(fac[int64_t(kb + i) * nc + t], lp[i], s0);
+    double v = (bcol[t] - s0) / sq;
+    if (t == tp) v = sq;
+    facw[int64_t(col) * nc + t] = v;
+    d[t] = (t == tp) ? 0.0 : d[t] - v * v;
+  }
+}
+
 }  // namespace
 
 namespace {
@@ -452,6 +825,297 @@ isdf_status select_loop(Plan* p, int nip, double tol, const double* d0full, int*
   return ISDF_OK;
 }
 
+__global__ void k_scatter_pos(const int* __restrict__ cidx, int64_t nc, int* __restrict__ gpos) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < nc) gpos[cidx[t]] = int(t);
+}
+
+constexpr int kSlices = 8;  // FP64-grade sliced products for the selection
+
+// Speculative-block form of select_loop (same result: every pivot is the
+// greedy one).  Per block: S from the residual's local maxima, three
+// tensor-core products per level for the columns of S, then up to s greedy
+// steps replayed from a CUDA graph; a step whose pivot lies outside S ends the
+// block (if it was the block's first step, one ordinary step is taken).
+isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0full, int* const* cidx,
+                                const int64_t* nc, int* nfound, int* kl_out) {
+  cudaStream_t s = p->stream;
+  isdf_status st = ISDF_OK;
+  const int smax = p->opt.select_block;
+  const int nlev = p->nlev;
+  SelParams P{};
+  P.nlev = nlev;
+  P.coff[0] = 0;
+  int nGmax = 1;
+  for (int l = 0; l < nlev; ++l) {
+    P.coff[l + 1] = P.coff[l] + nc[l];
+    P.cidx[l] = cidx[l];
+    P.nc[l] = nc[l];
+  }
+  P.ntot = P.coff[nlev];
+  dfree(p->d_diag);
+  p->d_diag = nullptr;
+  if ((st = dalloc_t(p, &p->d_diag, size_t(std::max<int64_t>(P.ntot, 1)), "residual diagonal"))) return st;
+  P.d = p->d_diag;
+
+  struct LevBuf {
+    OzOperand aL, aN, aF, bL, bN, bF;
+    double *cL = nullptr, *cN = nullptr, *cF = nullptr;
+    int* gpos = nullptr;
+    int sliced = 0;
+  } lb[ISDF_MAX_LEVELS];
+  int *counts = nullptr, *nlist = nullptr, *list = nullptr, *sidx = nullptr, *sg = nullptr, *stp = nullptr,
+      *scount = nullptr, *spos = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  auto cleanup = [&]() {
+    for (int l = 0; l < nlev; ++l) {
+      oz_free(lb[l].aL), oz_free(lb[l].aN), oz_free(lb[l].aF);
+      oz_free(lb[l].bL), oz_free(lb[l].bN), oz_free(lb[l].bF);
+      dfree(lb[l].cL), dfree(lb[l].cN), dfree(lb[l].cF), dfree(lb[l].gpos);
+      dfree(p->lev[l].fac);
+      p->lev[l].fac = nullptr;
+    }
+    dfree(counts), dfree(nlist), dfree(list), dfree(sidx), dfree(sg), dfree(stp), dfree(scount), dfree(spos);
+    if (exec) cudaGraphExecDestroy(exec);
+  };
+  auto bail = [&](isdf_status r) {
+    cleanup();
+    return r;
+  };
+
+  // ---- set-up: residual, factor storage, candidate-side operands
+  LmParams Q{};
+  Q.d = P.d;
+  Q.nlev = nlev;
+  Q.ntot = P.ntot;
+  for (int l = 0; l <= nlev; ++l) Q.coff[l] = P.coff[l];
+  for (int l = 0; l < nlev; ++l) {
+    Level& lv = p->lev[l];
+    LevBuf& b = lb[l];
+    dfree(lv.fac);
+    lv.fac = nullptr;
+    lv.fac_cap = std::min<int64_t>(nip, nc[l]);
+    if ((st = dalloc_t(p, &lv.fac, size_t(std::max<int64_t>(lv.fac_cap * nc[l], 1)), "selection factor columns")))
+      return bail(st);
+    P.fac[l] = lv.fac;
+    P.phi[l] = lv.phi;
+    P.ng[l] = lv.ng;
+    P.nL[l] = lv.nL;
+    P.nG[l] = lv.nG;
+    P.w[l] = lv.w;
+    nGmax = std::max(nGmax, lv.nG);
+    Q.cidx[l] = cidx[l];
+    for (int a = 0; a < 3; ++a) Q.n[l][a] = lv.n[a];
+    if (!nc[l]) continue;
+    k_gather_diag<<<unsigned((nc[l] + 255) / 256), 256, 0, s>>>(d0full + p->off[l], cidx[l], nc[l], p->d_diag + P.coff[l]);
+    count_launches(1);
+    if (cidx[l]) {
+      if ((st = dalloc_t(p, &b.gpos, size_t(lv.ng), "grid-to-candidate map"))) return bail(st);
+      cudaMemsetAsync(b.gpos, 0xFF, sizeof(int) * size_t(lv.ng), s);
+      k_scatter_pos<<<unsigned((nc[l] + 255) / 256), 256, 0, s>>>(cidx[l], nc[l], b.gpos);
+      count_launches(1);
+    }
+    Q.gpos[l] = b.gpos;
+    const int bn = oz_bn(kSlices);
+    if ((st = oz_alloc(p, b.aL, nc[l], std::max(lv.nL, 1), 128, kSlices, "selection slices")) ||
+        (st = oz_alloc(p, b.bL, smax, std::max(lv.nL, 1), bn, kSlices, "selection slices")) ||
+        (st = oz_alloc(p, b.aF, nc[l], lv.fac_cap, 128, kSlices, "selection slices")) ||
+        (st = oz_alloc(p, b.bF, smax, lv.fac_cap, bn, kSlices, "selection slices")) ||
+        (st = dalloc_t(p, &b.cL, size_t(smax) * nc[l], "selection columns")) ||
+        (st = dalloc_t(p, &b.cF, size_t(smax) * nc[l], "selection columns")))
+      return bail(st);
+    if (lv.nN > 0 && ((st = oz_alloc(p, b.aN, nc[l], lv.nN, 128, kSlices, "selection slices")) ||
+                      (st = oz_alloc(p, b.bN, smax, lv.nN, bn, kSlices, "selection slices")) ||
+                      (st = dalloc_t(p, &b.cN, size_t(smax) * nc[l], "selection columns"))))
+      return bail(st);
+    {
+      Prof pr(p, "select_slice", 8.0 * double(nc[l]) * lv.nG, "byte", 4);
+      if (lv.nL > 0) oz_slice_ex(lv.phi, 1, lv.ng, cidx[l], b.aL, 0, b.aL.nkt, false, s);
+      if (lv.nN > 0) oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, cidx[l], b.aN, 0, b.aN.nkt, false, s);
+      // factor rows are bounded by sqrt(d0): fixed scales, columns appended in place
+      k_fac_exps<<<unsigned((b.aF.nrt * 128 + 255) / 256), 256, 0, s>>>(p->d_diag + P.coff[l], nc[l], b.aF.nrt * 128,
+                                                                         b.aF.exps);
+      count_launches(1);
+    }
+    b.aF.K = 0;
+    b.aF.nkt = 0;
+  }
+  P.piv = p->d_piv;
+  P.dval = p->d_dval;
+  P.nip = nip;
+  P.tol = tol;
+  P.tie_rel = p->opt.tie_rel;
+  P.tie_abs = p->opt.tie_abs;
+  P.timeout_ns = (unsigned long long)p->opt.timeout_ms * 1000000ull;
+  const int64_t nbk = (P.ntot + kCompactBlock - 1) / kCompactBlock;
+  if ((st = dalloc_t(p, &counts, size_t(std::max<int64_t>(nbk, 1)), "block counts")) ||
+      (st = dalloc_t(p, &nlist, 1, "list size")) ||
+      (st = dalloc_t(p, &list, size_t(std::max<int64_t>(P.ntot, 1)), "local maxima")) ||
+      (st = dalloc_t(p, &sidx, size_t(smax), "speculative set")) || (st = dalloc_t(p, &sg, size_t(smax), "speculative set")) ||
+      (st = dalloc_t(p, &stp, size_t(smax), "speculative set")) ||
+      (st = dalloc_t(p, &scount, size_t(ISDF_MAX_LEVELS + 1), "speculative set")) ||
+      (st = dalloc_t(p, &spos, size_t(std::max<int64_t>(P.ntot, 1)), "speculative positions")))
+    return bail(st);
+  cudaMemsetAsync(spos, 0xFF, sizeof(int) * size_t(std::max<int64_t>(P.ntot, 1)), s);
+  BlkParams BP{};
+  BP.P = P;
+  BP.spos = spos;
+  for (int l = 0; l < nlev; ++l) BP.bm[l] = lb[l].cL;
+  TopSOut O{sidx, sg, stp, scount, spos};
+
+  SelState h{};
+  h.dmax_bits = 0;
+  h.first = ULLONG_MAX;
+  h.skip = 1;
+  if ((st = cuda_check(p, cudaMemcpyAsync(p->d_selstate, &h, sizeof(h), cudaMemcpyHostToDevice, s), "state init")))
+    return bail(st);
+  SelState* dst = static_cast<SelState*>(p->d_selstate);
+  const size_t smem = sizeof(double) * (size_t((nGmax + 1) & ~1) + 3 * kColWarps * 32);
+  if (smem > 48 * 1024 &&
+      (st = cuda_check(p, cudaFuncSetAttribute(k_sel_col, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                       "smem attribute")))
+    return bail(st);
+  int dev = 0, nsm = 152, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sel_col, 32 * kColWarps, smem);
+  const unsigned red_blocks = unsigned(nsm) * 4;
+  const unsigned col_blocks = per_sm > 0 ? unsigned(per_sm * nsm) : kColBlocks;
+  auto block_step = [&]() {
+    k_sel_max<<<red_blocks, 256, 0, s>>>(P, dst);
+    k_sel_first<<<red_blocks, 256, 0, s>>>(P, dst);
+    k_blk_pick<<<1, 32, 0, s>>>(BP, dst);
+    k_blk_col<<<unsigned(nsm) * 8, 256, 0, s>>>(BP, dst);
+  };
+  if (s != nullptr) {
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      for (int i = 0; i < smax; ++i) block_step();
+      if (cudaStreamEndCapture(s, &graph) != cudaSuccess || !graph || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess)
+        exec = nullptr;
+      if (graph) cudaGraphDestroy(graph);
+    }
+    cudaGetLastError();
+  }
+
+  double gemm_flop = 0.0;
+  int64_t nblocks = 0, nplain = 0;
+  std::vector<int> hcount(ISDF_MAX_LEVELS + 1);
+  while (true) {
+    // ---- 1. the speculative set S
+    {
+      Prof pr(p, "select_spec", double(P.ntot) * 8.0, "byte", 4);
+      k_lm_count<<<unsigned(std::max<int64_t>(nbk, 1)), kCompactBlock, 0, s>>>(Q, counts);
+      k_scan_counts<<<1, 1024, 0, s>>>(counts, nbk, nlist);
+      k_lm_write<<<unsigned(std::max<int64_t>(nbk, 1)), kCompactBlock, 0, s>>>(Q, counts, list);
+      k_top_s<<<1, 1024, 0, s>>>(Q, list, nlist, smax, O);
+      count_launches(4);
+    }
+    cudaMemcpyAsync(hcount.data(), scount, sizeof(int) * hcount.size(), cudaMemcpyDeviceToHost, s);
+    if ((st = cuda_check(p, cudaStreamSynchronize(s), "speculative set"))) return bail(st);
+    // ---- 2. columns of S: three products per level, then B = w M - F
+    int soff = 0;
+    for (int l = 0; l < nlev; ++l) {
+      const int sl = hcount[l];
+      if (!sl) continue;
+      Level& lv = p->lev[l];
+      LevBuf& b = lb[l];
+      const int kb = h.kl[l];
+      const double flop = 2.0 * double(nc[l]) * sl * (lv.nL + lv.nN + kb);
+      gemm_flop += flop;
+      Prof pr(p, "select_gemm", flop, "flop", 3);
+      auto setrows = [&](OzOperand& op, int rows) {
+        op.rows = rows;
+        op.nrt = (rows + op.rt - 1) / op.rt;
+      };
+      setrows(b.bL, sl);
+      oz_slice_ex(lv.phi, 1, lv.ng, sg + soff, b.bL, 0, b.bL.nkt, false, s);
+      oz_gemm(b.aL, b.bL, b.cL, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      if (lv.nN > 0) {
+        setrows(b.bN, sl);
+        oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, sg + soff, b.bN, 0, b.bN.nkt, false, s);
+        oz_gemm(b.aN, b.bN, b.cN, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      }
+      if (kb > 0) {
+        setrows(b.bF, sl);
+        b.bF.K = kb;
+        b.bF.nkt = (kb + 31) / 32;
+        oz_slice_ex(lv.fac, 1, nc[l], stp + soff, b.bF, 0, b.bF.nkt, false, s);
+        b.aF.K = kb;
+        b.aF.nkt = (kb + 31) / 32;
+        oz_gemm(b.aF, b.bF, b.cF, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      }
+      const int64_t n = int64_t(sl) * nc[l];
+      k_blk_combine<<<unsigned(std::min<int64_t>((n + 255) / 256, int64_t(nsm) * 16)), 256, 0, s>>>(
+          b.cL, lv.nN > 0 ? b.cN : nullptr, kb > 0 ? b.cF : nullptr, n, lv.w);
+      count_launches(1);
+      soff += sl;
+    }
+    // ---- 3. greedy steps of this block
+    {
+      Prof pr(p, "select_steps", 0.0, "byte", 4ll * smax);
+      k_blk_begin<<<1, 32, 0, s>>>(dst);
+      if (exec)
+        cudaGraphLaunch(exec, s);
+      else
+        for (int i = 0; i < smax; ++i) block_step();
+      k_spos_clear<<<unsigned((smax + 255) / 256), 256, 0, s>>>(sidx, scount, spos);
+      count_launches(2 + 4ll * smax);
+    }
+    ++nblocks;
+    if ((st = cuda_check(p, cudaGetLastError(), "selection kernels"))) return bail(st);
+    int kl_before[ISDF_MAX_LEVELS];
+    for (int l = 0; l < nlev; ++l) kl_before[l] = h.kl[l];
+    cudaMemcpyAsync(&h, dst, sizeof(h), cudaMemcpyDeviceToHost, s);
+    if ((st = cuda_check(p, cudaStreamSynchronize(s), "block state"))) return bail(st);
+    if (p->opt.profile && !p->pend.empty() && p->pend.back().name == "select_steps") {
+      // algorithmic bytes of the block's steps: two passes over the residual
+      // (max, tie rule), then per candidate of the pivot's level the column of
+      // B, the block's earlier columns, the new column and the residual
+      double bytes = 0.0;
+      for (int l = 0; l < nlev; ++l) {
+        const double dk = h.kl[l] - kl_before[l], n = double(nc[l]);
+        bytes += dk * (16.0 * double(P.ntot) + 32.0 * n) + 8.0 * n * dk * (dk - 1.0) / 2.0;
+      }
+      p->pend.back().work = bytes;
+    }
+    if (h.err || h.final_ || h.k >= nip) break;
+    if (h.bsteps == 0) {
+      // the greedy pivot was not in S: one ordinary step
+      Prof pr(p, "select_loop", 0.0, "flop", 4);
+      k_blk_begin<<<1, 32, 0, s>>>(dst);
+      k_sel_max<<<red_blocks, 256, 0, s>>>(P, dst);
+      k_sel_first<<<red_blocks, 256, 0, s>>>(P, dst);
+      k_sel_pick<<<1, 32, 0, s>>>(P, dst);
+      k_sel_col<<<col_blocks, 256, smem, s>>>(P, dst);
+      count_launches(5);
+      ++nplain;
+      cudaMemcpyAsync(&h, dst, sizeof(h), cudaMemcpyDeviceToHost, s);
+      if ((st = cuda_check(p, cudaStreamSynchronize(s), "plain step"))) return bail(st);
+      if (h.err || h.final_ || h.k >= nip) break;
+    }
+    // ---- 4. digits of the new factor columns (whole k tiles from the first changed one)
+    {
+      Prof pr(p, "select_slice", 0.0, "byte", nlev);
+      for (int l = 0; l < nlev; ++l) {
+        LevBuf& b = lb[l];
+        if (h.kl[l] <= b.sliced) continue;
+        b.aF.K = h.kl[l];
+        oz_slice_ex(p->lev[l].fac, 1, nc[l], nullptr, b.aF, b.sliced / 32, (h.kl[l] + 31) / 32, true, s);
+        b.sliced = h.kl[l];
+      }
+    }
+  }
+  if ((st = oz_check(p))) return bail(st);
+  *nfound = h.k;
+  for (int l = 0; l < nlev; ++l) kl_out[l] = h.kl[l];
+  p->sel_blocks = nblocks;
+  p->sel_plain_steps = nplain;
+  cleanup();
+  if (h.err == ISDF_ERR_TIMEOUT) return fail(p, ISDF_ERR_TIMEOUT, "selection loop exceeded options.timeout_ms");
+  return ISDF_OK;
+}
+
 }  // namespace
 
 isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>* cand, int* nfound) {
@@ -486,6 +1150,10 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     return r;
   };
   int kl[ISDF_MAX_LEVELS];
+  auto loop = [&](int* const* ci, const int64_t* n) {
+    return p->opt.select_block > 0 ? select_loop_blocked(p, nip, tol, d0, ci, n, nfound, kl)
+                                   : select_loop(p, nip, tol, d0, ci, n, nfound, kl);
+  };
   if (cand) {
     // caller-given candidates: ascending, unique per level
     std::vector<std::vector<int>> per(p->nlev);
@@ -501,11 +1169,11 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
         return done(st);
     }
     if ((st = cuda_check(p, cudaStreamSynchronize(s), "copy candidates"))) return done(st);
-    return done(select_loop(p, nip, tol, d0, cidx, nc, nfound, kl));
+    return done(loop(cidx, nc));
   }
   if (!p->opt.prefilter) {
     for (int l = 0; l < p->nlev; ++l) nc[l] = p->lev[l].ng;
-    return done(select_loop(p, nip, tol, d0, cidx, nc, nfound, kl));
+    return done(loop(cidx, nc));
   }
   // exact prefilter: tau relative to the largest initial residual d_0
   unsigned long long* dmax_slot = nullptr;
@@ -564,9 +1232,9 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     for (int l = 0; l < p->nlev; ++l) all_kept = all_kept && nc[l] == p->lev[l].ng;
     if (all_kept) {  // nothing dropped: this is the full greedy run
       free_cidx();
-      return done(select_loop(p, nip, tol, d0, cidx, nc, nfound, kl));
+      return done(loop(cidx, nc));
     }
-    st = select_loop(p, nip, tol, d0, cidx, nc, nfound, kl);
+    st = loop(cidx, nc);
     if (st || tau <= 0.0) return done(st);
     // certificate: every step's tie threshold stayed above tau
     std::vector<double> dv(*nfound);
