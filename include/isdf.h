@@ -206,8 +206,8 @@ enum {
                               and the summed residual w (M(g,g) - M(g,P)
                               M_PP^-1 M(P,g)) over all grid points after
                               isdf_fit, i.e. the Schur complement left by the
-                              pivots (sum = weighted fit error^2); -1 for a
-                              level without pivots                         */
+                              pivots (sum = weighted fit error^2); on a level
+                              without pivots, of w M(g,g)                  */
   ISDF_GET_PHI_LEVEL0 = 10, /* double[|G_l| x N_g,l] basis values of level
                               0 (rows: functions of the level in index order,
                               then coarser ones); add the level index      */
@@ -266,6 +266,16 @@ isdf_status isdf_mlp_score(const float* params, const float* X, int64_t n, float
  * 0 <= quota[l] <= N_g,l.  params: device.  cand_out: host or device, sum of
  * the quotas int64. */
 isdf_status isdf_propose(isdf_plan_t plan, const float* params, const int64_t* quota, int64_t* cand_out);
+
+/* After isdf_fit: on every level l the quota[l] grid points with the largest
+ * fit residual w (M(g,g) - M(g,P) M_PP^-1 M(P,g)) -- the diagonal of the
+ * Schur complement the pivots leave (Section II.A, Eq. 2 and 3), i.e. the
+ * points the current pivots represent worst -- as pivot codes in ascending
+ * (level, g) order, ties to the smallest g.  Used to repair a candidate list
+ * that missed important points.  quota: host, nlevel entries, 0 <= quota[l]
+ * <= N_g,l.  cand_out: host or device, sum of the quotas int64.  Before
+ * isdf_fit: ISDF_ERR_STATE. */
+isdf_status isdf_propose_residual(isdf_plan_t plan, const int64_t* quota, int64_t* cand_out);
 
 /* FP64-accurate matrix product on the tensor cores -- the contraction
  * kernel behind options.precision = 1, exposed for verification and reuse

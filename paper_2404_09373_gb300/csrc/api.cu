@@ -116,6 +116,7 @@ void free_plan(Plan* p) {
     dfree(lv.fac);
     dfree(lv.d_pg);
     dfree(lv.xiT);
+    dfree(lv.resid);
     dfree(lv.spec);
     lv = Level();
   }
@@ -631,6 +632,32 @@ isdf_status isdf_propose(isdf_plan_t h, const float* params, const int64_t* quot
   if (!dev && (st = dalloc_t(p, &stage, size_t(ncand), "candidates"))) return st;
   if (!dev) d = stage;
   st = learn_propose(p, params, q.data(), d);
+  if (!st && !dev) st = from_device(p, cand_out, stage, size_t(ncand), true);
+  dfree(stage);
+  return st;
+}
+
+isdf_status isdf_propose_residual(isdf_plan_t h, const int64_t* quota, int64_t* cand_out) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (!quota || !cand_out) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_propose_residual");
+  if (p->state < 2) return fail(p, ISDF_ERR_STATE, "isdf_propose_residual needs isdf_fit first");
+  std::vector<int64_t> q(p->nlev);
+  int64_t ncand = 0;
+  for (int l = 0; l < p->nlev; ++l) {
+    if (quota[l] < 0 || quota[l] > p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "quota out of range");
+    if (quota[l] > 0 && !p->lev[l].resid) return fail(p, ISDF_ERR_STATE, "no fit residual on this level");
+    q[l] = quota[l];
+    ncand += q[l];
+  }
+  if (ncand < 1) return fail(p, ISDF_ERR_ARG, "empty candidate quota");
+  int64_t* d = cand_out;
+  int64_t* stage = nullptr;
+  const bool dev = is_device_ptr(cand_out);
+  isdf_status st = ISDF_OK;
+  if (!dev && (st = dalloc_t(p, &stage, size_t(ncand), "candidates"))) return st;
+  if (!dev) d = stage;
+  st = learn_propose_residual(p, q.data(), d);
   if (!st && !dev) st = from_device(p, cand_out, stage, size_t(ncand), true);
   dfree(stage);
   return st;

@@ -18,11 +18,44 @@
 // one real GEMM over interleaved (Re, Im) with a per-k weight.
 #include <algorithm>
 #include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
 
 #include "internal.cuh"
 
 namespace isdf {
 namespace {
+
+// Process-wide pool of cuFFT plans keyed by (device, nz, ny, nx, batch):
+// creating a plan allocates its work area and synchronises the device, so a
+// plan is created once and checked out by one caller at a time (concurrent
+// library plans on other streams get their own handles).  Handles live until
+// the process exits.
+using FftKey = std::tuple<int, int, int, int, int>;
+std::mutex g_fft_mu;
+std::multimap<FftKey, cufftHandle> g_fft_free;
+
+cufftResult fft_acquire(const FftKey& key, cufftHandle* h) {
+  {
+    std::lock_guard<std::mutex> lock(g_fft_mu);
+    auto it = g_fft_free.find(key);
+    if (it != g_fft_free.end()) {
+      *h = it->second;
+      g_fft_free.erase(it);
+      return CUFFT_SUCCESS;
+    }
+  }
+  int dims[3] = {std::get<1>(key), std::get<2>(key), std::get<3>(key)};
+  const int ng = dims[0] * dims[1] * dims[2];
+  const int nq = dims[0] * dims[1] * (dims[2] / 2 + 1);
+  return cufftPlanMany(h, 3, dims, nullptr, 1, ng, nullptr, 1, nq, CUFFT_D2Z, std::get<4>(key));
+}
+
+void fft_release(const FftKey& key, cufftHandle h) {
+  std::lock_guard<std::mutex> lock(g_fft_mu);
+  g_fft_free.emplace(key, h);
+}
 
 __global__ void k_coul_weights(int nx, int ny, int nz, double Lx, double Ly, double Lz, double pref, int same,
                                double* __restrict__ wt2) {
@@ -163,28 +196,32 @@ isdf_status coulomb_run(Plan* p) {
     lv.nq = int64_t(lv.nh[0]) * lv.nh[1] * lv.nh[2];
     if (lv.k == 0) continue;
     if ((st = dalloc_t(p, &lv.spec, size_t(lv.k) * lv.nq, "spectra"))) return st;
-    int batch = p->opt.col_batch > 0 ? p->opt.col_batch : 64;
+    // batches of about 256 MB of input (at least one vector, at most 64)
+    int batch = p->opt.col_batch > 0 ? p->opt.col_batch
+                                     : int(std::max<int64_t>(1, std::min<int64_t>(64, (int64_t(256) << 20) / (8 * lv.ng))));
     if (batch > lv.k) batch = lv.k;
-    int dims[3] = {lv.n[2], lv.n[1], lv.n[0]};
+    if (p->fault == "fft_plan") return fail(p, ISDF_ERR_CUFFT, "cufftPlanMany failed (injected)");
+    int dev = 0;
+    cudaGetDevice(&dev);
     Prof pr(p, "coulomb_fft", double(lv.k) * (8.0 * double(lv.ng) + 16.0 * double(lv.nq)), "byte", 0);
     for (int b0 = 0; b0 < lv.k;) {
       const int nb = (lv.k - b0 >= batch) ? batch : lv.k - b0;
+      const FftKey key{dev, lv.n[2], lv.n[1], lv.n[0], nb};
       cufftHandle h = 0;
-      cufftResult r = CUFFT_SUCCESS;
-      if (p->fault == "fft_plan") r = CUFFT_ALLOC_FAILED;
-      if (r == CUFFT_SUCCESS)
-        r = cufftPlanMany(&h, 3, dims, nullptr, 1, int(lv.ng), nullptr, 1, int(lv.nq), CUFFT_D2Z, nb);
+      cufftResult r = fft_acquire(key, &h);
       if (r != CUFFT_SUCCESS) return fail(p, ISDF_ERR_CUFFT, "cufftPlanMany failed (" + std::to_string(int(r)) + ")");
-      cufftSetStream(h, s);
-      // run every full batch with this plan, then the remainder with its own
+      r = cufftSetStream(h, s);
+      // every full batch with this plan, then the remainder with its own
       const int nfull = (lv.k - b0) / nb;
       for (int c = 0; c < nfull && r == CUFFT_SUCCESS; ++c) {
         r = cufftExecD2Z(h, lv.xiT + int64_t(b0) * lv.ng, reinterpret_cast<cufftDoubleComplex*>(lv.spec + int64_t(b0) * lv.nq));
         b0 += nb;
       }
-      cudaStreamSynchronize(s);
-      cufftDestroy(h);
+      // the handle goes back to the pool only once its work on this stream is done
+      const cudaError_t e = cudaStreamSynchronize(s);
+      fft_release(key, h);
       if (r != CUFFT_SUCCESS) return fail(p, ISDF_ERR_CUFFT, "cufftExecD2Z failed (" + std::to_string(int(r)) + ")");
+      if ((st = cuda_check(p, e, "FFT"))) return st;
     }
   }
   // 2. V blocks

@@ -128,7 +128,8 @@ isdf_status fit_solve_tc(Plan* p, int k, double* zct, double* y, const double* l
 // with Y = R^-1 (ZC^T)^T: the Schur complement left after the pivots; max and
 // sum (= the weighted Frobenius fit error^2) go to out[0], out[1]
 __global__ void k_fit_residual(const double* __restrict__ phi, int64_t ng, int nL, int nG, double w,
-                               const double* __restrict__ y, int k, unsigned long long* out_max, double* out_sum) {
+                               const double* __restrict__ y, int k, unsigned long long* out_max, double* out_sum,
+                               float* __restrict__ rpt) {
   double mx = 0.0, sm = 0.0;
   for (int64_t g = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; g < ng; g += int64_t(gridDim.x) * blockDim.x) {
     double aL = 0.0, aN = 0.0, q = 0.0;
@@ -136,6 +137,7 @@ __global__ void k_fit_residual(const double* __restrict__ phi, int64_t ng, int n
     for (int r = nL; r < nG; ++r) aN = fma(phi[int64_t(r) * ng + g], phi[int64_t(r) * ng + g], aN);
     for (int j = 0; j < k; ++j) q = fma(y[int64_t(j) * ng + g], y[int64_t(j) * ng + g], q);
     const double res = w * (aL * (aL + 2.0 * aN) - q);
+    if (rpt) rpt[g] = float(res);
     mx = fmax(mx, res);
     sm += res;
   }
@@ -158,8 +160,23 @@ isdf_status fit_run(Plan* p) {
     Level& lv = p->lev[l];
     dfree(lv.xiT);
     lv.xiT = nullptr;
-    p->fit_resid[2 * l] = p->fit_resid[2 * l + 1] = -1.0;  // not computed (no pivots on the level)
-    if (lv.k == 0) continue;
+    dfree(lv.resid);
+    lv.resid = nullptr;
+    if ((st = dalloc_t(p, &lv.resid, size_t(lv.ng), "fit residual"))) return st;
+    if (lv.k == 0) {
+      // no pivots: the residual is the whole diagonal w M(g,g)
+      double* scr = nullptr;
+      if ((st = dalloc_t(p, &scr, 2, "residual statistics"))) return st;
+      cudaMemsetAsync(scr, 0, 2 * sizeof(double), s);
+      k_fit_residual<<<152 * 4, 256, 0, s>>>(lv.phi, lv.ng, lv.nL, lv.nG, lv.w, nullptr, 0,
+                                             reinterpret_cast<unsigned long long*>(scr), scr + 1, lv.resid);
+      count_launches(1);
+      cudaMemcpyAsync(&p->fit_resid[2 * l], scr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+      st = cuda_check(p, cudaStreamSynchronize(s), "fit residual");
+      dfree(scr);
+      if (st) return st;
+      continue;
+    }
     const int k = lv.k;
     const int64_t ng = lv.ng;
     double *phiP = nullptr, *zct = nullptr, *y = nullptr, *cc = nullptr, *li = nullptr, *scr = nullptr;
@@ -255,7 +272,7 @@ isdf_status fit_run(Plan* p) {
       unsigned long long* rmax = reinterpret_cast<unsigned long long*>(scr);
       double* rsum = scr + 1;
       cudaMemsetAsync(scr, 0, 2 * sizeof(double), s);
-      k_fit_residual<<<152 * 4, 256, 0, s>>>(lv.phi, ng, lv.nL, lv.nG, lv.w, y, k, rmax, rsum);
+      k_fit_residual<<<152 * 4, 256, 0, s>>>(lv.phi, ng, lv.nL, lv.nG, lv.w, y, k, rmax, rsum, lv.resid);
       count_launches(1);
       cudaMemcpyAsync(&p->fit_resid[2 * l], scr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     }

@@ -35,6 +35,7 @@ struct Level {
   std::vector<int64_t> pg;   // pivot grid indices (selection order)
   int64_t* d_pg = nullptr;
   double* xiT = nullptr;     // Xi^T [k][ng]
+  float* resid = nullptr;    // fit residual per grid point (FP32 copy, for proposals)
   // Coulomb
   int nh[3] = {0, 0, 0};     // half-spectrum dims (nx/2+1, ny, nz)
   int64_t nq = 0;            // half-spectrum modes
@@ -160,6 +161,7 @@ void dtrtri_lower(const double* Lm, double* Li, int64_t n, double* scratch, cuda
 // An operand is rows x K, pre-sliced into S BF16 digit planes (S = 5 or 6)
 // and pre-tiled for the tensor cores; A operands use row tiles of 128, B
 // operands row tiles of oz_bn(S).
+constexpr int kOzBK = 32;  // k values per digit tile (two K = 16 tcgen05.mma steps, one pipeline stage)
 struct OzOperand {
   void* tiles = nullptr;  // __nv_bfloat16 slices
   int* exps = nullptr;    // per-row power-of-two scale
@@ -192,6 +194,7 @@ isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M,
 // learned point proposer (learn.cu)
 int mlp_num_params();
 isdf_status learn_features(Plan* p, float* dfeat);
+isdf_status learn_propose_residual(Plan* p, const int64_t* quota, int64_t* dcand);
 isdf_status mlp_grad_step(float* params, float* m, float* v, int step, float lr, const float* X, const float* y,
                           const float* w, int64_t n, float* loss_host, float* grad_dev, cudaStream_t s,
                           std::string& why);

@@ -506,6 +506,21 @@ isdf_status topk_level(Plan* p, const float* score, int64_t n, int level, int64_
 
 }  // namespace
 
+isdf_status learn_propose_residual(Plan* p, const int64_t* quota, int64_t* dcand) {
+  unsigned long long* cnt = nullptr;
+  isdf_status r;
+  if ((r = dalloc_t(p, &cnt, 1, "count"))) return r;
+  int64_t written = 0;
+  for (int l = 0; l < p->nlev; ++l) {
+    const int64_t K = std::min<int64_t>(quota[l], p->lev[l].ng);
+    if (K <= 0) continue;
+    if ((r = topk_level(p, p->lev[l].resid, p->lev[l].ng, l, K, dcand + written, cnt))) break;
+    written += K;
+  }
+  dfree(cnt);
+  return r;
+}
+
 isdf_status learn_propose(Plan* p, const float* params, const int64_t* quota, int64_t* dcand) {
   cudaStream_t s = p->stream;
   const int64_t n = p->ntot;

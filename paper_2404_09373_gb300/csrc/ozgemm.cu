@@ -38,22 +38,20 @@ namespace isdf {
 namespace {
 
 constexpr int kBM = 128;  // A rows per CTA = TMEM lanes
-constexpr int kBK = 32;   // k values per tile / pipeline stage
-constexpr int kKcTiles = 32;  // 1024 k values per exact chunk
-constexpr int kEpiWarps = 8;
-constexpr int kThreads = 32 * (2 + kEpiWarps);
+constexpr int kBK = kOzBK;  // k values per tile / pipeline stage
+constexpr int kKcTiles = 1024 / kBK;  // 1024 k values per exact chunk
 constexpr long long kWaitLimit = 1ll << 30;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s of device time per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr) {
-  // K-major, no swizzle: LBO = 128 B (next core matrix along K), SBO = 512 B
-  // (next 8-row group), descriptor version 1 (bits 46-47), layout type 0.
+  // K-major, no swizzle: LBO = 128 B (next core matrix along K), SBO = 16 kBK
+  // bytes (next 8-row group), descriptor version 1 (bits 46-47), layout type 0.
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
   d |= (uint64_t)(128 >> 4) << 16;
-  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)((16 * kBK) >> 4) << 32;
   d |= (uint64_t)1 << 46;
   return d;
 }
@@ -132,8 +130,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "r"(taddr));
 }
 
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, uint32_t (&r)[2]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];" : "=r"(r[0]), "=r"(r[1]) : "r"(taddr));
+
+// Compiler fence on 16 accumulators: the empty volatile statement reads and
+// writes them, so their updates are complete here and no later volatile
+// statement (a tensor-memory load) is moved above it.
+__device__ __forceinline__ void reg_fence16(long long (&a)[16], uint32_t (&b)[16]) {
+  asm volatile("" : "+l"(a[0]), "+l"(a[1]), "+l"(a[2]), "+l"(a[3]), "+l"(a[4]), "+l"(a[5]), "+l"(a[6]), "+l"(a[7]));
+  asm volatile("" : "+l"(a[8]), "+l"(a[9]), "+l"(a[10]), "+l"(a[11]), "+l"(a[12]), "+l"(a[13]), "+l"(a[14]),
+               "+l"(a[15]));
+  asm volatile("" : "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+               "+r"(b[8]), "+r"(b[9]), "+r"(b[10]), "+r"(b[11]), "+r"(b[12]), "+r"(b[13]), "+r"(b[14]), "+r"(b[15]));
 }
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
@@ -270,7 +276,7 @@ __global__ void k_oz_digits(const double* __restrict__ src, int64_t sr, int64_t 
   const int64_t it = r / rt, rr = r % rt, jt = kg / (kBK / 8), kc = kg % (kBK / 8);
   const int64_t tile_elems = int64_t(rt) * kBK;
   __nv_bfloat16* base = tiles + ((it * kst + jt) * S) * tile_elems;
-  const int64_t inner = ((rr / 8) * 512 + kc * 128 + (rr % 8) * 16) / 2;  // element offset in a tile
+  const int64_t inner = ((rr / 8) * (16 * kBK) + kc * 128 + (rr % 8) * 16) / 2;  // element offset in a tile
   // digits from the least significant end (balanced, in [-64, 63]); top digit last
   for (int s = S - 1; s >= 0; --s) {
     __align__(16) __nv_bfloat16 d[8];
@@ -321,19 +327,24 @@ struct OzCfg {
   static constexpr int smem = nst * stage + 2048;  // + barriers and 1024-byte alignment slack
   static constexpr int cols = S * BN;
   static constexpr uint32_t tcols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
-  // S >= 7: every level is kept exact (chunks of 256 k keep each level's
-  // integer sum below 2^24) and summed in 64-bit integers; else double-float
+  // S = 8: levels 0..5 are kept exact (chunks of 512 k keep their integer
+  // sums at most 2^24; levels 6, 7 weigh less than 2^-42, where FP32 rounding
+  // is harmless) and summed in integers; else double-float
   static constexpr bool exact = S >= 7;
-  static constexpr int kc = exact ? 8 : kKcTiles;  // k tiles per chunk
+  static constexpr int kc = exact ? 512 / kBK : kKcTiles;  // k tiles per chunk
+  // epilogue warps: two per tensor-memory lane quarter (BN/2 columns each),
+  // three when exact (BN/3 columns each, so the integer state fits in registers)
+  static constexpr int epi = exact ? 12 : 8;
+  static constexpr int threads = 32 * (2 + epi);
   static_assert(!exact || S == 8, "the integer epilogue splits the levels of exactly 8 digits");
   static_assert(cols <= 512, "levels x BN must fit in tensor memory");
   static_assert(nst >= 2, "need at least two pipeline stages");
-  static_assert(BN % 32 == 0, "BN must split into two halves of x16 loads");
+  static_assert((BN / (epi / 4)) % 16 == 0, "each epilogue warp reads whole 16-column groups");
   static_assert(smem <= 232448, "shared memory per CTA");
 };
 
 template <int S, int BN>
-__global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
+__global__ void __launch_bounds__(OzCfg<S, BN>::threads, 1) k_oz_gemm(OzGemmParams P) {
   using Cfg = OzCfg<S, BN>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -371,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
       mbar_init(&empty[i], 1);
     }
     mbar_init(acc_full, 1);
-    mbar_init(acc_empty, kEpiWarps);
+    mbar_init(acc_empty, Cfg::epi);
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;");
@@ -418,7 +429,6 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      constexpr uint32_t idesc = umma_idesc(kBM, BN);
       for (int64_t it = 0; it < nk; ++it) {
         const int st = int(it % Cfg::nst);
         const int64_t round = it / Cfg::nst;
@@ -437,17 +447,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
         asm volatile("tcgen05.fence::after_thread_sync;");
         const uint32_t sA = smem_u32(smem + st * Cfg::stage);
         const uint32_t sB = sA + Cfg::stageA;
+        // For A digit s the products with B digits t = 0..S-1-s land in
+        // levels s..S-1, i.e. tensor-memory columns [s BN, S BN); the B
+        // digit tiles of a stage are contiguous, so B rows [0, (S-s) BN) are
+        // exactly digits 0..S-1-s and one MMA (N up to 256, else split)
+        // covers them all.  The first MMA of a chunk (s = 0) spans every
+        // level and initialises the accumulators.
 #pragma unroll
-        for (int q = 0; q < S; ++q) {
+        for (int s = 0; s < S; ++s) {
 #pragma unroll
-          for (int s = 0; s <= q; ++s) {
-            const int t = q - s;
+          for (int c0 = 0; c0 < BN * (S - s); c0 += 256) {
+            const int n = (BN * (S - s) - c0) < 256 ? (BN * (S - s) - c0) : 256;
+            const uint32_t idesc = umma_idesc(kBM, n);
 #pragma unroll
             for (int ks = 0; ks < kBK / 16; ++ks) {
               const uint64_t da = umma_desc(sA + s * Cfg::tileA + ks * 256);
-              const uint64_t db = umma_desc(sB + t * Cfg::tileB + ks * 256);
+              const uint64_t db = umma_desc(sB + (c0 / 8) * (16 * kBK) + ks * 256);
               const uint32_t acc = (cpos > 0 || s > 0 || ks > 0) ? 1u : 0u;
-              umma_bf16(tmem + uint32_t(q * BN), da, db, idesc, acc);
+              umma_bf16(tmem + uint32_t(s * BN + c0), da, db, idesc, acc);
             }
           }
         }
@@ -459,21 +476,26 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
       mbar_wait(drain, 0, nullptr);
     }
   } else {
-    // ------------------------------------------------ epilogue (8 warps)
-    const int quarter = warp % 4;
-    const int half = (warp - 2) / 4;
+    // ------------------------------------------------ epilogue warps
+    const int quarter = warp % 4;  // a warp reads tensor-memory lanes 32 (warp % 4) ..
+    const int half = (warp - 2) / 4;  // which share of the columns
     const int row = quarter * 32 + lane;
-    constexpr int HC = BN / 2;  // columns per thread
+    constexpr int HC = BN / (Cfg::epi / 4);  // columns per thread
     const int64_t m = m0 + row;
     if constexpr (Cfg::exact) {
-      // Per column and chunk: hi = sum_{q<4} L_q 2^{7(3-q)}, lo = sum_{q>=4}
-      // L_q 2^{7(S-1-q)} (64-bit, exact).  th accumulates hi plus the part of
-      // lo above 2^28; rem keeps lo's low 28 bits (carried into th whenever
-      // it passes 2^28), so value = th + rem 2^-28 in units of 2^-21.
+      // Levels 0..7 of one column and chunk (512 k: levels 0..5 are exact
+      // integers below 2^24) are paired exactly in 32-bit integers,
+      //   P01 = L0 2^7 + L1, P23 = L2 2^7 + L3, P45 = L4 2^7 + L5  (< 2^31),
+      // and levels 6, 7 (weights below 2^-42) are combined in FP32.  Per
+      // column th accumulates P01 2^14 + P23 plus the part of
+      // lo = P45 2^14 + (L6 2^7 + L7) above 2^28; rem keeps lo's low 28 bits
+      // (carried into th), so the value is th + rem 2^-28 in units of 2^-21.
+      static_assert(S == 8 && HC % 16 == 0, "8 levels, 16-column tensor-memory loads");
       long long th[HC];
       uint32_t rem[HC];
 #pragma unroll
       for (int j = 0; j < HC; ++j) th[j] = 0, rem[j] = 0u;
+      const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(half * HC);
       for (int64_t c = 0; c < nchunks; ++c) {
         if (!mbar_wait(acc_full, uint32_t(c & 1), P.err)) {
           set_err(P.err, 14);
@@ -482,29 +504,40 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
         }
         asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-        for (int c0 = 0; c0 < HC; c0 += 2) {
-          uint32_t r[S][2];
+        for (int c0 = 0; c0 < HC; c0 += 16) {
 #pragma unroll
-          for (int q = 0; q < S; ++q)
-            tmem_ld2(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(q * BN + half * HC + c0), r[q]);
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
+          for (int pq = 0; pq < 4; ++pq) {  // level pairs (0,1) (2,3) (4,5) (6,7)
+            uint32_t ra[16], rb[16];
+            tmem_ld16(tbase + uint32_t((2 * pq) * BN + c0), ra);
+            tmem_ld16(tbase + uint32_t((2 * pq + 1) * BN + c0), rb);
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-          for (int j = 0; j < 2; ++j) {
-            long long hi = 0, lo = 0;
-#pragma unroll
-            for (int q = 0; q < S; ++q) {
-              const long long v = (long long)__float2int_rn(__uint_as_float(r[q][j]));  // exact: |v| < 2^24
-              if (q < 4)
-                hi += v * (1ll << (7 * (3 - q)));
-              else
-                lo += v * (1ll << (7 * (S - 1 - q)));
+            for (int j = 0; j < 16; ++j) {
+              const float fa = __uint_as_float(ra[j]), fb = __uint_as_float(rb[j]);
+              if (pq < 3) {
+                const int pair = __float2int_rn(fa) * 128 + __float2int_rn(fb);  // exact, |pair| < 2^31
+                if (pq == 0) {
+                  th[c0 + j] += (long long)pair * (1ll << 14);
+                } else if (pq == 1) {
+                  th[c0 + j] += (long long)pair;
+                } else {
+                  const long long x = (long long)pair * (1ll << 14);  // lo part of levels 4, 5
+                  th[c0 + j] += x >> 28;
+                  rem[c0 + j] += uint32_t(x & 0x0FFFFFFFll);
+                }
+              } else {
+                const long long x = __float2ll_rn(fmaf(fa, 128.0f, fb));  // levels 6, 7
+                th[c0 + j] += x >> 28;
+                rem[c0 + j] += uint32_t(x & 0x0FFFFFFFll);
+              }
             }
-            const long long carry = lo >> 28;  // floor; lo - carry 2^28 in [0, 2^28)
-            const uint32_t low = uint32_t(lo - carry * (1ll << 28));
-            uint32_t rr = rem[c0 + j] + low;  // < 2^29
-            th[c0 + j] += hi + carry + (long long)(rr >> 28);
-            rem[c0 + j] = rr & 0x0FFFFFFFu;
+            reg_fence16(th, rem);
           }
+        }
+#pragma unroll
+        for (int j = 0; j < HC; ++j) {  // rem < 3 * 2^28 here
+          th[j] += (long long)(rem[j] >> 28);
+          rem[j] &= 0x0FFFFFFFu;
         }
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncwarp();
@@ -517,8 +550,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_oz_gemm(OzGemmParams P) {
           const int64_t n = n0 + half * HC + j;
           if (n >= P.N) continue;
           const int e = ea + P.eb[n] - 14 - 21;
-          const double t = double(th[j]) + ldexp(double(rem[j]), -28);  // one rounding
-          double v = ldexp(t, e);
+          const double t = double(th[j]) + double(rem[j]) * 0x1p-28;  // one rounding
+          // t 2^e: exact power-of-two factor built from its bits in the normal range
+          double v = (e >= -1022 && e <= 1023) ? t * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(t, e);
           if (P.alpha != 1.0) v *= P.alpha;
           if (P.splits > 1)
             P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
@@ -612,7 +646,7 @@ void launch_oz(const OzGemmParams& P, dim3 grid, cudaStream_t s) {
     cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::smem);
     configured = true;
   }
-  k_oz_gemm<S, BN><<<grid, kThreads, Cfg::smem, s>>>(P);
+  k_oz_gemm<S, BN><<<grid, Cfg::threads, Cfg::smem, s>>>(P);
 }
 
 }  // namespace
@@ -664,7 +698,8 @@ void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzO
   if (op.rows <= 0 || kt1 <= kt0) return;
   const bool rowwise = sr >= sk;
   if (!exps_ready) {
-    if (rowwise && op.K >= 4096)
+    // few long rows (a gathered set of rows with large K): one block per row
+    if ((rowwise && op.K >= 4096) || (op.K >= 256 && op.rows <= 8192))
       k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, sr, sk, op.K, nullptr, 1.0, ridx, op.exps);
     else
       k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, nullptr, 1.0,
@@ -678,7 +713,7 @@ void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzO
   count_launches(1);
 }
 
-int oz_bn(int S) { return S == 5 ? 96 : 64; }  // S levels x BN columns fill at most 512 of tensor memory
+int oz_bn(int S) { return S == 5 ? 96 : S == 8 ? 48 : 64; }  // S levels x BN columns fill at most 512 of tensor memory
 
 void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, double alpha, int tri, int sym,
              int splits, double* work, int* err, cudaStream_t s) {
@@ -705,7 +740,7 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   if (A.S == 5)
     launch_oz<5, 96>(P, grid, s);
   else if (A.S == 8)
-    launch_oz<8, 64>(P, grid, s);
+    launch_oz<8, 48>(P, grid, s);
   else
     launch_oz<6, 64>(P, grid, s);
   count_launches(1);

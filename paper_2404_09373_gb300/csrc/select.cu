@@ -998,7 +998,6 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
     cudaGetLastError();
   }
 
-  double gemm_flop = 0.0;
   int64_t nblocks = 0, nplain = 0;
   std::vector<int> hcount(ISDF_MAX_LEVELS + 1);
   while (true) {
@@ -1021,28 +1020,33 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
       Level& lv = p->lev[l];
       LevBuf& b = lb[l];
       const int kb = h.kl[l];
-      const double flop = 2.0 * double(nc[l]) * sl * (lv.nL + lv.nN + kb);
-      gemm_flop += flop;
-      Prof pr(p, "select_gemm", flop, "flop", 3);
       auto setrows = [&](OzOperand& op, int rows) {
         op.rows = rows;
         op.nrt = (rows + op.rt - 1) / op.rt;
       };
-      setrows(b.bL, sl);
-      oz_slice_ex(lv.phi, 1, lv.ng, sg + soff, b.bL, 0, b.bL.nkt, false, s);
-      oz_gemm(b.aL, b.bL, b.cL, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
-      if (lv.nN > 0) {
-        setrows(b.bN, sl);
-        oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, sg + soff, b.bN, 0, b.bN.nkt, false, s);
-        oz_gemm(b.aN, b.bN, b.cN, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      {
+        // digits of S's rows: basis values and factor rows of the set
+        Prof pb(p, "select_sslice", 8.0 * sl * (lv.nL + lv.nN + kb), "byte", 6);
+        setrows(b.bL, sl);
+        oz_slice_ex(lv.phi, 1, lv.ng, sg + soff, b.bL, 0, b.bL.nkt, false, s);
+        if (lv.nN > 0) {
+          setrows(b.bN, sl);
+          oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, sg + soff, b.bN, 0, b.bN.nkt, false, s);
+        }
+        if (kb > 0) {
+          setrows(b.bF, sl);
+          b.bF.K = kb;
+          b.bF.nkt = (kb + kOzBK - 1) / kOzBK;
+          oz_slice_ex(lv.fac, 1, nc[l], stp + soff, b.bF, 0, b.bF.nkt, false, s);
+        }
       }
+      // algorithmic traffic: the candidates' FP64 basis values and factor rows, read once per block
+      Prof pr(p, "select_gemm", 8.0 * double(nc[l]) * (lv.nL + lv.nN + kb), "byte", 3);
+      oz_gemm(b.aL, b.bL, b.cL, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      if (lv.nN > 0) oz_gemm(b.aN, b.bN, b.cN, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
       if (kb > 0) {
-        setrows(b.bF, sl);
-        b.bF.K = kb;
-        b.bF.nkt = (kb + 31) / 32;
-        oz_slice_ex(lv.fac, 1, nc[l], stp + soff, b.bF, 0, b.bF.nkt, false, s);
         b.aF.K = kb;
-        b.aF.nkt = (kb + 31) / 32;
+        b.aF.nkt = (kb + kOzBK - 1) / kOzBK;
         oz_gemm(b.aF, b.bF, b.cF, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
       }
       const int64_t n = int64_t(sl) * nc[l];
@@ -1101,7 +1105,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
         LevBuf& b = lb[l];
         if (h.kl[l] <= b.sliced) continue;
         b.aF.K = h.kl[l];
-        oz_slice_ex(p->lev[l].fac, 1, nc[l], nullptr, b.aF, b.sliced / 32, (h.kl[l] + 31) / 32, true, s);
+        oz_slice_ex(p->lev[l].fac, 1, nc[l], nullptr, b.aF, b.sliced / kOzBK, (h.kl[l] + kOzBK - 1) / kOzBK, true, s);
         b.sliced = h.kl[l];
       }
     }

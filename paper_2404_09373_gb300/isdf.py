@@ -46,6 +46,7 @@ EXPORTED = [
     "isdf_mlp_train_step",
     "isdf_mlp_score",
     "isdf_propose",
+    "isdf_propose_residual",
     "isdf_gemm_f64_noalloc",
     "isdf_gemm_f64_noalloc_capacity",
 ]
@@ -141,6 +142,8 @@ def load_library(build_if_missing: bool = True):
     lib.isdf_mlp_score.restype = c_int
     lib.isdf_propose.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
     lib.isdf_propose.restype = c_int
+    lib.isdf_propose_residual.argtypes = [c_void_p, c_void_p, c_void_p]
+    lib.isdf_propose_residual.restype = c_int
     lib.isdf_gemm_f64_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64,
                                           c_int64, c_double, c_int, c_void_p]
     lib.isdf_gemm_f64_noalloc.restype = c_int
@@ -373,6 +376,14 @@ def isdf_propose(plan: Plan, params, quota):
     q = np.ascontiguousarray(quota, dtype=np.int64)
     out = np.zeros(int(q.sum()), dtype=np.int64)
     plan._check(plan._lib.isdf_propose(plan.handle, params.data_ptr(), q.ctypes.data, out.ctypes.data))
+    return out
+
+
+def isdf_propose_residual(plan: Plan, quota):
+    """After isdf_fit: per level the quota[l] points with the largest fit residual (pivot codes)."""
+    q = np.ascontiguousarray(quota, dtype=np.int64)
+    out = np.zeros(int(q.sum()), dtype=np.int64)
+    plan._check(plan._lib.isdf_propose_residual(plan.handle, q.ctypes.data, out.ctypes.data))
     return out
 
 

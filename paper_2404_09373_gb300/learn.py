@@ -15,7 +15,9 @@ residual over ALL grid points (the Schur complement the pivots leave,
 reported by isdf_fit) is compared with the last pivot value.  The full
 greedy run leaves no residual above its last pivot value; if the restricted
 run leaves one larger than ``kappa`` times it, the network missed important
-points and the full selection is run instead.
+points.  A corrective pass then adds the points with the largest fit residual
+on the offending levels to the candidates and selects again; if the check
+still fails, the full selection is run instead.
 
 Candidates are proposed per level: ``factor * N_ip`` split over the levels
 like the pivots of the training cells (pivot density of each level times its
@@ -126,28 +128,46 @@ def quotas(grids, level_density, nip, factor):
     return np.minimum(q, pts.astype(np.int64))
 
 
-def select_learned(plan, params, nip, level_density, factor=4, kappa=10.0):
-    """Candidate-restricted selection + fit with the fallback check.
+def select_learned(plan, params, nip, level_density, factor=4, kappa=10.0, repair=1):
+    """Candidate-restricted selection + fit with the residual check.
 
-    Returns (pivots, info): info has the candidate count, whether the
-    fallback ran, the residual ratio and the selection / fit times."""
+    If the largest fit residual exceeds kappa times the last pivot value, up
+    to ``repair`` corrective passes add, on every level whose residual is
+    above the last pivot value, the points with the largest fit residual
+    (as many as the level's share of N_ip) to the candidates and select and
+    fit again; if the check still fails the full selection runs.
+
+    Returns (pivots, info): info has the candidate count, the passes, whether
+    the fallback ran, the residual ratio and the selection / fit times."""
     t0 = time.perf_counter()
     n_points = int(B.isdf_get(plan, B.GET_NPOINTS)[0])
     q = quotas(plan.system["grids"], level_density, nip, factor)
-    ncand = int(q.sum())
     cand = B.isdf_propose(plan, params, q)
-    piv, dv = B.isdf_select_points(plan, nip, cand=cand)
-    t1 = time.perf_counter()
-    B.isdf_fit(plan, piv)
+    info = {"quota": q.tolist(), "n_points": n_points, "fallback": False, "repairs": 0}
+    t_fit = 0.0
+    while True:
+        piv, dv = B.isdf_select_points(plan, nip, cand=cand)
+        t1 = time.perf_counter()
+        B.isdf_fit(plan, piv)
+        t_fit += time.perf_counter() - t1
+        res = B.isdf_get(plan, B.GET_FIT_RESIDUAL).reshape(-1, 2)
+        dlast = float(dv[-1]) if dv.size else np.inf
+        ratio = float(res[:, 0].max()) / dlast if dv.size else np.inf
+        ok = ratio <= kappa and piv.size == nip
+        if ok or info["repairs"] >= repair or not dv.size:
+            break
+        extra_q = np.where(res[:, 0] > dlast, np.ceil(q / factor), 0).astype(np.int64)
+        if extra_q.sum() == 0:
+            break
+        extra = B.isdf_propose_residual(plan, extra_q)
+        cand = np.unique(np.concatenate([cand, extra]))
+        info["repairs"] += 1
     t2 = time.perf_counter()
-    res = B.isdf_get(plan, B.GET_FIT_RESIDUAL).reshape(-1, 2)
-    rmax = float(res[:, 0].max())
-    ratio = rmax / float(dv[-1]) if dv.size else np.inf
-    info = {"ncand": ncand, "quota": q.tolist(), "n_points": n_points, "residual_ratio": ratio,
-            "residual_ratio_per_level": (res[:, 0] / float(dv[-1])).tolist() if dv.size else None,
-            "pivots_per_level": np.bincount(piv >> B.PIVOT_SHIFT, minlength=len(q)).tolist(),
-            "fallback": False, "t_select_s": t1 - t0, "t_fit_s": t2 - t1}
-    if not (ratio <= kappa) or piv.size < nip:
+    info.update({"ncand": int(cand.size), "residual_ratio": ratio,
+                 "residual_ratio_per_level": (res[:, 0] / dlast).tolist() if dv.size else None,
+                 "pivots_per_level": np.bincount(piv >> B.PIVOT_SHIFT, minlength=len(q)).tolist(),
+                 "t_select_s": t2 - t0 - t_fit, "t_fit_s": t_fit})
+    if not ok:
         t3 = time.perf_counter()
         piv, dv = B.isdf_select_points(plan, nip)
         B.isdf_fit(plan, piv)

@@ -167,9 +167,42 @@ def test_learned_proposer_gain_judged_by_oracle_exchange_error():
     err_full = np.max(np.abs(K_full - Kn))
     err_l = np.max(np.abs(K_l - Kn))
     print(f"\nlearned proposer: ncand {info['ncand']} of {info['n_points']} points, residual ratio "
-          f"{info['residual_ratio']:.3g}, fallback {info['fallback']}; |K - K_nofit|: full {err_full:.3e}, "
+          f"{info['residual_ratio']:.3g}, repairs {info['repairs']}, fallback {info['fallback']}; "
+          f"|K - K_nofit|: full {err_full:.3e}, "
           f"learned {err_l:.3e}; untrained ratio {info_u['residual_ratio']:.3g} fallback {info_u['fallback']}")
     assert not info["fallback"]
     assert info["ncand"] * 5 < info["n_points"]
     assert err_l <= 2.0 * err_full + 1e-5
     assert info_u["fallback"] or info_u["residual_ratio"] > info["residual_ratio"]
+
+
+def test_propose_residual_returns_the_worst_represented_points():
+    """After the fit, isdf_propose_residual returns per level the points with
+    the largest residual w (M(g,g) - M(g,P) M_PP^-1 M(P,g)) (Section II.A),
+    checked against the oracle's residual of the same pivots (FP32 ordering:
+    every returned point is within 1e-5 of the K-th largest)."""
+    sysd, _ = S.small_multigrid(per_cell=(12, 6, 4), seed=23)
+    f = O.expand_functions(sysd)
+    levels = O._level_data(sysd, f)
+    plan = B.isdf_plan(sysd)
+    try:
+        piv, _ = B.isdf_select_points(plan, 60)
+        B.isdf_fit(plan, piv)
+        quota = [25, 10, 5]
+        got = B.isdf_propose_residual(plan, quota)
+    finally:
+        plan.close()
+    assert np.all(np.diff(got) > 0)
+    per = O.split_pivots(piv, len(levels))
+    off = 0
+    for lev, ld in enumerate(levels):
+        P = per[lev]
+        d = O.initial_diagonal(ld)
+        if P.size:
+            Mc = ld["w"] * O.m_columns(ld, P)
+            d = d - np.einsum("gp,gp->g", Mc, np.linalg.solve(Mc[P, :], Mc.T).T)
+        g = got[off:off + quota[lev]]
+        off += quota[lev]
+        assert np.all(g >> 40 == lev)
+        kth = np.sort(d)[-quota[lev]]
+        assert np.all(d[g & ((1 << 40) - 1)] >= kth - 1e-5 * abs(d).max())
