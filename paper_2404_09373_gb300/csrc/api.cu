@@ -10,6 +10,9 @@
 #include <new>
 #include <set>
 
+#include <mutex>
+#include <unordered_map>
+
 #include "internal.cuh"
 
 struct isdf_plan_s {
@@ -66,11 +69,47 @@ isdf_status cuda_check(Plan* p, cudaError_t e, const char* what) {
   return fail(p, ISDF_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// Plan buffers are stream-ordered: allocated with cudaMallocAsync on the
+// plan's stream from the device's default pool (whose release threshold is
+// raised once, so freed memory stays cached for the next allocation or the
+// next plan) and freed with cudaFreeAsync on the same stream.  The stream of
+// every live allocation is remembered for dfree.  Buffers without a plan
+// (the stand-alone product) use cudaMalloc / cudaFree.
+namespace {
+std::mutex g_alloc_mu;
+std::unordered_map<void*, cudaStream_t> g_async_owner;
+bool g_pool_ready[64] = {false};
+
+void pool_setup() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return;
+  }
+  if (g_pool_ready[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  g_pool_ready[dev] = true;
+}
+}  // namespace
+
 isdf_status dalloc(Plan* p, void** ptr, size_t bytes, const char* what) {
   *ptr = nullptr;
   if (p && p->fault == "oom") return fail(p, ISDF_ERR_OOM, std::string("device allocation failed (injected): ") + what);
   if (bytes == 0) bytes = 16;
-  cudaError_t e = cudaMalloc(ptr, bytes);
+  cudaError_t e;
+  if (p) {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    pool_setup();
+    e = cudaMallocAsync(ptr, bytes, p->stream);
+    if (e == cudaSuccess) g_async_owner[*ptr] = p->stream;
+  } else {
+    e = cudaMalloc(ptr, bytes);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     *ptr = nullptr;
@@ -94,7 +133,17 @@ isdf_status oz_check(Plan* p) {
 }
 
 void dfree(void* ptr) {
-  if (ptr) cudaFree(ptr);
+  if (!ptr) return;
+  {
+    std::lock_guard<std::mutex> lock(g_alloc_mu);
+    auto it = g_async_owner.find(ptr);
+    if (it != g_async_owner.end()) {
+      cudaFreeAsync(ptr, it->second);
+      g_async_owner.erase(it);
+      return;
+    }
+  }
+  cudaFree(ptr);
 }
 
 bool is_device_ptr(const void* ptr) {

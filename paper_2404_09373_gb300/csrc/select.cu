@@ -95,6 +95,9 @@ __device__ __forceinline__ T block_reduce(T v, Op op, T* sh) {
 struct MaxOp {
   __device__ double operator()(double a, double b) const { return fmax(a, b); }
 };
+struct MaxU64 {
+  __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a > b ? a : b; }
+};
 struct MinOp {
   __device__ unsigned long long operator()(unsigned long long a, unsigned long long b) const { return a < b ? a : b; }
 };
@@ -825,6 +828,214 @@ isdf_status select_loop(Plan* p, int nip, double tol, const double* d0full, int*
   return ISDF_OK;
 }
 
+// ---------------------------------------------------------------- persistent block steps
+//
+// All greedy steps of one speculative block in one cooperative launch (every
+// CTA resident).  Each step is two phases separated by grid barriers:
+//   B: tie rule on d_max (computed in the previous phase A): smallest index
+//      with d >= thr, atomicMin;
+//   A: every CTA derives the same pivot from the shared slots, keeps its own
+//      copy of the counters, writes its share of the new column and residual
+//      and reduces the residual's maximum for the next step; CTA 0 records
+//      the pivot.
+// The pivot's own residual is zeroed in the next phase B (other CTAs read it
+// during phase A), and that phase's search skips it.  Barriers are bounded:
+// after ~1 s of device time a CTA records an error and leaves; every CTA
+// leaves at the next barrier it reaches, so the launch always ends.
+
+struct StepSync {
+  unsigned int count;
+  unsigned int gen;
+  int abort;
+  int pad;
+  unsigned long long dmax[2];
+  unsigned long long first[2];
+};
+
+constexpr unsigned long long kBarrierNs = 1000000000ull;
+
+__device__ bool grid_sync(StepSync* sy, unsigned int nblocks) {
+  __shared__ int ok_sh;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned int* gen = &sy->gen;
+    const unsigned int g = *gen;
+    __threadfence();
+    if (atomicAdd(&sy->count, 1u) == nblocks - 1) {
+      sy->count = 0;
+      __threadfence();
+      atomicAdd(&sy->gen, 1u);
+    } else {
+      const unsigned long long t0 = globaltimer();
+      long long i = 0;
+      while (*gen == g) {
+        if (*(volatile int*)&sy->abort) { ok = 0; break; }
+        if ((++i & 1023) == 0 && globaltimer() - t0 > kBarrierNs) {
+          atomicExch(&sy->abort, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+    if (*(volatile int*)&sy->abort) ok = 0;
+    ok_sh = ok;
+  }
+  __syncthreads();
+  return ok_sh != 0;
+}
+
+__global__ void k_sync_init(StepSync* sy) {
+  if (threadIdx.x != 0) return;
+  sy->count = 0;
+  sy->gen = 0;
+  sy->abort = 0;
+  sy->dmax[0] = sy->dmax[1] = 0ull;
+  sy->first[0] = sy->first[1] = ULLONG_MAX;
+}
+
+__global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, StepSync* sy, int smax) {
+  const SelParams& P = B.P;
+  __shared__ double lp[256];
+  __shared__ int kl_sh[ISDF_MAX_LEVELS];
+  __shared__ unsigned long long red[32];
+  const unsigned int nb = gridDim.x;
+  const int tid = threadIdx.x;
+  const int64_t gtid = int64_t(blockIdx.x) * blockDim.x + tid, gstride = int64_t(gridDim.x) * blockDim.x;
+  // private copies of the counters (identical in every CTA)
+  int k = st->k;
+  double d0 = st->d0;
+  __shared__ int kb[ISDF_MAX_LEVELS];  // columns per level when the block began
+  if (tid < ISDF_MAX_LEVELS) kl_sh[tid] = kb[tid] = st->kl[tid];
+  __syncthreads();
+  long long last = -1;  // global index of the previous step's pivot (its residual is zeroed next phase B)
+  int bsteps = 0, reason = 0;  // reason: 0 running, 1 block end, 2 final, 3 timeout, 4 barrier failure
+  // phase 0: d_max of the current residual into slot 0
+  {
+    double m = 0.0;
+    for (int64_t i = gtid; i < P.ntot; i += gstride) m = fmax(m, __ldcg(P.d + i));
+    unsigned long long mb = block_reduce((unsigned long long)__double_as_longlong(m),
+                                         MaxU64(),
+                                         red);
+    if (tid == 0) atomicMax(&sy->dmax[0], mb);
+  }
+  if (!grid_sync(sy, nb)) reason = 4;
+  for (int j = 0; reason == 0; ++j) {
+    const int par = j & 1;
+    // ---------------- phase B
+    if (last >= 0 && gtid == 0) P.d[last] = 0.0;  // visible after the barrier
+    const double dmax = __longlong_as_double((long long)*(volatile unsigned long long*)&sy->dmax[par]);
+    const double dz = (k == 0) ? dmax : d0;
+    if (j >= smax) { reason = 1; break; }
+    if (k >= P.nip || !(dmax > 0.0) || dmax < P.tol * dz) { reason = 2; break; }
+    const double thr = dmax - fmax(P.tie_rel * dmax, P.tie_abs * dz);
+    unsigned long long best = ULLONG_MAX;
+    for (int64_t i = gtid; i < P.ntot; i += gstride) {
+      if (i == last) continue;
+      const double v = __ldcg(P.d + i);
+      if (v >= thr && v > 0.0) {
+        best = (unsigned long long)i;
+        break;
+      }
+    }
+    best = block_reduce(best, MinOp(), red);
+    if (tid == 0 && best != ULLONG_MAX) atomicMin(&sy->first[par], best);
+    if (gtid == 0) {  // slots of the next step
+      sy->dmax[par ^ 1] = 0ull;
+      sy->first[par ^ 1] = ULLONG_MAX;
+    }
+    if (!grid_sync(sy, nb)) { reason = 4; break; }
+    // ---------------- phase A
+    const unsigned long long idx = *(volatile unsigned long long*)&sy->first[par];
+    if (idx == ULLONG_MAX) { reason = 2; break; }
+    const int pos = __ldcg(B.spos + idx);
+    if (pos < 0) { reason = 1; break; }  // greedy pivot outside S: block ends
+    int l = 0;
+    while (l + 1 < P.nlev && (long long)idx >= P.coff[l + 1]) ++l;
+    const long long tp = (long long)idx - P.coff[l];
+    const double dp = __ldcg(P.d + idx);
+    const int col = kl_sh[l];
+    const int nbk = col - kb[l];
+    const int64_t nc = P.nc[l];
+    const double* fac = P.fac[l];
+    __syncthreads();
+    for (int i = tid; i < nbk; i += blockDim.x) lp[i] = __ldcg(fac + int64_t(kb[l] + i) * nc + tp);
+    __syncthreads();
+    if (k == 0) d0 = dmax;
+    if (gtid == 0) {
+      const long long g = P.cidx[l] ? P.cidx[l][tp] : tp;
+      P.piv[k] = ((long long)l << kPivShift) | g;
+      P.dval[k] = dp;
+      if (k == 0) {
+        st->d0 = dmax;
+        st->t0 = globaltimer();
+      }
+    }
+    const double sq = sqrt(dp);
+    const double* __restrict__ bcol = B.bm[l] + int64_t(pos) * nc;
+    double* __restrict__ facw = P.fac[l];
+    const int64_t lo = P.coff[l], hi = P.coff[l + 1];
+    double m = 0.0;
+    for (int64_t i = gtid; i < P.ntot; i += gstride) {
+      double dn;
+      if (i >= lo && i < hi) {
+        const int64_t t = i - lo;
+        double s0 = 0.0;
+        for (int q = 0; q < nbk; ++q) s0 = fma(__ldcg(fac + int64_t(kb[l] + q) * nc + t), lp[q], s0);
+        double v = (bcol[t] - s0) / sq;
+        if (t == tp) v = sq;
+        facw[int64_t(col) * nc + t] = v;
+        if (t == tp) {
+          dn = 0.0;  // written as 0 in the next phase B
+        } else {
+          dn = __ldcg(P.d + i) - v * v;
+          P.d[i] = dn;
+        }
+      } else {
+        dn = (i == (long long)idx) ? 0.0 : __ldcg(P.d + i);
+      }
+      m = fmax(m, dn);
+    }
+    unsigned long long mb = block_reduce((unsigned long long)__double_as_longlong(m),
+                                         MaxU64(),
+                                         red);
+    if (tid == 0) atomicMax(&sy->dmax[par ^ 1], mb);
+    // counters advance identically in every CTA
+    __syncthreads();
+    if (tid == 0) kl_sh[l] = col + 1;
+    __syncthreads();
+    ++k;
+    ++bsteps;
+    last = (long long)idx;
+    // time budget: CTA 0's clock decides for everyone and publishes the decision
+    // before the barrier (this step's column is complete)
+    if (gtid == 0 && P.timeout_ns && globaltimer() - st->t0 > P.timeout_ns) atomicExch(&sy->abort, 2);
+    if (!grid_sync(sy, nb)) {
+      reason = (*(volatile int*)&sy->abort == 2) ? 3 : 4;
+      break;
+    }
+  }
+  // the last pivot's residual is zeroed here if no phase B followed it
+  if (last >= 0 && gtid == 0) P.d[last] = 0.0;
+  if (gtid == 0) {
+    st->k = k;
+    for (int l = 0; l < ISDF_MAX_LEVELS; ++l) st->kl[l] = kl_sh[l];
+    st->bsteps = bsteps;
+    st->done = 1;
+    st->skip = 1;
+    if (reason == 2) st->final_ = 1;
+    if (reason == 3) {
+      st->err = ISDF_ERR_TIMEOUT;
+      st->final_ = 1;
+    }
+    if (reason == 4) {
+      st->err = ISDF_ERR_CUDA;
+      st->final_ = 1;
+    }
+  }
+}
+
 __global__ void k_scatter_pos(const int* __restrict__ cidx, int64_t nc, int* __restrict__ gpos) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t < nc) gpos[cidx[t]] = int(t);
@@ -867,6 +1078,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
   int *counts = nullptr, *nlist = nullptr, *list = nullptr, *sidx = nullptr, *sg = nullptr, *stp = nullptr,
       *scount = nullptr, *spos = nullptr;
   cudaGraphExec_t exec = nullptr;
+  void* sync_mem = nullptr;
   auto cleanup = [&]() {
     for (int l = 0; l < nlev; ++l) {
       oz_free(lb[l].aL), oz_free(lb[l].aN), oz_free(lb[l].aF);
@@ -876,6 +1088,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
       p->lev[l].fac = nullptr;
     }
     dfree(counts), dfree(nlist), dfree(list), dfree(sidx), dfree(sg), dfree(stp), dfree(scount), dfree(spos);
+    dfree(sync_mem);
     if (exec) cudaGraphExecDestroy(exec);
   };
   auto bail = [&](isdf_status r) {
@@ -987,7 +1200,17 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
     k_blk_pick<<<1, 32, 0, s>>>(BP, dst);
     k_blk_col<<<unsigned(nsm) * 8, 256, 0, s>>>(BP, dst);
   };
-  if (s != nullptr) {
+  // persistent steps: one cooperative launch per block (every CTA resident)
+  StepSync* sync = nullptr;
+  int coop_dev = 0, steps_per_sm = 0;
+  cudaDeviceGetAttribute(&coop_dev, cudaDevAttrCooperativeLaunch, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&steps_per_sm, k_blk_steps, 512, 0);
+  cudaGetLastError();
+  const unsigned steps_blocks = unsigned(nsm) * unsigned(std::min(steps_per_sm, 2));
+  const bool coop = coop_dev && steps_per_sm > 0;
+  if (coop && (st = dalloc_t(p, &sync, 1, "step barrier"))) return bail(st);
+  sync_mem = sync;
+  if (!coop && s != nullptr) {
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
       for (int i = 0; i < smax; ++i) block_step();
@@ -1057,14 +1280,26 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
     }
     // ---- 3. greedy steps of this block
     {
-      Prof pr(p, "select_steps", 0.0, "byte", 4ll * smax);
+      Prof pr(p, "select_steps", 0.0, "byte", coop ? 1 : 4ll * smax);
       k_blk_begin<<<1, 32, 0, s>>>(dst);
-      if (exec)
+      if (coop) {
+        k_sync_init<<<1, 32, 0, s>>>(sync);
+        int smax_arg = smax;
+        void* args[] = {&BP, &dst, &sync, &smax_arg};
+        if ((st = cuda_check(p, cudaLaunchCooperativeKernel((const void*)k_blk_steps, dim3(steps_blocks), dim3(512), args,
+                                                            0, s),
+                             "block steps launch")))
+          return bail(st);
+        count_launches(2);
+      } else if (exec) {
         cudaGraphLaunch(exec, s);
-      else
+        count_launches(4ll * smax);
+      } else {
         for (int i = 0; i < smax; ++i) block_step();
+        count_launches(4ll * smax);
+      }
       k_spos_clear<<<unsigned((smax + 255) / 256), 256, 0, s>>>(sidx, scount, spos);
-      count_launches(2 + 4ll * smax);
+      count_launches(2);
     }
     ++nblocks;
     if ((st = cuda_check(p, cudaGetLastError(), "selection kernels"))) return bail(st);
