@@ -161,6 +161,16 @@ void dtrtri_lower(const double* Lm, double* Li, int64_t n, double* scratch, cuda
 // An operand is rows x K, pre-sliced into S BF16 digit planes (S = 5 or 6)
 // and pre-tiled for the tensor cores; A operands use row tiles of 128, B
 // operands row tiles of oz_bn(S).
+// Two-level index map i -> (i / in) so + (i % in) si (in = 0: i si) of
+// operand rows / k values and result rows / columns (plain strides today).
+struct OzMap {
+  int64_t in = 0, so = 0, si = 1;
+};
+inline OzMap oz_stride(int64_t st) {
+  OzMap m;
+  m.si = st;
+  return m;
+}
 constexpr int kOzBK = 32;  // k values per digit tile (two K = 16 tcgen05.mma steps, one pipeline stage)
 struct OzOperand {
   void* tiles = nullptr;  // __nv_bfloat16 slices

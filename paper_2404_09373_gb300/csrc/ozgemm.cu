@@ -194,17 +194,27 @@ __device__ __forceinline__ long long round_scaled(double x, int shift) {
   return (b >> 63) ? -q : q;
 }
 
-// e_r: max_k |x(r,k)| < 2^e_r, x = mul * kw[k] * src[r*sr + k*sk]; one thread per row
-// (ridx: row r of the operand is source row ridx[r])
-__global__ void k_oz_rowexp_thread(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t rows, int64_t K,
+__device__ __forceinline__ int64_t map_at(const OzMap& m, int64_t i) {
+  return m.in ? (i / m.in) * m.so + (i % m.in) * m.si : i * m.si;
+}
+
+// source offset of row r: ridx[r] rows of stride rm.si, else the row map
+__device__ __forceinline__ int64_t row_base(const OzMap& rm, const int* ridx, int64_t r) {
+  return ridx ? int64_t(ridx[r]) * rm.si : map_at(rm, r);
+}
+
+// e_r: max_k |x(r,k)| < 2^e_r, x = mul * kw[k] * src[row(r) + map_k(k)]; one thread per row
+__global__ void k_oz_rowexp_thread(const double* __restrict__ src, OzMap rm, OzMap km, int64_t rows, int64_t K,
                                    const double* __restrict__ kw, double mul, const int* __restrict__ ridx,
                                    int* __restrict__ exps) {
   const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (r >= rows) return;
-  const int64_t rs = ridx ? int64_t(ridx[r]) : r;
+  const double* row = src + row_base(rm, ridx, r);
   uint64_t m = 0;
+  int64_t q = 0, rem = 0;  // k = q km.in + rem, advanced without division
   for (int64_t k = 0; k < K; ++k) {
-    double v = src[rs * sr + k * sk];
+    double v = row[km.in ? q * km.so + rem * km.si : k * km.si];
+    if (km.in && ++rem == km.in) rem = 0, ++q;
     if (mul != 1.0) v *= mul;
     if (kw) v *= kw[k];
     const uint64_t key = abs_key(v);
@@ -213,16 +223,16 @@ __global__ void k_oz_rowexp_thread(const double* __restrict__ src, int64_t sr, i
   exps[r] = exp_of_key(m);
 }
 
-// same, one block per row (long rows with unit k stride)
-__global__ void k_oz_rowexp_block(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t K,
+// same, one block per row (few long rows)
+__global__ void k_oz_rowexp_block(const double* __restrict__ src, OzMap rm, OzMap km, int64_t K,
                                   const double* __restrict__ kw, double mul, const int* __restrict__ ridx,
                                   int* __restrict__ exps) {
   __shared__ unsigned long long sh[256];
   const int64_t r = blockIdx.x;
-  const int64_t rs = ridx ? int64_t(ridx[r]) : r;
+  const double* row = src + row_base(rm, ridx, r);
   uint64_t m = 0;
   for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-    double v = src[rs * sr + k * sk];
+    double v = row[map_at(km, k)];
     if (mul != 1.0) v *= mul;
     if (kw) v *= kw[k];
     const uint64_t key = abs_key(v);
@@ -242,7 +252,7 @@ __global__ void k_oz_rowexp_block(const double* __restrict__ src, int64_t sr, in
 // Only k tiles [kt0, kt0 + nkt) are written; tile (row tile i, k tile j) sits
 // at position i * kst + j, so an operand whose K grows can be extended in
 // place.  ridx: row r is source row ridx[r].
-__global__ void k_oz_digits(const double* __restrict__ src, int64_t sr, int64_t sk, int64_t rows, int64_t K,
+__global__ void k_oz_digits(const double* __restrict__ src, OzMap rm, OzMap km, int64_t rows, int64_t K,
                             const double* __restrict__ kw, double mul, const int* __restrict__ exps, int S, int rt,
                             int64_t nrt, int64_t kt0, int64_t nkt, int64_t kst, int order,
                             const int* __restrict__ ridx, __nv_bfloat16* __restrict__ tiles) {
@@ -261,13 +271,17 @@ __global__ void k_oz_digits(const double* __restrict__ src, int64_t sr, int64_t 
   long long X[8];
   const int e = (r < rows) ? exps[r] : 0;
   const int shift = 7 * S - e;
-  const int64_t rs = (r < rows && ridx) ? int64_t(ridx[r]) : r;
+  const double* row = src + ((r < rows) ? row_base(rm, ridx, r) : 0);
+  int64_t q = 0, rem = 0;  // kg * 8 = q km.in + rem
+  if (km.in) q = (kg * 8) / km.in, rem = (kg * 8) % km.in;
 #pragma unroll
   for (int u = 0; u < 8; ++u) {
     const int64_t k = kg * 8 + u;
+    const int64_t off = km.in ? q * km.so + rem * km.si : k * km.si;
+    if (km.in && ++rem == km.in) rem = 0, ++q;
     double v = 0.0;
     if (r < rows && k < K) {
-      v = src[rs * sr + k * sk];
+      v = row[off];
       if (mul != 1.0) v *= mul;
       if (kw) v *= kw[k];
     }
@@ -308,8 +322,7 @@ struct OzGemmParams {
   int sym;     // compute only tiles that touch the lower triangle (n <= m)
   int splits;  // split-K factor (gridDim.z)
   double* C;
-  int64_t ldc;
-  int trans;   // 1: C[n*ldc + m], 0: C[m*ldc + n]
+  OzMap cm, cn;  // C[map_m(m) + map_n(n)]
   double alpha;
   double* work;  // split-K partials [z][M][N]
   int* err;
@@ -545,6 +558,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, 1) k_oz_gemm(OzGemmPara
       }
       if (m < P.M && !*(volatile int*)abort_flag) {
         const int ea = P.ea[m];
+        const int64_t cbase = map_at(P.cm, m);
 #pragma unroll
         for (int j = 0; j < HC; ++j) {
           const int64_t n = n0 + half * HC + j;
@@ -556,10 +570,8 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, 1) k_oz_gemm(OzGemmPara
           if (P.alpha != 1.0) v *= P.alpha;
           if (P.splits > 1)
             P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
-          else if (P.trans)
-            P.C[n * P.ldc + m] = v;
           else
-            P.C[m * P.ldc + n] = v;
+            P.C[cbase + map_at(P.cn, n)] = v;
         }
       }
     } else {
@@ -598,6 +610,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, 1) k_oz_gemm(OzGemmPara
       }
       if (m < P.M && !*(volatile int*)abort_flag) {
         const int ea = P.ea[m];
+        const int64_t cbase = map_at(P.cm, m);
 #pragma unroll
         for (int j = 0; j < HC; ++j) {
           const int64_t n = n0 + half * HC + j;
@@ -607,10 +620,8 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, 1) k_oz_gemm(OzGemmPara
           if (P.alpha != 1.0) v *= P.alpha;
           if (P.splits > 1)
             P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
-          else if (P.trans)
-            P.C[n * P.ldc + m] = v;
           else
-            P.C[m * P.ldc + n] = v;
+            P.C[cbase + map_at(P.cn, n)] = v;
         }
       }
     }
@@ -623,19 +634,16 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, 1) k_oz_gemm(OzGemmPara
   }
 }
 
-// C = sum_z work[z] (deterministic order), same store modes as the GEMM
+// C = sum_z work[z] (deterministic order), same store maps as the GEMM
 __global__ void k_oz_reduce(const double* __restrict__ work, int splits, int64_t M, int64_t N, double* __restrict__ C,
-                            int64_t ldc, int trans, int sym) {
+                            OzMap cm, OzMap cn, int sym) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (e >= M * N) return;
   const int64_t m = e / N, n = e % N;
   if (sym && n > m) return;
   double s = 0.0;
   for (int z = 0; z < splits; ++z) s += work[int64_t(z) * M * N + e];
-  if (trans)
-    C[n * ldc + m] = s;
-  else
-    C[m * ldc + n] = s;
+  C[map_at(cm, m) + map_at(cn, n)] = s;
 }
 
 template <int S, int BN>
@@ -680,14 +688,15 @@ void oz_free(OzOperand& op) {
 
 void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s) {
   const bool rowwise = sr >= sk;  // k contiguous: one block per row
+  const OzMap rm = oz_stride(sr), km = oz_stride(sk);
   if (rowwise && op.K >= 4096) {
-    k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, sr, sk, op.K, kw, mul, nullptr, op.exps);
+    k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, rm, km, op.K, kw, mul, nullptr, op.exps);
   } else {
-    k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, kw, mul, nullptr,
+    k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, nullptr,
                                                                         op.exps);
   }
   const int64_t total = op.nrt * op.rt * op.nkt * (kBK / 8);
-  k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, kw, mul, op.exps, op.S, op.rt,
+  k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.S, op.rt,
                                                              op.nrt, 0, op.nkt, op.kst, rowwise ? 1 : 0, nullptr,
                                                              static_cast<__nv_bfloat16*>(op.tiles));
   count_launches(2);
@@ -697,17 +706,18 @@ void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzO
                  bool exps_ready, cudaStream_t s) {
   if (op.rows <= 0 || kt1 <= kt0) return;
   const bool rowwise = sr >= sk;
+  const OzMap rm = oz_stride(sr), km = oz_stride(sk);
   if (!exps_ready) {
     // few long rows (a gathered set of rows with large K): one block per row
     if ((rowwise && op.K >= 4096) || (op.K >= 256 && op.rows <= 8192))
-      k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, sr, sk, op.K, nullptr, 1.0, ridx, op.exps);
+      k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, rm, km, op.K, nullptr, 1.0, ridx, op.exps);
     else
-      k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, nullptr, 1.0,
+      k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, nullptr, 1.0,
                                                                           ridx, op.exps);
     count_launches(1);
   }
   const int64_t total = op.nrt * op.rt * (kt1 - kt0) * (kBK / 8);
-  k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, sr, sk, op.rows, op.K, nullptr, 1.0, op.exps, op.S,
+  k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, nullptr, 1.0, op.exps, op.S,
                                                              op.rt, op.nrt, kt0, kt1 - kt0, op.kst, rowwise ? 1 : 0,
                                                              ridx, static_cast<__nv_bfloat16*>(op.tiles));
   count_launches(1);
@@ -731,8 +741,8 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   P.sym = sym;
   P.splits = splits < 1 ? 1 : splits;
   P.C = C;
-  P.ldc = ldc;
-  P.trans = trans;
+  P.cm = trans ? oz_stride(1) : oz_stride(ldc);
+  P.cn = trans ? oz_stride(ldc) : oz_stride(1);
   P.alpha = alpha;
   P.work = work;
   P.err = err;
@@ -746,7 +756,7 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   count_launches(1);
   if (P.splits > 1) {
     const int64_t tot = A.rows * B.rows;
-    k_oz_reduce<<<unsigned((tot + 255) / 256), 256, 0, s>>>(work, P.splits, A.rows, B.rows, C, ldc, trans, sym);
+    k_oz_reduce<<<unsigned((tot + 255) / 256), 256, 0, s>>>(work, P.splits, A.rows, B.rows, C, P.cm, P.cn, sym);
     count_launches(1);
   }
 }
