@@ -258,39 +258,54 @@ void dpotrf_lower(double* A, int64_t n, int64_t lda, int* err, double* /*scratch
   }
 }
 
+namespace {
+
+// Off-diagonal blocks of the inverse, top-down on [r0, r0 + n):
+//   inv([A 0; C B]) = [A^-1 0; -B^-1 C A^-1  B^-1],  A: n1 x n1, B: n2 x n2,
+// with n1 a multiple of the 64-row diagonal blocks (already inverted).
+// T = C A^-1 goes to the scratch (n2 x n1), then Li[C] = -B^-1 T.
+void trtri_rec(const double* Lm, double* Li, int64_t ld, int64_t r0, int64_t n, double* scratch, cudaStream_t s) {
+  if (n <= CB) return;
+  const int64_t n1 = ((n / 2 + CB - 1) / CB) * CB, n2 = n - n1;
+  trtri_rec(Lm, Li, ld, r0, n1, scratch, s);
+  trtri_rec(Lm, Li, ld, r0 + n1, n2, scratch, s);
+  GemmArgs g;  // T = C A^-1
+  g.M = n2;
+  g.N = n1;
+  g.K = n1;
+  g.A = Lm + (r0 + n1) * ld + r0;
+  g.lda = ld;
+  g.B = Li + r0 * ld + r0;
+  g.ldb = ld;
+  g.C = scratch;
+  g.ldc = n1;
+  dgemm(g, s);
+  GemmArgs h;  // Li[C] = -B^-1 T (B^-1 lower triangular: opA(m, k) nonzero for k <= m)
+  h.M = n2;
+  h.N = n1;
+  h.K = n2;
+  h.alpha = -1.0;
+  h.A = Li + (r0 + n1) * ld + r0 + n1;
+  h.lda = ld;
+  h.B = scratch;
+  h.ldb = n1;
+  h.C = Li + (r0 + n1) * ld + r0;
+  h.ldc = ld;
+  h.tri = 1;
+  dgemm(h, s);
+}
+
+}  // namespace
+
+// Inverse of a lower-triangular n x n matrix: every 64 x 64 diagonal block in
+// one launch, then the off-diagonal blocks by recursive halving (products of
+// the size of the halves instead of 64-row strips).
+// scratch: (n / 2 + 64) * n doubles.
 void dtrtri_lower(const double* Lm, double* Li, int64_t n, double* scratch, cudaStream_t s) {
   cudaMemsetAsync(Li, 0, sizeof(double) * n * n, s);
   const int64_t nb = (n + CB - 1) / CB;
   k_trtri_diag<<<unsigned(nb), 64, 0, s>>>(Lm, Li, n, n);
-  for (int64_t bi = 1; bi < nb; ++bi) {
-    const int64_t r0 = bi * CB;
-    const int64_t b = (n - r0 < CB) ? n - r0 : CB;
-    // T = L[r0:r0+b, 0:r0] * Li[0:r0, 0:r0]
-    GemmArgs g;
-    g.M = b;
-    g.N = r0;
-    g.K = r0;
-    g.A = Lm + r0 * n;
-    g.lda = n;
-    g.B = Li;
-    g.ldb = n;
-    g.C = scratch;
-    g.ldc = r0;
-    dgemm(g, s);
-    // Li[r0:r0+b, 0:r0] = -Li_bb * T
-    GemmArgs h;
-    h.M = b;
-    h.N = r0;
-    h.K = b;
-    h.alpha = -1.0;
-    h.A = Li + r0 * n + r0;
-    h.lda = n;
-    h.B = scratch;
-    h.ldb = r0;
-    h.C = Li + r0 * n;
-    h.ldc = n;
-    dgemm(h, s);
-  }
+  trtri_rec(Lm, Li, n, 0, n, scratch, s);
 }
 
 }  // namespace isdf

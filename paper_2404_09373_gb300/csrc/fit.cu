@@ -190,7 +190,7 @@ isdf_status fit_run(Plan* p) {
     if ((st = dalloc_t(p, &phiP, size_t(lv.nG) * k, "phi at pivots")) ||
         (st = dalloc_t(p, &zct, size_t(k) * ng, "ZC^T / Xi")) || (st = dalloc_t(p, &y, size_t(k) * ng, "fit scratch")) ||
         (st = dalloc_t(p, &cc, size_t(k) * k, "CC^T")) || (st = dalloc_t(p, &li, size_t(k) * k, "R^-1")) ||
-        (st = dalloc_t(p, &scr, size_t(64) * k + 64, "trtri scratch"))) {
+        (st = dalloc_t(p, &scr, size_t(k / 2 + 64) * k + 64, "trtri scratch"))) {
       cleanup();
       dfree(zct);
       return st;

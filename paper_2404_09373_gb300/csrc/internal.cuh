@@ -184,11 +184,12 @@ isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, in
 void oz_free(OzOperand& op);
 // X(r, k) = mul * kw[k] * src[r*sr + k*sk]  (kw nullable)
 void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s);
-// Gathered rows (row r = source row ridx[r], ridx nullable) and a k-tile
-// window [kt0, kt1) of an operand allocated for op.kst k tiles; op.K is the
-// current K (entries at k >= op.K are zero).  exps_ready: the row scales are
-// already in op.exps (they must bound every |x| the operand will ever hold).
-void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzOperand& op, int64_t kt0, int64_t kt1,
+// Gathered rows (row r = source row ridx[r], ridx nullable) and a window
+// [kg0, kg1) of 8-wide k groups of an operand allocated for op.kst k tiles;
+// op.K is the current K (entries at k >= op.K are written as zero).
+// exps_ready: the row scales are already in op.exps (they must bound every
+// |x| the operand will ever hold).  Groups outside the window are untouched.
+void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzOperand& op, int64_t kg0, int64_t kg1,
                  bool exps_ready, cudaStream_t s);
 // C = alpha * A B^T (A: M x K as the 128-row side, B: N x K); trans: C[n*ldc+m];
 // tri 1/2: B-side lower/upper triangular in (n, k); sym: lower-triangle tiles only;
@@ -200,6 +201,12 @@ int64_t oz_tile_elems(int64_t rows, int64_t K, int rt, int S);
 size_t gemm_noalloc_capacity();
 isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
                          int64_t ldb, int64_t ldc, double alpha, int slices, cudaStream_t s, std::string& why);
+
+// batched 3-D real-to-half-complex transform in double-float arithmetic (fft.cu):
+// f batch x (nz ny nx) FP64 -> S batch x (nz ny (nx/2+1)) double2, D2Z layout;
+// every axis 2^a 3^b <= 128 (rfft3_df_supported), else ISDF_ERR_ARG
+bool rfft3_df_supported(int nx, int ny, int nz);
+isdf_status rfft3_df(Plan* p, const double* f, int nx, int ny, int nz, int64_t batch, double2* S, cudaStream_t s);
 
 // learned point proposer (learn.cu)
 int mlp_num_params();

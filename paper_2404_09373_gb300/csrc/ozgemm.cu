@@ -249,14 +249,14 @@ __global__ void k_oz_rowexp_block(const double* __restrict__ src, OzMap rm, OzMa
 
 // Digits of one row and one group of 8 k values, written as 16 bytes per slice.
 // order 0: consecutive threads take consecutive rows; 1: consecutive k groups.
-// Only k tiles [kt0, kt0 + nkt) are written; tile (row tile i, k tile j) sits
-// at position i * kst + j, so an operand whose K grows can be extended in
-// place.  ridx: row r is source row ridx[r].
+// Only the 8-wide k groups [kg0, kg0 + ngrp) are written; tile (row tile i,
+// k tile j) sits at position i * kst + j, so an operand whose K grows can be
+// extended in place.  ridx: row r is source row ridx[r].
 __global__ void k_oz_digits(const double* __restrict__ src, OzMap rm, OzMap km, int64_t rows, int64_t K,
                             const double* __restrict__ kw, double mul, const int* __restrict__ exps, int S, int rt,
-                            int64_t nrt, int64_t kt0, int64_t nkt, int64_t kst, int order,
+                            int64_t nrt, int64_t kg0, int64_t ngrp, int64_t kst, int order,
                             const int* __restrict__ ridx, __nv_bfloat16* __restrict__ tiles) {
-  const int64_t rows_pad = nrt * rt, ngrp = nkt * (kBK / 8);
+  const int64_t rows_pad = nrt * rt;
   const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (idx >= rows_pad * ngrp) return;
   int64_t r, kg;
@@ -267,7 +267,7 @@ __global__ void k_oz_digits(const double* __restrict__ src, OzMap rm, OzMap km, 
     kg = idx % ngrp;
     r = idx / ngrp;
   }
-  kg += kt0 * (kBK / 8);
+  kg += kg0;
   long long X[8];
   const int e = (r < rows) ? exps[r] : 0;
   const int shift = 7 * S - e;
@@ -697,14 +697,14 @@ void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, doubl
   }
   const int64_t total = op.nrt * op.rt * op.nkt * (kBK / 8);
   k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.S, op.rt,
-                                                             op.nrt, 0, op.nkt, op.kst, rowwise ? 1 : 0, nullptr,
-                                                             static_cast<__nv_bfloat16*>(op.tiles));
+                                                             op.nrt, 0, op.nkt * (kBK / 8), op.kst, rowwise ? 1 : 0,
+                                                             nullptr, static_cast<__nv_bfloat16*>(op.tiles));
   count_launches(2);
 }
 
-void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzOperand& op, int64_t kt0, int64_t kt1,
+void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzOperand& op, int64_t kg0, int64_t kg1,
                  bool exps_ready, cudaStream_t s) {
-  if (op.rows <= 0 || kt1 <= kt0) return;
+  if (op.rows <= 0 || kg1 <= kg0) return;
   const bool rowwise = sr >= sk;
   const OzMap rm = oz_stride(sr), km = oz_stride(sk);
   if (!exps_ready) {
@@ -716,9 +716,9 @@ void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzO
                                                                           ridx, op.exps);
     count_launches(1);
   }
-  const int64_t total = op.nrt * op.rt * (kt1 - kt0) * (kBK / 8);
+  const int64_t total = op.nrt * op.rt * (kg1 - kg0);
   k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, nullptr, 1.0, op.exps, op.S,
-                                                             op.rt, op.nrt, kt0, kt1 - kt0, op.kst, rowwise ? 1 : 0,
+                                                             op.rt, op.nrt, kg0, kg1 - kg0, op.kst, rowwise ? 1 : 0,
                                                              ridx, static_cast<__nv_bfloat16*>(op.tiles));
   count_launches(1);
 }

@@ -1143,8 +1143,12 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
       return bail(st);
     {
       Prof pr(p, "select_slice", 8.0 * double(nc[l]) * lv.nG, "byte", 4);
-      if (lv.nL > 0) oz_slice_ex(lv.phi, 1, lv.ng, cidx[l], b.aL, 0, b.aL.nkt, false, s);
-      if (lv.nN > 0) oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, cidx[l], b.aN, 0, b.aN.nkt, false, s);
+      if (lv.nL > 0) oz_slice_ex(lv.phi, 1, lv.ng, cidx[l], b.aL, 0, b.aL.nkt * (kOzBK / 8), false, s);
+      if (lv.nN > 0)
+        oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, cidx[l], b.aN, 0, b.aN.nkt * (kOzBK / 8), false, s);
+      // factor-column digits are written group by group as columns appear:
+      // groups not yet written must read as zero
+      cudaMemsetAsync(b.aF.tiles, 0, size_t(oz_tile_elems(nc[l], lv.fac_cap, 128, kSlices)) * 2, s);
       // factor rows are bounded by sqrt(d0): fixed scales, columns appended in place
       k_fac_exps<<<unsigned((b.aF.nrt * 128 + 255) / 256), 256, 0, s>>>(p->d_diag + P.coff[l], nc[l], b.aF.nrt * 128,
                                                                          b.aF.exps);
@@ -1251,16 +1255,16 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
         // digits of S's rows: basis values and factor rows of the set
         Prof pb(p, "select_sslice", 8.0 * sl * (lv.nL + lv.nN + kb), "byte", 6);
         setrows(b.bL, sl);
-        oz_slice_ex(lv.phi, 1, lv.ng, sg + soff, b.bL, 0, b.bL.nkt, false, s);
+        oz_slice_ex(lv.phi, 1, lv.ng, sg + soff, b.bL, 0, b.bL.nkt * (kOzBK / 8), false, s);
         if (lv.nN > 0) {
           setrows(b.bN, sl);
-          oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, sg + soff, b.bN, 0, b.bN.nkt, false, s);
+          oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, sg + soff, b.bN, 0, b.bN.nkt * (kOzBK / 8), false, s);
         }
         if (kb > 0) {
           setrows(b.bF, sl);
           b.bF.K = kb;
           b.bF.nkt = (kb + kOzBK - 1) / kOzBK;
-          oz_slice_ex(lv.fac, 1, nc[l], stp + soff, b.bF, 0, b.bF.nkt, false, s);
+          oz_slice_ex(lv.fac, 1, nc[l], stp + soff, b.bF, 0, b.bF.nkt * (kOzBK / 8), false, s);
         }
       }
       // algorithmic traffic: the candidates' FP64 basis values and factor rows, read once per block
@@ -1340,7 +1344,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
         LevBuf& b = lb[l];
         if (h.kl[l] <= b.sliced) continue;
         b.aF.K = h.kl[l];
-        oz_slice_ex(p->lev[l].fac, 1, nc[l], nullptr, b.aF, b.sliced / kOzBK, (h.kl[l] + kOzBK - 1) / kOzBK, true, s);
+        oz_slice_ex(p->lev[l].fac, 1, nc[l], nullptr, b.aF, b.sliced / 8, (h.kl[l] + 7) / 8, true, s);
         b.sliced = h.kl[l];
       }
     }
