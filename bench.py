@@ -196,9 +196,12 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- GPU arm
 
-# dram bytes per launch of the dominant kernel, from one ncu capture of the
-# same kernel (None until such a capture exists for the current kernel)
-TRAFFIC = {}
+# DRAM traffic of a kernel family per unit of its algorithmic work, from one
+# ncu capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum
+# over the algorithmic bytes of the captured launches); absent where no capture
+# of the current kernel exists.  select_gemm: three full-size launches of the
+# 2x2x2 selection, ratio 2.18-2.24 (16-byte digit planes streamed once).
+TRAFFIC_PER_WORK = {"select_gemm": 2.2}
 
 
 # BF16 digit-pair products per FP64-equivalent flop: 5 digits (s + t <= 4) in
@@ -233,7 +236,9 @@ def roofline(kern, precision):
         hbm = pk.get("hbm_gbs", 6800.0)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
-    roof.update({"traffic": TRAFFIC.get(name), "kernel": name, "launches": st["launches"],
+    ratio = TRAFFIC_PER_WORK.get(name)
+    roof.update({"traffic": ratio * per_launch if ratio else None, "traffic_unit": "byte per launch",
+                 "kernel": name, "launches": st["launches"],
                  "avg_launch_ms": avg_s * 1e3, "work_per_launch": per_launch, "work_unit": st["unit"]})
     return kern, roof
 

@@ -286,9 +286,10 @@ isdf_status isdf_propose_residual(isdf_plan_t plan, const int64_t* quota, int64_
  * about 7 bits each).  With 5 or 6, digit-pair products accumulate in FP32
  * tensor memory per 1024-wide k chunk and are summed in double-float
  * registers; the error is below 2^-(7*slices-2) * K * max_k|A[m,k]| *
- * max_k|B[n,k]| per element.  With 8 (FP64-grade), every digit level is
- * summed exactly (256-wide chunks, 64-bit integer accumulation); the error is
- * below 2^-52 * K * max_k|A[m,k]| * max_k|B[n,k]| + 2^-53 |C[m,n]|.
+ * max_k|B[n,k]| per element.  With 8 (FP64-grade), the six leading digit
+ * levels are summed exactly (512-wide chunks, integer accumulation) and the
+ * two smallest, below 2^-42 of the result, in FP32; the error is below
+ * 2^-52 * K * max_k|A[m,k]| * max_k|B[n,k]| + 2^-53 |C[m,n]|.
  * splits > 1 divides K over that many CTAs (needs splits*M*N*8 bytes of
  * scratch, allocated by the call).  Enqueued on `stream`; returns after the
  * stream is idle.  A pipeline wait that exceeds its bound returns
@@ -318,6 +319,18 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
 isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K,
                                   int64_t lda, int64_t ldb, int64_t ldc, double alpha, int slices, void* stream);
 int64_t isdf_gemm_f64_noalloc_capacity(void);
+
+/* Batched 3-D real-to-half-complex DFT -- the transform behind the Coulomb
+ * integrals of Section II, Eq. 1 (the half spectra that isdf_coulomb builds
+ * with options.precision = 1), exposed for verification:
+ *   S[b][qz][qy][qx] = sum_{z,y,x} f[b][z][y][x] exp(-2 pi i (qx x/nx + qy y/ny + qz z/nz)),
+ * qx in [0, nx/2] (the unnormalised D2Z layout), computed in double-float
+ * arithmetic (pairs of FP32 values, about 48 significant bits) on the FP32
+ * pipes.  f: batch x nz x ny x nx FP64; S: batch x nz x ny x (nx/2+1) complex
+ * FP64 (interleaved re, im); DEVICE pointers, S must not overlap f.  Every axis
+ * must be 2^a 3^b <= 128, else ISDF_ERR_ARG (isdf_coulomb then uses cuFFT).
+ * Enqueued on `stream`; returns after the stream is idle. */
+isdf_status isdf_rfft3(const double* f, int nx, int ny, int nz, int64_t batch, double* S, void* stream);
 
 /* Message of the last failed call on this plan (or of the last failed
  * isdf_plan when plan is NULL).  Valid until the next call. */

@@ -771,6 +771,25 @@ isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, i
 
 int64_t isdf_gemm_f64_noalloc_capacity(void) { return int64_t(gemm_noalloc_capacity()); }
 
+isdf_status isdf_rfft3(const double* f, int nx, int ny, int nz, int64_t batch, double* S, void* stream) {
+  if (!f || !S || batch < 1 || !rfft3_df_supported(nx, ny, nz)) {
+    g_plan_error = "invalid arguments to isdf_rfft3 (every axis must be 2^a 3^b <= 128)";
+    return ISDF_ERR_ARG;
+  }
+  if (!is_device_ptr(f) || !is_device_ptr(S)) {
+    g_plan_error = "isdf_rfft3 takes device pointers";
+    return ISDF_ERR_ARG;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  isdf_status st = rfft3_df(nullptr, f, nx, ny, nz, batch, reinterpret_cast<double2*>(S), s);
+  const cudaError_t e = cudaStreamSynchronize(s);
+  if (!st && e != cudaSuccess) {
+    g_plan_error = std::string("isdf_rfft3: ") + cudaGetErrorString(e);
+    st = ISDF_ERR_CUDA;
+  }
+  return st;
+}
+
 const char* isdf_last_error(isdf_plan_t h) {
   if (!h) return g_plan_error.c_str();
   return h->p.err.c_str();

@@ -196,6 +196,12 @@ isdf_status coulomb_run(Plan* p) {
     lv.nq = int64_t(lv.nh[0]) * lv.nh[1] * lv.nh[2];
     if (lv.k == 0) continue;
     if ((st = dalloc_t(p, &lv.spec, size_t(lv.k) * lv.nq, "spectra"))) return st;
+    if (p->opt.precision == 1 && p->fault != "fft_plan" && rfft3_df_supported(lv.n[0], lv.n[1], lv.n[2])) {
+      // double-float transform on the FP32 pipes (the FP64 one is bound by the FP64 rate)
+      Prof pr(p, "coulomb_fft", double(lv.k) * (8.0 * double(lv.ng) + 16.0 * double(lv.nq)), "byte", 3);
+      if ((st = rfft3_df(p, lv.xiT, lv.n[0], lv.n[1], lv.n[2], lv.k, lv.spec, s))) return st;
+      continue;
+    }
     // batches of about 256 MB of input (at least one vector, at most 64)
     int batch = p->opt.col_batch > 0 ? p->opt.col_batch
                                      : int(std::max<int64_t>(1, std::min<int64_t>(64, (int64_t(256) << 20) / (8 * lv.ng))));

@@ -1,0 +1,322 @@
+// Batched 3-D real-to-half-complex DFT in double-float arithmetic: the half
+// spectra S(q) = sum_r f(r) exp(-2 pi i q.r / n) (unnormalised, the layout of
+// a D2Z transform: [qz][qy][qx], qx in [0, nx/2]) that the Coulomb integrals
+// of Section II, Eq. 1 are built from.
+//
+// Every value is a pair of FP32 numbers (hi, lo) with hi + lo the represented
+// number (about 48 significant bits); sums use an error-free two-sum and
+// products an FMA-based two-product, so the transform runs on the FP32 pipes
+// (tens of times the FP64 rate on this GPU) with an error of a few 2^-48 per
+// stage relative to the vector's magnitude.
+//
+// One pass per axis: a CTA loads a tile of lines into shared memory, runs the
+// mixed-radix (4, 2, 3) Stockham stages there and writes the tile back:
+//   x: real lines f[v][z][y][0..nx)   -> complex [v][z][y][0..nx/2]  (into the output)
+//   y: complex lines along y, in place;  z: along z, in place, converted to FP64.
+// A double-float complex value takes 16 bytes like a double2, so the output
+// buffer holds the intermediate passes.  Axes other than 2^a 3^b <= 128 are
+// not handled here (the caller falls back to cuFFT).
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace isdf {
+namespace {
+
+constexpr int kMaxN = 128;
+constexpr int kMaxStages = 8;
+
+struct DF {
+  float hi, lo;
+};
+
+// Error-free transformations with explicitly rounded operations (the
+// compiler must not contract them into FMAs or reassociate them).
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF x, DF y) {
+  DF s = two_sum(x.hi, y.hi);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_neg(DF x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ DF df_sub(DF x, DF y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ DF df_mul(DF x, DF y) {
+  const float p = __fmul_rn(x.hi, y.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);  // exact error of the product
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  return quick_two_sum(p, e);
+}
+__device__ __forceinline__ DF df_half(DF x) { return {__fmul_rn(0.5f, x.hi), __fmul_rn(0.5f, x.lo)}; }
+
+struct DC {
+  DF re, im;
+};
+__device__ __forceinline__ DC dc_add(DC a, DC b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ DC dc_sub(DC a, DC b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ DC dc_mul(DC a, DC b) {
+  return {df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ DC dc_mul_mi(DC a) { return {a.im, df_neg(a.re)}; }  // a * (-i)
+__device__ __forceinline__ DC dc_mul_pi(DC a) { return {df_neg(a.im), a.re}; }  // a * (+i)
+
+__device__ __forceinline__ DF df_from_double(double x) {
+  const float hi = __double2float_rn(x);
+  return {hi, __double2float_rn(x - double(hi))};
+}
+__device__ __forceinline__ double df_to_double(DF x) { return double(x.hi) + double(x.lo); }
+
+__device__ __forceinline__ float4 dc_pack(DC a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
+__device__ __forceinline__ DC dc_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+
+struct FftPass {
+  int n;                    // transform length
+  int nstage;
+  int radix[kMaxStages];
+  int64_t nlines;
+  // line l starts at (l / lin) * lso + (l % lin) * lsi; element e at + e * es
+  // (all in values of the input / output arrays)
+  int64_t lin, lso, lsi, es;
+  int nout;                 // elements written per line (x pass: n / 2 + 1)
+  const float4* tw;         // exp(-2 pi i k / n), k < n
+  const double* in_real;    // x pass input (real), else nullptr
+  float4* io;               // complex data (double-float), in/out
+  double2* out64;           // last pass: FP64 output (same buffer), else nullptr
+};
+
+// one Stockham stage on LPB lines held in shared memory
+template <int R>
+__device__ __forceinline__ void stage(const float4* __restrict__ x, float4* __restrict__ y, const float4* tw, int n,
+                                      int s, int lines, int tid, int nthreads) {
+  const int m = n / (R * s);  // butterflies per line: m * s
+  const int per_line = m * s;
+  for (int b = tid; b < lines * per_line; b += nthreads) {
+    const int li = b / per_line, j = b % per_line;
+    const int p = j / s, q = j % s;
+    const float4* xl = x + li * n;
+    float4* yl = y + li * n;
+    DC a[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) a[t] = dc_unpack(xl[q + s * (p + t * m)]);
+    DC o[R];
+    if (R == 2) {
+      o[0] = dc_add(a[0], a[1]);
+      o[1] = dc_sub(a[0], a[1]);
+    } else if (R == 4) {
+      const DC s02 = dc_add(a[0], a[2]), d02 = dc_sub(a[0], a[2]);
+      const DC s13 = dc_add(a[1], a[3]), d13 = dc_sub(a[1], a[3]);
+      o[0] = dc_add(s02, s13);
+      o[2] = dc_sub(s02, s13);
+      o[1] = dc_add(d02, dc_mul_mi(d13));  // a0 - i a1 - a2 + i a3
+      o[3] = dc_add(d02, dc_mul_pi(d13));  // a0 + i a1 - a2 - i a3
+    } else {  // R == 3: w = exp(-2 pi i / 3) = -1/2 - i sqrt(3)/2
+      const DF k = {0.8660253882408142f, 1.5543625053737742e-08f};  // sqrt(3)/2 as hi + lo
+      const DC b = dc_add(a[1], a[2]), c = dc_sub(a[1], a[2]);
+      o[0] = dc_add(a[0], b);
+      const DC t0 = {df_sub(a[0].re, df_half(b.re)), df_sub(a[0].im, df_half(b.im))};
+      const DC kc = {df_mul(k, c.re), df_mul(k, c.im)};
+      o[1] = dc_add(t0, dc_mul_mi(kc));  // t0 - i (sqrt3/2) c
+      o[2] = dc_add(t0, dc_mul_pi(kc));  // t0 + i (sqrt3/2) c
+    }
+    const int N = n;
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      DC v = o[u];
+      const int e = (p * u * s) % N;
+      if (e) v = dc_mul(v, dc_unpack(tw[e]));
+      yl[q + s * (R * p + u)] = dc_pack(v);
+    }
+  }
+}
+
+template <int LPB>
+__global__ void __launch_bounds__(256) k_fft_pass(FftPass P) {
+  extern __shared__ float4 sm[];
+  float4* buf0 = sm;
+  float4* buf1 = sm + LPB * kMaxN;
+  __shared__ float4 tws[kMaxN];
+  const int n = P.n, tid = threadIdx.x, nt = blockDim.x;
+  for (int i = tid; i < n; i += nt) tws[i] = P.tw[i];
+  const int64_t l0 = int64_t(blockIdx.x) * LPB;
+  const int lines = int(P.nlines - l0 < LPB ? P.nlines - l0 : LPB);
+  // load: consecutive threads take consecutive elements of a line when the
+  // line is contiguous, else consecutive lines of one element
+  const bool contiguous = P.es == 1;
+  for (int idx = tid; idx < lines * n; idx += nt) {
+    int li, e;
+    if (contiguous) {
+      li = idx / n, e = idx % n;
+    } else {
+      e = idx / lines, li = idx % lines;
+    }
+    const int64_t l = l0 + li;
+    const int64_t base = (P.lin ? (l / P.lin) * P.lso + (l % P.lin) * P.lsi : l * P.lsi) + int64_t(e) * P.es;
+    DC v;
+    if (P.in_real) {
+      v.re = df_from_double(P.in_real[base]);
+      v.im = {0.0f, 0.0f};
+    } else {
+      v = dc_unpack(P.io[base]);
+    }
+    buf0[li * n + e] = dc_pack(v);
+  }
+  __syncthreads();
+  float4* x = buf0;
+  float4* y = buf1;
+  int s = 1;
+  for (int st = 0; st < P.nstage; ++st) {
+    const int r = P.radix[st];
+    if (r == 4)
+      stage<4>(x, y, tws, n, s, lines, tid, nt);
+    else if (r == 2)
+      stage<2>(x, y, tws, n, s, lines, tid, nt);
+    else
+      stage<3>(x, y, tws, n, s, lines, tid, nt);
+    __syncthreads();
+    float4* t = x;
+    x = y;
+    y = t;
+    s *= r;
+  }
+  // store the first nout elements of every line
+  const int nout = P.nout;
+  const int64_t lso_o = P.in_real ? 0 : P.lso;  // x pass: output lines are contiguous (stride nout)
+  for (int idx = tid; idx < lines * nout; idx += nt) {
+    int li, e;
+    if (contiguous) {
+      li = idx / nout, e = idx % nout;
+    } else {
+      e = idx / lines, li = idx % lines;
+    }
+    const int64_t l = l0 + li;
+    int64_t base;
+    if (P.in_real)
+      base = l * nout + e;
+    else
+      base = (P.lin ? (l / P.lin) * lso_o + (l % P.lin) * P.lsi : l * P.lsi) + int64_t(e) * P.es;
+    const DC v = dc_unpack(x[li * n + e]);
+    if (P.out64)
+      P.out64[base] = make_double2(df_to_double(v.re), df_to_double(v.im));
+    else
+      P.io[base] = dc_pack(v);
+  }
+}
+
+bool factor(int n, int* radix, int* nstage) {
+  int k = 0, m = n;
+  while (m % 4 == 0 && m > 4 && k < kMaxStages) radix[k++] = 4, m /= 4;
+  while (m % 2 == 0 && k < kMaxStages) radix[k++] = 2, m /= 2;
+  while (m % 3 == 0 && k < kMaxStages) radix[k++] = 3, m /= 3;
+  *nstage = k;
+  return m == 1;
+}
+
+constexpr int kLPB = 16;
+
+}  // namespace
+
+bool rfft3_df_supported(int nx, int ny, int nz) {
+  int r[kMaxStages], k;
+  for (int n : {nx, ny, nz})
+    if (n < 1 || n > kMaxN || !factor(n, r, &k)) return false;
+  return true;
+}
+
+// f: batch x (nz ny nx) FP64, S: batch x (nz ny (nx/2+1)) double2 (device);
+// tw: device scratch of 2 (nx + ny + nz) float4 (twiddle tables).
+isdf_status rfft3_df(Plan* p, const double* f, int nx, int ny, int nz, int64_t batch, double2* S, cudaStream_t s) {
+  if (!rfft3_df_supported(nx, ny, nz)) return fail(p, ISDF_ERR_ARG, "double-float transform: unsupported grid");
+  if (batch <= 0) return ISDF_OK;
+  const int nxh = nx / 2 + 1;
+  // twiddle tables exp(-2 pi i k / n) as double-float, from FP64
+  std::vector<float> tw(size_t(4) * (nx + ny + nz));
+  size_t o = 0;
+  int64_t toff[3];
+  const int ns[3] = {nx, ny, nz};
+  for (int a = 0; a < 3; ++a) {
+    toff[a] = int64_t(o / 4);
+    for (int k = 0; k < ns[a]; ++k) {
+      const double th = -2.0 * 3.14159265358979323846 * double(k) / double(ns[a]);
+      const double c = std::cos(th), sn = std::sin(th);
+      const float ch = float(c), sh = float(sn);
+      tw[o++] = ch;
+      tw[o++] = float(c - double(ch));
+      tw[o++] = sh;
+      tw[o++] = float(sn - double(sh));
+    }
+  }
+  float4* dtw = nullptr;
+  isdf_status st;
+  if ((st = dalloc_t(p, &dtw, tw.size() / 4, "transform twiddles"))) return st;
+  if ((st = cuda_check(p, cudaMemcpyAsync(dtw, tw.data(), sizeof(float) * tw.size(), cudaMemcpyHostToDevice, s),
+                       "twiddle copy"))) {
+    dfree(dtw);
+    return st;
+  }
+  const size_t smem = size_t(2) * kLPB * kMaxN * sizeof(float4);
+  static bool configured = false;
+  if (!configured) {
+    cudaFuncSetAttribute(k_fft_pass<kLPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    configured = true;
+  }
+  float4* io = reinterpret_cast<float4*>(S);
+  const int64_t nq = int64_t(nz) * ny * nxh;
+  auto launch = [&](FftPass P) {
+    const int64_t blocks = (P.nlines + kLPB - 1) / kLPB;
+    k_fft_pass<kLPB><<<unsigned(blocks), 256, smem, s>>>(P);
+    count_launches(1);
+  };
+  // x: lines (v, z, y), contiguous
+  FftPass P{};
+  P.n = nx;
+  factor(nx, P.radix, &P.nstage);
+  P.nlines = batch * nz * ny;
+  P.lin = 0;
+  P.lsi = nx;
+  P.es = 1;
+  P.nout = nxh;
+  P.tw = dtw + toff[0];
+  P.in_real = f;
+  P.io = io;
+  launch(P);
+  // y: lines (v, z, qx), element stride nxh, in place
+  FftPass Q{};
+  Q.n = ny;
+  factor(ny, Q.radix, &Q.nstage);
+  Q.nlines = batch * nz * nxh;
+  Q.lin = nxh;
+  Q.lso = int64_t(ny) * nxh;
+  Q.lsi = 1;
+  Q.es = nxh;
+  Q.nout = ny;
+  Q.tw = dtw + toff[1];
+  Q.io = io;
+  launch(Q);
+  // z: lines (v, qy, qx), element stride ny nxh, in place, FP64 out
+  FftPass R{};
+  R.n = nz;
+  factor(nz, R.radix, &R.nstage);
+  R.nlines = batch * ny * nxh;
+  R.lin = int64_t(ny) * nxh;
+  R.lso = nq;
+  R.lsi = 1;
+  R.es = int64_t(ny) * nxh;
+  R.nout = nz;
+  R.tw = dtw + toff[2];
+  R.io = io;
+  R.out64 = S;
+  launch(R);
+  dfree(dtw);
+  return ISDF_OK;
+}
+
+}  // namespace isdf

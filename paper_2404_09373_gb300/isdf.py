@@ -49,6 +49,7 @@ EXPORTED = [
     "isdf_propose_residual",
     "isdf_gemm_f64_noalloc",
     "isdf_gemm_f64_noalloc_capacity",
+    "isdf_rfft3",
 ]
 
 
@@ -144,6 +145,8 @@ def load_library(build_if_missing: bool = True):
     lib.isdf_propose.restype = c_int
     lib.isdf_propose_residual.argtypes = [c_void_p, c_void_p, c_void_p]
     lib.isdf_propose_residual.restype = c_int
+    lib.isdf_rfft3.argtypes = [c_void_p, c_int, c_int, c_int, c_int64, c_void_p, c_void_p]
+    lib.isdf_rfft3.restype = c_int
     lib.isdf_gemm_f64_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64,
                                           c_int64, c_double, c_int, c_void_p]
     lib.isdf_gemm_f64_noalloc.restype = c_int
@@ -385,6 +388,22 @@ def isdf_propose_residual(plan: Plan, quota):
     out = np.zeros(int(q.sum()), dtype=np.int64)
     plan._check(plan._lib.isdf_propose_residual(plan.handle, q.ctypes.data, out.ctypes.data))
     return out
+
+
+def isdf_rfft3(f, S=None, stream=None):
+    """Half spectra of a batch of real grids (torch CUDA float64, shape (b, nz, ny, nx))
+    -> complex128 tensor (b, nz, ny, nx/2+1), computed by the library's double-float transform."""
+    import torch
+
+    b, nz, ny, nx = f.shape
+    if S is None:
+        S = torch.empty((b, nz, ny, nx // 2 + 1), dtype=torch.complex128, device=f.device)
+    lib = load_library()
+    st = lib.isdf_rfft3(f.data_ptr(), nx, ny, nz, b, S.data_ptr(),
+                        c_void_p(_default_stream() if stream is None else stream))
+    if st != ISDF_OK:
+        raise IsdfError(st, lib.isdf_last_error(None).decode())
+    return S
 
 
 def isdf_kernel_launches() -> int:
