@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--precision", type=int, default=1, help="1: tensor-core products, 0: plain FP64")
     ap.add_argument("--prefilter", type=int, default=1, help="exact candidate prefilter in the selection")
-    ap.add_argument("--select-block", type=int, default=64,
+    ap.add_argument("--select-block", type=int, default=96,
                     help="speculative block size of the selection (0: one FP64 step at a time)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 comparison step")
     ap.add_argument("--batch", action="store_true",

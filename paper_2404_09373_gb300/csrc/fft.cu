@@ -93,15 +93,27 @@ struct FftPass {
   double2* out64;           // last pass: FP64 output (same buffer), else nullptr
 };
 
+// floor(x / d) for x < 2^16, 1 <= d <= 128: with M = ceil(2^32 / d) the high
+// word of x M is exact (the rounding error x (M - 2^32/d) / 2^32 < 2^-16 stays
+// below the gap 1/d between x/d and the next integer).  M = 0 encodes d = 1.
+struct FastDiv {
+  unsigned int d, M;
+};
+__host__ __device__ inline FastDiv fast_div(unsigned int d) {
+  return {d, d == 1 ? 0u : (unsigned int)((0xFFFFFFFFull + d) / d)};
+}
+__device__ __forceinline__ int fdiv(int x, FastDiv f) { return f.M ? int(__umulhi(unsigned(x), f.M)) : x; }
+
 // one Stockham stage on LPB lines held in shared memory
 template <int R>
 __device__ __forceinline__ void stage(const float4* __restrict__ x, float4* __restrict__ y, const float4* tw, int n,
                                       int s, int lines, int tid, int nthreads) {
   const int m = n / (R * s);  // butterflies per line: m * s
   const int per_line = m * s;
+  const FastDiv dl = fast_div(per_line), ds = fast_div(s);
   for (int b = tid; b < lines * per_line; b += nthreads) {
-    const int li = b / per_line, j = b % per_line;
-    const int p = j / s, q = j % s;
+    const int li = fdiv(b, dl), j = b - li * per_line;
+    const int p = fdiv(j, ds), q = j - p * s;
     const float4* xl = x + li * n;
     float4* yl = y + li * n;
     DC a[R];
@@ -127,11 +139,10 @@ __device__ __forceinline__ void stage(const float4* __restrict__ x, float4* __re
       o[1] = dc_add(t0, dc_mul_mi(kc));  // t0 - i (sqrt3/2) c
       o[2] = dc_add(t0, dc_mul_pi(kc));  // t0 + i (sqrt3/2) c
     }
-    const int N = n;
 #pragma unroll
     for (int u = 0; u < R; ++u) {
       DC v = o[u];
-      const int e = (p * u * s) % N;
+      const int e = p * u * s;  // < (m - 1)(R - 1) s < n
       if (e) v = dc_mul(v, dc_unpack(tw[e]));
       yl[q + s * (R * p + u)] = dc_pack(v);
     }
@@ -147,27 +158,33 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass P) {
   const int n = P.n, tid = threadIdx.x, nt = blockDim.x;
   for (int i = tid; i < n; i += nt) tws[i] = P.tw[i];
   const int64_t l0 = int64_t(blockIdx.x) * LPB;
-  const int lines = int(P.nlines - l0 < LPB ? P.nlines - l0 : LPB);
+  const int lines_in = int(P.nlines - l0 < LPB ? P.nlines - l0 : LPB);
+  // x pass: two real lines per complex line (z = f_2c + i f_2c+1), split after
+  const bool pairs = P.in_real != nullptr;
+  const int lines = pairs ? (lines_in + 1) / 2 : lines_in;
   // load: consecutive threads take consecutive elements of a line when the
   // line is contiguous, else consecutive lines of one element
   const bool contiguous = P.es == 1;
-  for (int idx = tid; idx < lines * n; idx += nt) {
+  const FastDiv dn = fast_div(n), dlines = fast_div(lines_in), dout = fast_div(P.nout);
+  if (pairs && (lines_in & 1)) {  // the last complex line has no partner: imaginary part 0
+    float2* h = reinterpret_cast<float2*>(buf0);
+    for (int e = tid; e < n; e += nt) h[2 * ((lines - 1) * n + e) + 1] = make_float2(0.0f, 0.0f);
+  }
+  for (int idx = tid; idx < lines_in * n; idx += nt) {
     int li, e;
     if (contiguous) {
-      li = idx / n, e = idx % n;
+      li = fdiv(idx, dn), e = idx - li * n;
     } else {
-      e = idx / lines, li = idx % lines;
+      e = fdiv(idx, dlines), li = idx - e * lines_in;
     }
     const int64_t l = l0 + li;
     const int64_t base = (P.lin ? (l / P.lin) * P.lso + (l % P.lin) * P.lsi : l * P.lsi) + int64_t(e) * P.es;
-    DC v;
-    if (P.in_real) {
-      v.re = df_from_double(P.in_real[base]);
-      v.im = {0.0f, 0.0f};
+    if (pairs) {
+      const DF v = df_from_double(P.in_real[base]);
+      reinterpret_cast<float2*>(buf0)[2 * ((li >> 1) * n + e) + (li & 1)] = make_float2(v.hi, v.lo);
     } else {
-      v = dc_unpack(P.io[base]);
+      buf0[li * n + e] = P.io[base];
     }
-    buf0[li * n + e] = dc_pack(v);
   }
   __syncthreads();
   float4* x = buf0;
@@ -189,21 +206,35 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass P) {
   }
   // store the first nout elements of every line
   const int nout = P.nout;
-  const int64_t lso_o = P.in_real ? 0 : P.lso;  // x pass: output lines are contiguous (stride nout)
-  for (int idx = tid; idx < lines * nout; idx += nt) {
+  for (int idx = tid; idx < lines_in * nout; idx += nt) {
     int li, e;
     if (contiguous) {
-      li = idx / nout, e = idx % nout;
+      li = fdiv(idx, dout), e = idx - li * nout;
     } else {
-      e = idx / lines, li = idx % lines;
+      e = fdiv(idx, dlines), li = idx - e * lines_in;
     }
     const int64_t l = l0 + li;
+    DC v;
     int64_t base;
-    if (P.in_real)
+    if (pairs) {
+      // Z = F_a + i F_b with F_a, F_b Hermitian:  F_a = (Z_k + conj Z_{n-k}) / 2,
+      // F_b = -i (Z_k - conj Z_{n-k}) / 2
+      const float4* zl = x + (li >> 1) * n;
+      const DC zk = dc_unpack(zl[e]);
+      const DC zc = dc_unpack(zl[e == 0 ? 0 : n - e]);
+      const DC w = {zc.re, df_neg(zc.im)};
+      if (li & 1) {
+        const DC d = dc_sub(zk, w);
+        v = {df_half(d.im), df_half(df_neg(d.re))};
+      } else {
+        const DC sm2 = dc_add(zk, w);
+        v = {df_half(sm2.re), df_half(sm2.im)};
+      }
       base = l * nout + e;
-    else
-      base = (P.lin ? (l / P.lin) * lso_o + (l % P.lin) * P.lsi : l * P.lsi) + int64_t(e) * P.es;
-    const DC v = dc_unpack(x[li * n + e]);
+    } else {
+      v = dc_unpack(x[li * n + e]);
+      base = (P.lin ? (l / P.lin) * P.lso + (l % P.lin) * P.lsi : l * P.lsi) + int64_t(e) * P.es;
+    }
     if (P.out64)
       P.out64[base] = make_double2(df_to_double(v.re), df_to_double(v.im));
     else
