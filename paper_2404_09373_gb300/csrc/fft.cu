@@ -107,15 +107,15 @@ __device__ __forceinline__ int fdiv(int x, FastDiv f) { return f.M ? int(__umulh
 // one Stockham stage on LPB lines held in shared memory
 template <int R>
 __device__ __forceinline__ void stage(const float4* __restrict__ x, float4* __restrict__ y, const float4* tw, int n,
-                                      int s, int lines, int tid, int nthreads) {
+                                      int ld, int s, int lines, int tid, int nthreads) {
   const int m = n / (R * s);  // butterflies per line: m * s
   const int per_line = m * s;
   const FastDiv dl = fast_div(per_line), ds = fast_div(s);
   for (int b = tid; b < lines * per_line; b += nthreads) {
     const int li = fdiv(b, dl), j = b - li * per_line;
     const int p = fdiv(j, ds), q = j - p * s;
-    const float4* xl = x + li * n;
-    float4* yl = y + li * n;
+    const float4* xl = x + li * ld;
+    float4* yl = y + li * ld;
     DC a[R];
 #pragma unroll
     for (int t = 0; t < R; ++t) a[t] = dc_unpack(xl[q + s * (p + t * m)]);
@@ -152,10 +152,13 @@ __device__ __forceinline__ void stage(const float4* __restrict__ x, float4* __re
 template <int LPB>
 __global__ void __launch_bounds__(256) k_fft_pass(FftPass P) {
   extern __shared__ float4 sm[];
-  float4* buf0 = sm;
-  float4* buf1 = sm + LPB * kMaxN;
   __shared__ float4 tws[kMaxN];
   const int n = P.n, tid = threadIdx.x, nt = blockDim.x;
+  // lines n + 1 values apart: consecutive lines of one element fall in
+  // different shared-memory banks
+  const int ld = n + 1;
+  float4* buf0 = sm;
+  float4* buf1 = sm + LPB * ld;
   for (int i = tid; i < n; i += nt) tws[i] = P.tw[i];
   const int64_t l0 = int64_t(blockIdx.x) * LPB;
   const int lines_in = int(P.nlines - l0 < LPB ? P.nlines - l0 : LPB);
@@ -168,7 +171,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass P) {
   const FastDiv dn = fast_div(n), dlines = fast_div(lines_in), dout = fast_div(P.nout);
   if (pairs && (lines_in & 1)) {  // the last complex line has no partner: imaginary part 0
     float2* h = reinterpret_cast<float2*>(buf0);
-    for (int e = tid; e < n; e += nt) h[2 * ((lines - 1) * n + e) + 1] = make_float2(0.0f, 0.0f);
+    for (int e = tid; e < n; e += nt) h[2 * ((lines - 1) * ld + e) + 1] = make_float2(0.0f, 0.0f);
   }
   for (int idx = tid; idx < lines_in * n; idx += nt) {
     int li, e;
@@ -181,9 +184,9 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass P) {
     const int64_t base = (P.lin ? (l / P.lin) * P.lso + (l % P.lin) * P.lsi : l * P.lsi) + int64_t(e) * P.es;
     if (pairs) {
       const DF v = df_from_double(P.in_real[base]);
-      reinterpret_cast<float2*>(buf0)[2 * ((li >> 1) * n + e) + (li & 1)] = make_float2(v.hi, v.lo);
+      reinterpret_cast<float2*>(buf0)[2 * ((li >> 1) * ld + e) + (li & 1)] = make_float2(v.hi, v.lo);
     } else {
-      buf0[li * n + e] = P.io[base];
+      buf0[li * ld + e] = P.io[base];
     }
   }
   __syncthreads();
@@ -193,11 +196,11 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass P) {
   for (int st = 0; st < P.nstage; ++st) {
     const int r = P.radix[st];
     if (r == 4)
-      stage<4>(x, y, tws, n, s, lines, tid, nt);
+      stage<4>(x, y, tws, n, ld, s, lines, tid, nt);
     else if (r == 2)
-      stage<2>(x, y, tws, n, s, lines, tid, nt);
+      stage<2>(x, y, tws, n, ld, s, lines, tid, nt);
     else
-      stage<3>(x, y, tws, n, s, lines, tid, nt);
+      stage<3>(x, y, tws, n, ld, s, lines, tid, nt);
     __syncthreads();
     float4* t = x;
     x = y;
@@ -219,7 +222,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass P) {
     if (pairs) {
       // Z = F_a + i F_b with F_a, F_b Hermitian:  F_a = (Z_k + conj Z_{n-k}) / 2,
       // F_b = -i (Z_k - conj Z_{n-k}) / 2
-      const float4* zl = x + (li >> 1) * n;
+      const float4* zl = x + (li >> 1) * ld;
       const DC zk = dc_unpack(zl[e]);
       const DC zc = dc_unpack(zl[e == 0 ? 0 : n - e]);
       const DC w = {zc.re, df_neg(zc.im)};
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass P) {
       }
       base = l * nout + e;
     } else {
-      v = dc_unpack(x[li * n + e]);
+      v = dc_unpack(x[li * ld + e]);
       base = (P.lin ? (l / P.lin) * P.lso + (l % P.lin) * P.lsi : l * P.lsi) + int64_t(e) * P.es;
     }
     if (P.out64)
@@ -293,16 +296,17 @@ isdf_status rfft3_df(Plan* p, const double* f, int nx, int ny, int nz, int64_t b
     dfree(dtw);
     return st;
   }
-  const size_t smem = size_t(2) * kLPB * kMaxN * sizeof(float4);
   static bool configured = false;
   if (!configured) {
-    cudaFuncSetAttribute(k_fft_pass<kLPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+    cudaFuncSetAttribute(k_fft_pass<kLPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         int(size_t(2) * kLPB * (kMaxN + 1) * sizeof(float4)));
     configured = true;
   }
   float4* io = reinterpret_cast<float4*>(S);
   const int64_t nq = int64_t(nz) * ny * nxh;
   auto launch = [&](FftPass P) {
     const int64_t blocks = (P.nlines + kLPB - 1) / kLPB;
+    const size_t smem = size_t(2) * kLPB * (P.n + 1) * sizeof(float4);  // two tiles of lines
     k_fft_pass<kLPB><<<unsigned(blocks), 256, smem, s>>>(P);
     count_launches(1);
   };
