@@ -97,7 +97,11 @@ typedef struct {
  *               1: the dense contractions of the fit, the Coulomb matrix and
  *                  the exchange build on the tensor cores with FP64-accurate
  *                  sliced BF16 products (FP64 pivot decisions, Cholesky and
- *                  energy reduction are unchanged)
+ *                  energy reduction are unchanged); the fit is kept in the
+ *                  factored form Xi = ZC (CC^T)^-1 and the Coulomb matrix is
+ *                  built as W (ZC^T v ZC) W with W = (CC^T)^-1, so the
+ *                  interpolation vectors and the fit residual are computed
+ *                  only when isdf_get asks for them
  *   tie_rel, tie_abs  pivot tie rule: among points whose residual is at
  *               least d_max - max(tie_rel d_max, tie_abs d_0) the smallest
  *               (level, g) wins (defaults 1e-9, 1e-13)
@@ -200,14 +204,16 @@ enum {
   ISDF_GET_XN = 4,         /* double[N x nip] X^N                          */
   ISDF_GET_V = 5,          /* double[nip x nip]                            */
   ISDF_GET_XI_LEVEL0 = 6,  /* double[k_l x N_g,l] Xi^T of level 0; add the
-                              level index for the others                   */
+                              level index for the others (precision 1:
+                              computed on the first request)               */
   ISDF_GET_NPOINTS = 4 + 16,  /* int64[1]: grid points of all levels       */
   ISDF_GET_FIT_RESIDUAL = 5 + 16, /* double[2 nlevel]: per level the largest
                               and the summed residual w (M(g,g) - M(g,P)
                               M_PP^-1 M(P,g)) over all grid points after
                               isdf_fit, i.e. the Schur complement left by the
                               pivots (sum = weighted fit error^2); on a level
-                              without pivots, of w M(g,g)                  */
+                              without pivots, of w M(g,g) (precision 1:
+                              computed on the first request)               */
   ISDF_GET_PHI_LEVEL0 = 10, /* double[|G_l| x N_g,l] basis values of level
                               0 (rows: functions of the level in index order,
                               then coarser ones); add the level index      */

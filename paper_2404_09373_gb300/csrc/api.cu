@@ -166,6 +166,8 @@ void free_plan(Plan* p) {
     dfree(lv.d_pg);
     dfree(lv.xiT);
     dfree(lv.resid);
+    dfree(lv.zct);
+    dfree(lv.rinv);
     dfree(lv.spec);
     lv = Level();
   }
@@ -528,7 +530,7 @@ int64_t isdf_get_size(isdf_plan_t h, int what) {
   }
   if (what >= ISDF_GET_XI_LEVEL0 && what < ISDF_GET_XI_LEVEL0 + p->nlev) {
     const Level& lv = p->lev[what - ISDF_GET_XI_LEVEL0];
-    return (p->state >= 2 && lv.xiT) ? int64_t(lv.k) * lv.ng : 0;
+    return (p->state >= 2 && (lv.xiT || lv.zct)) ? int64_t(lv.k) * lv.ng : 0;
   }
   if (what >= ISDF_GET_PHI_LEVEL0 && what < ISDF_GET_PHI_LEVEL0 + p->nlev) {
     const Level& lv = p->lev[what - ISDF_GET_PHI_LEVEL0];
@@ -572,8 +574,11 @@ isdf_status isdf_get(isdf_plan_t h, int what, void* dst) {
       const int64_t v = p->ntot;
       return put_host(&v, sizeof(v));
     }
-    case ISDF_GET_FIT_RESIDUAL:
+    case ISDF_GET_FIT_RESIDUAL: {
+      isdf_status st = fit_residual_run(p);  // a factored fit computes it on request
+      if (st) return st;
       return put_host(p->fit_resid, sizeof(double) * 2 * p->nlev);
+    }
     case ISDF_GET_SELECT_STATS: {
       const int64_t v[2] = {p->sel_blocks, p->sel_plain_steps};
       return put_host(v, sizeof(v));
@@ -581,8 +586,11 @@ isdf_status isdf_get(isdf_plan_t h, int what, void* dst) {
     default:
       break;
   }
-  if (what >= ISDF_GET_XI_LEVEL0 && what < ISDF_GET_XI_LEVEL0 + p->nlev)
+  if (what >= ISDF_GET_XI_LEVEL0 && what < ISDF_GET_XI_LEVEL0 + p->nlev) {
+    isdf_status st = fit_xi_run(p, what - ISDF_GET_XI_LEVEL0);  // a factored fit makes Xi on request
+    if (st) return st;
     return from_device(p, static_cast<double*>(dst), p->lev[what - ISDF_GET_XI_LEVEL0].xiT, size_t(n), true);
+  }
   if (what >= ISDF_GET_PHI_LEVEL0 && what < ISDF_GET_PHI_LEVEL0 + p->nlev)
     return from_device(p, static_cast<double*>(dst), p->lev[what - ISDF_GET_PHI_LEVEL0].phi, size_t(n), true);
   return fail(p, ISDF_ERR_ARG, "unknown isdf_get selector");
@@ -706,7 +714,8 @@ isdf_status isdf_propose_residual(isdf_plan_t h, const int64_t* quota, int64_t* 
   isdf_status st = ISDF_OK;
   if (!dev && (st = dalloc_t(p, &stage, size_t(ncand), "candidates"))) return st;
   if (!dev) d = stage;
-  st = learn_propose_residual(p, q.data(), d);
+  st = fit_residual_run(p);
+  if (!st) st = learn_propose_residual(p, q.data(), d);
   if (!st && !dev) st = from_device(p, cand_out, stage, size_t(ncand), true);
   dfree(stage);
   return st;

@@ -145,7 +145,9 @@ __global__ void k_sqrt_inplace(int64_t n, double* w) {
 isdf_status coulomb_block_tc(Plan* p, const double2* left, const Level& la, const Level& lb, double* wt2, bool same,
                              double* Cblk) {
   cudaStream_t s = p->stream;
-  const int S = 5;
+  // 8 digits (FP64-grade) when the blocks are those of ZC: W = (CC^T)^-1 applied
+  // afterwards amplifies their error by up to cond(CC^T); else 5
+  const int S = (la.zct || lb.zct) ? 8 : 5;
   const int64_t K2 = 2 * lb.nq;
   k_sqrt_inplace<<<unsigned((K2 + 255) / 256), 256, 0, s>>>(K2, wt2);
   count_launches(1);
@@ -181,6 +183,87 @@ isdf_status coulomb_block_tc(Plan* p, const double2* left, const Level& la, cons
 
 }  // namespace
 
+namespace {
+
+// V_ab <- W_a V_ab W_b for every block of levels a <= b (then mirrored), with
+// W_a = R_a^-T R_a^-1 = (C C^T)_a^-1, all in FP64-grade 8-digit products:
+// the blocks computed from the spectra of ZC are those of Xi = ZC W.
+isdf_status apply_w(Plan* p) {
+  cudaStream_t s = p->stream;
+  const int S = 8, bn = oz_bn(S);
+  const int64_t nip = p->nip;
+  double* W[ISDF_MAX_LEVELS] = {nullptr, nullptr, nullptr, nullptr};
+  double* T = nullptr;
+  OzOperand a, b;
+  auto cleanup = [&]() {
+    for (int l = 0; l < p->nlev; ++l) dfree(W[l]);
+    dfree(T);
+    oz_free(a);
+    oz_free(b);
+  };
+  isdf_status st;
+  int kmax = 1;
+  for (int l = 0; l < p->nlev; ++l) kmax = std::max(kmax, p->lev[l].k);
+  if ((st = dalloc_t(p, &T, size_t(kmax) * kmax, "Coulomb transform")) ||
+      (st = oz_alloc(p, a, kmax, kmax, 128, S, "Coulomb transform")) ||
+      (st = oz_alloc(p, b, kmax, kmax, bn, S, "Coulomb transform")))
+    return cleanup(), st;
+  auto view = [&](OzOperand& op, int64_t rows, int64_t K) {
+    op.rows = rows;
+    op.K = K;
+    op.nrt = (rows + op.rt - 1) / op.rt;
+    op.nkt = (K + kOzBK - 1) / kOzBK;
+    op.kst = op.nkt;
+  };
+  double flop = 0.0;
+  for (int l = 0; l < p->nlev; ++l) flop += 2.0 * std::pow(double(p->lev[l].k), 3.0);
+  for (int x = 0; x < p->nlev; ++x)
+    for (int y = x; y < p->nlev; ++y) flop += 2.0 * 2.0 * double(p->lev[x].k) * p->lev[y].k * (p->lev[x].k + p->lev[y].k) / 2.0;
+  Prof pr(p, "coulomb_w", flop, "flop", 0);
+  // W_l[m][n] = sum_kk R^-1[kk][m] R^-1[kk][n]
+  for (int l = 0; l < p->nlev; ++l) {
+    const int k = p->lev[l].k;
+    if (!k) continue;
+    if ((st = dalloc_t(p, &W[l], size_t(k) * k, "W"))) return cleanup(), st;
+    view(a, k, k);
+    view(b, k, k);
+    oz_slice(p->lev[l].rinv, 1, k, nullptr, 1.0, a, s);
+    oz_slice(p->lev[l].rinv, 1, k, nullptr, 1.0, b, s);
+    oz_gemm(a, b, W[l], k, 0, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+  }
+  for (int x = 0; x < p->nlev; ++x) {
+    const int ka = p->lev[x].k;
+    if (!ka) continue;
+    for (int y = x; y < p->nlev; ++y) {
+      const int kb = p->lev[y].k;
+      if (!kb) continue;
+      double* blk = p->V + int64_t(p->poff[x]) * nip + p->poff[y];
+      // T = V_Z,ab W_b   (T[m][n] = sum_j V[m][j] W_b[n][j], W_b symmetric)
+      view(a, ka, kb);
+      view(b, kb, kb);
+      oz_slice(blk, nip, 1, nullptr, 1.0, a, s);
+      oz_slice(W[y], kb, 1, nullptr, 1.0, b, s);
+      oz_gemm(a, b, T, kb, 0, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      // V_ab = W_a T   (V[m][n] = sum_i W_a[m][i] T[i][n])
+      view(a, ka, ka);
+      view(b, kb, ka);
+      oz_slice(W[x], ka, 1, nullptr, 1.0, a, s);
+      oz_slice(T, 1, kb, nullptr, 1.0, b, s);
+      oz_gemm(a, b, blk, nip, 0, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      if (x != y) {
+        const int64_t tot = int64_t(ka) * kb;
+        k_mirror<<<unsigned((tot + 255) / 256), 256, 0, s>>>(p->V, nip, p->poff[x], p->poff[y], ka, kb, 0);
+        count_launches(1);
+      }
+    }
+  }
+  st = oz_check(p);
+  cleanup();
+  return st;
+}
+
+}  // namespace
+
 isdf_status coulomb_run(Plan* p) {
   cudaStream_t s = p->stream;
   isdf_status st;
@@ -199,7 +282,7 @@ isdf_status coulomb_run(Plan* p) {
     if (p->opt.precision == 1 && p->fault != "fft_plan" && rfft3_df_supported(lv.n[0], lv.n[1], lv.n[2])) {
       // double-float transform on the FP32 pipes (the FP64 one is bound by the FP64 rate)
       Prof pr(p, "coulomb_fft", double(lv.k) * (8.0 * double(lv.ng) + 16.0 * double(lv.nq)), "byte", 3);
-      if ((st = rfft3_df(p, lv.xiT, lv.n[0], lv.n[1], lv.n[2], lv.k, lv.spec, s))) return st;
+      if ((st = rfft3_df(p, lv.zct ? lv.zct : lv.xiT, lv.n[0], lv.n[1], lv.n[2], lv.k, lv.spec, s))) return st;
       continue;
     }
     // batches of about 256 MB of input (at least one vector, at most 64)
@@ -220,7 +303,8 @@ isdf_status coulomb_run(Plan* p) {
       // every full batch with this plan, then the remainder with its own
       const int nfull = (lv.k - b0) / nb;
       for (int c = 0; c < nfull && r == CUFFT_SUCCESS; ++c) {
-        r = cufftExecD2Z(h, lv.xiT + int64_t(b0) * lv.ng, reinterpret_cast<cufftDoubleComplex*>(lv.spec + int64_t(b0) * lv.nq));
+        r = cufftExecD2Z(h, (lv.zct ? lv.zct : lv.xiT) + int64_t(b0) * lv.ng,
+                         reinterpret_cast<cufftDoubleComplex*>(lv.spec + int64_t(b0) * lv.nq));
         b0 += nb;
       }
       // the handle goes back to the pool only once its work on this stream is done
@@ -294,7 +378,10 @@ isdf_status coulomb_run(Plan* p) {
       if (st) return st;
     }
   }
-  return ISDF_OK;
+  // A factored fit (Xi = ZC W, W = R^-T R^-1) transformed ZC: V = W V_Z W
+  bool factored = false;
+  for (int l = 0; l < p->nlev; ++l) factored = factored || p->lev[l].zct != nullptr;
+  return factored ? apply_w(p) : ISDF_OK;
 }
 
 }  // namespace isdf

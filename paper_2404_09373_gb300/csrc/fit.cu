@@ -103,22 +103,26 @@ isdf_status fit_products_tc(Plan* p, Level& lv, int k, const double* phiP, doubl
   return ISDF_OK;
 }
 
-isdf_status fit_solve_tc(Plan* p, int k, double* zct, double* y, const double* li, int64_t ng) {
+// Y = R^-1 ZC^T^T ([k][ng]); then, if xi_out, Xi^T = R^-T Y into xi_out
+// (which may be zct itself).
+isdf_status fit_solve_tc(Plan* p, int k, const double* zct, double* y, const double* li, int64_t ng, double* xi_out) {
   cudaStream_t s = p->stream;
   const int S = 5;
   OzOperand a, b;
   isdf_status st;
-  Prof pr(p, "fit_solve", 2.0 * double(k) * double(k + 1) * double(ng), "flop", 0);
+  Prof pr(p, "fit_solve", (xi_out ? 2.0 : 1.0) * double(k) * double(k + 1) * double(ng), "flop", 0);
   // Y^T[g][j] = sum_kk Z^T[g][kk] R^-1[j][kk]   (R^-1 lower: kk <= j)
   if ((st = oz_alloc(p, a, ng, k, 128, S, "solve slices")) || (st = oz_alloc(p, b, k, k, oz_bn(S), S, "solve slices")))
     return oz_free(a), oz_free(b), st;
   oz_slice(zct, 1, ng, nullptr, 1.0, a, s);
   oz_slice(li, k, 1, nullptr, 1.0, b, s);
   oz_gemm(a, b, y, ng, 1, 1.0, 1, 0, 1, nullptr, p->d_ozerr, s);
-  // Xi^T[j][g] = sum_kk Y[kk][g] R^-1[kk][j]   (R^-T upper: kk >= j)
-  oz_slice(y, 1, ng, nullptr, 1.0, a, s);
-  oz_slice(li, 1, k, nullptr, 1.0, b, s);
-  oz_gemm(a, b, zct, ng, 1, 1.0, 2, 0, 1, nullptr, p->d_ozerr, s);
+  if (xi_out) {
+    // Xi^T[j][g] = sum_kk Y[kk][g] R^-1[kk][j]   (R^-T upper: kk >= j)
+    oz_slice(y, 1, ng, nullptr, 1.0, a, s);
+    oz_slice(li, 1, k, nullptr, 1.0, b, s);
+    oz_gemm(a, b, xi_out, ng, 1, 1.0, 2, 0, 1, nullptr, p->d_ozerr, s);
+  }
   oz_free(a);
   oz_free(b);
   return ISDF_OK;
@@ -156,12 +160,17 @@ __global__ void k_fit_residual(const double* __restrict__ phi, int64_t ng, int n
 isdf_status fit_run(Plan* p) {
   cudaStream_t s = p->stream;
   isdf_status st;
+  p->resid_ready = false;
   for (int l = 0; l < p->nlev; ++l) {
     Level& lv = p->lev[l];
     dfree(lv.xiT);
     lv.xiT = nullptr;
     dfree(lv.resid);
     lv.resid = nullptr;
+    dfree(lv.zct);
+    lv.zct = nullptr;
+    dfree(lv.rinv);
+    lv.rinv = nullptr;
     if ((st = dalloc_t(p, &lv.resid, size_t(lv.ng), "fit residual"))) return st;
     if (lv.k == 0) {
       // no pivots: the residual is the whole diagonal w M(g,g)
@@ -195,7 +204,11 @@ isdf_status fit_run(Plan* p) {
       dfree(zct);
       return st;
     }
-    lv.xiT = zct;
+    const bool factored = p->opt.precision == 1;  // keep ZC^T and R^-1; Xi only on request
+    if (factored)
+      lv.zct = zct;
+    else
+      lv.xiT = zct;
     const int64_t np = int64_t(lv.nG) * k;
     count_launches(2 + (p->opt.reg_rel > 0.0));
     k_gather_phiP<<<unsigned((np + 255) / 256), 256, 0, s>>>(lv.nG, k, lv.phi, ng, lv.d_pg, phiP);
@@ -234,11 +247,16 @@ isdf_status fit_run(Plan* p) {
       Prof pr(p, "fit_trtri", double(k) * k * k / 3.0, "flop", 1 + 2 * (nb - 1));
       dtrtri_lower(cc, li, k, scr, s);
     }
-    if (p->opt.precision == 1) {
-      if ((st = fit_solve_tc(p, k, zct, y, li, ng))) {
-        cleanup();
-        return st;
-      }
+    if (factored) {
+      // Coulomb and exchange need Xi only through V = W (ZC^T v ZC) W with
+      // W = R^-T R^-1 (see coulomb.cu): no solve over the grid here
+      lv.rinv = li;
+      li = nullptr;
+      st = cuda_check(p, cudaStreamSynchronize(s), "fit");
+      if (!st) st = oz_check(p);
+      cleanup();
+      if (st) return st;
+      continue;
     } else {
     Prof pr_solve(p, "fit_solve", 2.0 * double(k) * double(k + 1) * double(ng), "flop", 2);
     GemmArgs g1;  // Y = R^-1 ZC^T^T (R^-1 lower triangular)
@@ -277,11 +295,65 @@ isdf_status fit_run(Plan* p) {
       cudaMemcpyAsync(&p->fit_resid[2 * l], scr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
     }
     st = cuda_check(p, cudaStreamSynchronize(s), "fit");
-    if (!st && p->opt.precision == 1) st = oz_check(p);
     cleanup();
     if (st) return st;
   }
+  p->resid_ready = p->opt.precision != 1;
   return gather_pivot_factors(p);
+}
+
+// Residual statistics of a factored fit: Y = R^-1 ZC^T^T, then w (M(g,g) - |Y[:,g]|^2).
+isdf_status fit_residual_run(Plan* p) {
+  if (p->resid_ready) return ISDF_OK;
+  cudaStream_t s = p->stream;
+  isdf_status st;
+  for (int l = 0; l < p->nlev; ++l) {
+    Level& lv = p->lev[l];
+    if (lv.k == 0 || !lv.zct) continue;  // a level without pivots was done by the fit
+    double *y = nullptr, *scr = nullptr;
+    if ((st = dalloc_t(p, &y, size_t(lv.k) * lv.ng, "fit scratch")) || (st = dalloc_t(p, &scr, 2, "residual statistics"))) {
+      dfree(y);
+      return st;
+    }
+    st = fit_solve_tc(p, lv.k, lv.zct, y, lv.rinv, lv.ng, nullptr);
+    if (!st) {
+      cudaMemsetAsync(scr, 0, 2 * sizeof(double), s);
+      k_fit_residual<<<152 * 4, 256, 0, s>>>(lv.phi, lv.ng, lv.nL, lv.nG, lv.w, y, lv.k,
+                                             reinterpret_cast<unsigned long long*>(scr), scr + 1, lv.resid);
+      count_launches(1);
+      cudaMemcpyAsync(&p->fit_resid[2 * l], scr, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+      st = cuda_check(p, cudaStreamSynchronize(s), "fit residual");
+      if (!st) st = oz_check(p);
+    }
+    dfree(y);
+    dfree(scr);
+    if (st) return st;
+  }
+  p->resid_ready = true;
+  return ISDF_OK;
+}
+
+// Xi^T of one level of a factored fit: Xi^T = R^-T R^-1 ZC^T^T.
+isdf_status fit_xi_run(Plan* p, int l) {
+  Level& lv = p->lev[l];
+  if (lv.xiT || lv.k == 0 || !lv.zct) return ISDF_OK;
+  isdf_status st;
+  double *y = nullptr, *xi = nullptr;
+  if ((st = dalloc_t(p, &y, size_t(lv.k) * lv.ng, "fit scratch")) ||
+      (st = dalloc_t(p, &xi, size_t(lv.k) * lv.ng, "interpolation vectors"))) {
+    dfree(y);
+    return st;
+  }
+  st = fit_solve_tc(p, lv.k, lv.zct, y, lv.rinv, lv.ng, xi);
+  if (!st) st = cuda_check(p, cudaStreamSynchronize(p->stream), "interpolation vectors");
+  if (!st) st = oz_check(p);
+  dfree(y);
+  if (st) {
+    dfree(xi);
+    return st;
+  }
+  lv.xiT = xi;
+  return ISDF_OK;
 }
 
 }  // namespace isdf

@@ -34,8 +34,11 @@ struct Level {
   int k = 0;                 // pivots on this level
   std::vector<int64_t> pg;   // pivot grid indices (selection order)
   int64_t* d_pg = nullptr;
-  double* xiT = nullptr;     // Xi^T [k][ng]
+  double* xiT = nullptr;     // Xi^T [k][ng] (precision 1: made on request from zct and rinv)
   float* resid = nullptr;    // fit residual per grid point (FP32 copy, for proposals)
+  // precision 1 keeps the fit in factored form, Xi = ZC W with W = R^-T R^-1:
+  double* zct = nullptr;     // ZC^T [k][ng]
+  double* rinv = nullptr;    // R^-1 [k][k], lower triangular (CC^T = R R^T)
   // Coulomb
   int nh[3] = {0, 0, 0};     // half-spectrum dims (nx/2+1, ny, nz)
   int64_t nq = 0;            // half-spectrum modes
@@ -92,6 +95,7 @@ struct Plan {
   int* d_err = nullptr;         // device error word (Cholesky breakdown etc.)
   int* d_ozerr = nullptr;       // tensor-core pipeline error word
   double fit_resid[2 * ISDF_MAX_LEVELS] = {0};  // per level: max and sum of the fit residual
+  bool resid_ready = false;     // fit_resid / lev[].resid computed for the current fit
   std::string err;
   std::string fault;            // host fault injection (ISDF_FAULT)
   // profiling
@@ -125,6 +129,8 @@ bool is_device_ptr(const void* ptr);
 isdf_status basis_build(Plan* p);                                    // basis.cu
 isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>* cand, int* nfound);  // select.cu
 isdf_status fit_run(Plan* p);                                        // fit.cu
+isdf_status fit_residual_run(Plan* p);  // fit.cu: residual statistics on request (precision 1)
+isdf_status fit_xi_run(Plan* p, int level);  // fit.cu: Xi^T of a level on request (precision 1)
 isdf_status coulomb_run(Plan* p);                                    // coulomb.cu
 isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* Ex);  // exchange.cu
 isdf_status gather_pivot_factors(Plan* p);                           // basis.cu
