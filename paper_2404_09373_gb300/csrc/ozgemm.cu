@@ -335,19 +335,24 @@ struct OzCfg {
   static constexpr int stageA = S * tileA;
   static constexpr int stageB = S * tileB;
   static constexpr int stage = stageA + stageB;
-  static constexpr int budget = 220 * 1024 - 2048;
+  static constexpr int cols = S * BN;
+  static constexpr bool exact = S >= 7;
+  // two CTAs per SM when the accumulators take at most half of tensor memory:
+  // one CTA's pipeline fill and accumulator drain overlap the other's MMAs
+  static constexpr bool dual = !exact && cols <= 256;
+  static constexpr int min_blocks = dual ? 2 : 1;
+  static constexpr int budget = dual ? 115712 - 2048 : 220 * 1024 - 2048;
   static constexpr int nst = budget / stage < 4 ? budget / stage : 4;
   static constexpr int smem = nst * stage + 2048;  // + barriers and 1024-byte alignment slack
-  static constexpr int cols = S * BN;
   static constexpr uint32_t tcols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
   // S = 8: levels 0..5 are kept exact (chunks of 512 k keep their integer
   // sums at most 2^24; levels 6, 7 weigh less than 2^-42, where FP32 rounding
   // is harmless) and summed in integers; else double-float
-  static constexpr bool exact = S >= 7;
   static constexpr int kc = exact ? 512 / kBK : kKcTiles;  // k tiles per chunk
   // epilogue warps: two per tensor-memory lane quarter (BN/2 columns each),
-  // three when exact (BN/3 columns each, so the integer state fits in registers)
-  static constexpr int epi = exact ? 12 : 8;
+  // three when exact (BN/3 columns each, so the integer state fits in
+  // registers), one when two CTAs share the SM
+  static constexpr int epi = exact ? 12 : dual ? 4 : 8;
   static constexpr int threads = 32 * (2 + epi);
   static_assert(!exact || S == 8, "the integer epilogue splits the levels of exactly 8 digits");
   static_assert(cols <= 512, "levels x BN must fit in tensor memory");
@@ -357,7 +362,7 @@ struct OzCfg {
 };
 
 template <int S, int BN>
-__global__ void __launch_bounds__(OzCfg<S, BN>::threads, 1) k_oz_gemm(OzGemmParams P) {
+__global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_blocks) k_oz_gemm(OzGemmParams P) {
   using Cfg = OzCfg<S, BN>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -652,6 +657,7 @@ void launch_oz(const OzGemmParams& P, dim3 grid, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
     cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::smem);
+    cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     configured = true;
   }
   k_oz_gemm<S, BN><<<grid, Cfg::threads, Cfg::smem, s>>>(P);
@@ -723,7 +729,8 @@ void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzO
   count_launches(1);
 }
 
-int oz_bn(int S) { return S == 5 ? 96 : S == 8 ? 48 : 64; }  // S levels x BN columns fill at most 512 of tensor memory
+// S levels x BN columns of tensor memory: 5 x 48 (two CTAs per SM), 6 x 64, 8 x 48
+int oz_bn(int S) { return S == 5 ? 48 : S == 8 ? 48 : 64; }
 
 void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, double alpha, int tri, int sym,
              int splits, double* work, int* err, cudaStream_t s) {
@@ -748,7 +755,7 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   P.err = err;
   dim3 grid(unsigned(B.nrt), unsigned(A.nrt), unsigned(P.splits));
   if (A.S == 5)
-    launch_oz<5, 96>(P, grid, s);
+    launch_oz<5, 48>(P, grid, s);
   else if (A.S == 8)
     launch_oz<8, 48>(P, grid, s);
   else
