@@ -29,6 +29,7 @@
 // lets its copies and MMAs in flight finish, frees tensor memory and exits.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <mutex>
 #include <string>
 
@@ -156,6 +157,48 @@ __device__ __forceinline__ double scaled_to_double(float f, int e) {
   return __longlong_as_double((long long)bits);
 }
 
+// An integer-valued float (|x| < 2^62) as a 64-bit integer without the
+// 64-bit conversion instruction, which runs on the narrow FP64 unit: below
+// 2^23 a 32-bit conversion is exact, above it the value is its significand
+// shifted left.
+__device__ __forceinline__ long long intf_to_ll(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const int ef = int((b >> 23) & 0xFF);
+  if (ef < 150) return (long long)__float2int_rz(x);
+  const long long m = (long long)((b & 0x7FFFFFu) | 0x800000u) << (ef - 150);
+  return (b >> 31) ? -m : m;
+}
+
+// (th + rem 2^-28) 2^e rounded once to the nearest double (ties to even),
+// from the fixed-point value with integer operations; outside the normal
+// range it takes the FP64 route.
+__device__ __forceinline__ double fixed_to_double(long long th, uint32_t rem, int e) {
+  const __int128 X = ((__int128)th << 28) + (__int128)rem;  // value X 2^(e - 28)
+  if (X == 0) return 0.0;
+  const bool neg = X < 0;
+  const unsigned __int128 U = neg ? (unsigned __int128)(-X) : (unsigned __int128)X;
+  const uint64_t hi = uint64_t(U >> 64), lo = uint64_t(U);
+  const int L = hi ? 128 - __clzll((long long)hi) : 64 - __clzll((long long)lo);  // bit length
+  int E = L - 1 + e - 28;
+  uint64_t M;  // significand, 53 bits
+  if (L <= 53) {
+    M = lo << (53 - L);
+  } else {
+    const int sh = L - 53;
+    const unsigned __int128 q = U >> sh;
+    const unsigned __int128 r = U - (q << sh);
+    const unsigned __int128 half = (unsigned __int128)1 << (sh - 1);
+    M = uint64_t(q);
+    if (r > half || (r == half && (M & 1ull))) {
+      ++M;
+      if (M >> 53) M >>= 1, ++E;
+    }
+  }
+  if (E < -1022 || E > 1023) return ldexp(neg ? -double(M) : double(M), E - 52);
+  const uint64_t bits = (uint64_t(neg) << 63) | (uint64_t(E + 1023) << 52) | (M & 0xFFFFFFFFFFFFFull);
+  return __longlong_as_double((long long)bits);
+}
+
 // ---------------------------------------------------------------- slicing
 
 // |x| as an order-preserving integer key (finite doubles)
@@ -203,7 +246,17 @@ __device__ __forceinline__ int64_t row_base(const OzMap& rm, const int* ridx, in
   return ridx ? int64_t(ridx[r]) * rm.si : map_at(rm, r);
 }
 
+// |mul * kw[k] * v| as an order-preserving key
+__device__ __forceinline__ uint64_t key_at(double v, int64_t k, const double* __restrict__ kw, double mul) {
+  if (mul != 1.0) v *= mul;
+  if (kw) v *= kw[k];
+  return abs_key(v);
+}
+
+__device__ __forceinline__ uint64_t umax64(uint64_t a, uint64_t b) { return a > b ? a : b; }
+
 // e_r: max_k |x(r,k)| < 2^e_r, x = mul * kw[k] * src[row(r) + map_k(k)]; one thread per row
+// (four loads in flight per thread on the plain-stride path)
 __global__ void k_oz_rowexp_thread(const double* __restrict__ src, OzMap rm, OzMap km, int64_t rows, int64_t K,
                                    const double* __restrict__ kw, double mul, const int* __restrict__ ridx,
                                    int* __restrict__ exps) {
@@ -211,19 +264,27 @@ __global__ void k_oz_rowexp_thread(const double* __restrict__ src, OzMap rm, OzM
   if (r >= rows) return;
   const double* row = src + row_base(rm, ridx, r);
   uint64_t m = 0;
-  int64_t q = 0, rem = 0;  // k = q km.in + rem, advanced without division
-  for (int64_t k = 0; k < K; ++k) {
-    double v = row[km.in ? q * km.so + rem * km.si : k * km.si];
-    if (km.in && ++rem == km.in) rem = 0, ++q;
-    if (mul != 1.0) v *= mul;
-    if (kw) v *= kw[k];
-    const uint64_t key = abs_key(v);
-    m = key > m ? key : m;
+  if (km.in == 0) {
+    const int64_t si = km.si;
+    int64_t k = 0;
+    for (; k + 4 <= K; k += 4) {
+      const double v0 = row[k * si], v1 = row[(k + 1) * si], v2 = row[(k + 2) * si], v3 = row[(k + 3) * si];
+      m = umax64(m, umax64(umax64(key_at(v0, k, kw, mul), key_at(v1, k + 1, kw, mul)),
+                           umax64(key_at(v2, k + 2, kw, mul), key_at(v3, k + 3, kw, mul))));
+    }
+    for (; k < K; ++k) m = umax64(m, key_at(row[k * si], k, kw, mul));
+  } else {
+    int64_t q = 0, rem = 0;  // k = q km.in + rem, advanced without division
+    for (int64_t k = 0; k < K; ++k) {
+      m = umax64(m, key_at(row[q * km.so + rem * km.si], k, kw, mul));
+      if (++rem == km.in) rem = 0, ++q;
+    }
   }
   exps[r] = exp_of_key(m);
 }
 
-// same, one block per row (few long rows)
+// same, one block per row (few long rows); contiguous rows are read as
+// 16-byte vectors, four per thread in flight
 __global__ void k_oz_rowexp_block(const double* __restrict__ src, OzMap rm, OzMap km, int64_t K,
                                   const double* __restrict__ kw, double mul, const int* __restrict__ ridx,
                                   int* __restrict__ exps) {
@@ -231,12 +292,28 @@ __global__ void k_oz_rowexp_block(const double* __restrict__ src, OzMap rm, OzMa
   const int64_t r = blockIdx.x;
   const double* row = src + row_base(rm, ridx, r);
   uint64_t m = 0;
-  for (int64_t k = threadIdx.x; k < K; k += blockDim.x) {
-    double v = row[map_at(km, k)];
-    if (mul != 1.0) v *= mul;
-    if (kw) v *= kw[k];
-    const uint64_t key = abs_key(v);
-    m = key > m ? key : m;
+  const int bd = blockDim.x;
+  if (km.in == 0 && km.si == 1 && (reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+    const double2* p = reinterpret_cast<const double2*>(row);
+    const int64_t K2 = K >> 1;
+    int64_t i = threadIdx.x;
+    for (; i + 3 * bd < K2; i += 4 * bd) {
+      double2 t[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) t[h] = __ldg(p + i + h * bd);
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int64_t k = 2 * (i + h * bd);
+        m = umax64(m, umax64(key_at(t[h].x, k, kw, mul), key_at(t[h].y, k + 1, kw, mul)));
+      }
+    }
+    for (; i < K2; i += bd) {
+      const double2 t = __ldg(p + i);
+      m = umax64(m, umax64(key_at(t.x, 2 * i, kw, mul), key_at(t.y, 2 * i + 1, kw, mul)));
+    }
+    if ((K & 1) && threadIdx.x == 0) m = umax64(m, key_at(row[K - 1], K - 1, kw, mul));
+  } else {
+    for (int64_t k = threadIdx.x; k < K; k += bd) m = umax64(m, key_at(row[map_at(km, k)], k, kw, mul));
   }
   sh[threadIdx.x] = m;
   __syncthreads();
@@ -247,66 +324,143 @@ __global__ void k_oz_rowexp_block(const double* __restrict__ src, OzMap rm, OzMa
   if (threadIdx.x == 0) exps[r] = exp_of_key(sh[0]);
 }
 
-// Digits of one row and one group of 8 k values, written as 16 bytes per slice.
-// order 0: consecutive threads take consecutive rows; 1: consecutive k groups.
-// Only the 8-wide k groups [kg0, kg0 + ngrp) are written; tile (row tile i,
-// k tile j) sits at position i * kst + j, so an operand whose K grows can be
-// extended in place.  ridx: row r is source row ridx[r].
+// BF16 bits of a small integer d (|d| <= 2^8): 1.5 * 2^23 + d is exact in
+// FP32 (unit spacing), subtracting 1.5 * 2^23 leaves d exactly, and d has at
+// most 8 significant bits, so the upper half of its FP32 pattern is its BF16
+// pattern.  Integer and FP32 operations only.
+__device__ __forceinline__ uint32_t bf16_bits_of_small(int d) {
+  return __float_as_uint(__int_as_float(0x4B400000 + d) - 12582912.0f);
+}
+
+// Digits of row r and k group kg (8 values), written as 16 bytes per slice:
+// tile (row tile i, k tile j) sits at position i * kst + j of the tile array.
+template <int S>
+__device__ __forceinline__ void oz_digit_group(const double* __restrict__ src, const OzMap& rm, const OzMap& km,
+                                               int64_t rows, int64_t K, const double* __restrict__ kw, double mul,
+                                               const int* __restrict__ exps, int rt, int64_t kst,
+                                               const int* __restrict__ ridx, __nv_bfloat16* __restrict__ tiles, int r,
+                                               int64_t kg) {
+  const bool live = r < rows;
+  const int e = live ? exps[r] : 0;
+  const double* row = src + (live ? row_base(rm, ridx, r) : 0);
+  const int64_t k0 = kg * 8;
+  double v[8];
+  if (live && km.in == 0 && km.si == 1 && k0 + 8 <= K && (reinterpret_cast<uintptr_t>(row + k0) & 15) == 0) {
+    const double2* p = reinterpret_cast<const double2*>(row + k0);
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+      const double2 t = __ldg(p + h);
+      v[2 * h] = t.x;
+      v[2 * h + 1] = t.y;
+    }
+  } else {
+    int64_t q = 0, rem = 0;  // k0 = q km.in + rem
+    if (km.in) q = k0 / km.in, rem = k0 % km.in;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t off = km.in ? q * km.so + rem * km.si : (k0 + u) * km.si;
+      if (km.in && ++rem == km.in) rem = 0, ++q;
+      v[u] = (live && k0 + u < K) ? row[off] : 0.0;
+    }
+  }
+  long long X[8];
+  const int shift = 7 * S - e;
+#pragma unroll
+  for (int u = 0; u < 8; ++u) {
+    double x = v[u];
+    if (k0 + u < K) {
+      if (mul != 1.0) x *= mul;
+      if (kw) x *= kw[k0 + u];
+    }
+    X[u] = round_scaled(x, shift);
+  }
+  const int it = r / rt, rr = r - it * rt;
+  const int64_t jt = kg >> 2;
+  const int kc = int(kg & 3);
+  const int64_t tile_elems = int64_t(rt) * kBK;
+  __nv_bfloat16* base = tiles + ((int64_t(it) * kst + jt) * S) * tile_elems;
+  const int inner = (rr >> 3) * (8 * kBK) + kc * 64 + (rr & 7) * 8;  // element offset in a tile
+  // Balanced digits from the least significant end (in [-64, 63]; the top one
+  // takes the rest, |d_0| <= 128), one slice at a time.  |X| < 2^(7S + 1), so
+  // once S - 4 digits are removed the remainder fits in 32 bits.
+  int Y[8];
+#pragma unroll
+  for (int u = 0; u < 8; ++u) Y[u] = int(X[u]);
+#pragma unroll
+  for (int s = S - 1; s >= 0; --s) {
+    uint32_t b[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      int dig;
+      if (s >= 4) {
+        dig = int((uint32_t(X[u]) + 64u) & 127u) - 64;
+        X[u] = (X[u] - dig) >> 7;
+        if (s == 4) Y[u] = int(X[u]);
+      } else if (s >= 1) {
+        dig = ((Y[u] + 64) & 127) - 64;
+        Y[u] = (Y[u] - dig) >> 7;
+      } else {
+        dig = Y[u];
+      }
+      b[u] = bf16_bits_of_small(dig);
+    }
+    uint4 w;
+    w.x = __byte_perm(b[0], b[1], 0x7632);
+    w.y = __byte_perm(b[2], b[3], 0x7632);
+    w.z = __byte_perm(b[4], b[5], 0x7632);
+    w.w = __byte_perm(b[6], b[7], 0x7632);
+    *reinterpret_cast<uint4*>(base + int64_t(s) * tile_elems + inner) = w;
+  }
+}
+
+// Digits of the k groups [kg0, kg0 + ngrp) of every row (padding rows zero).
+// order 0 (k strided): 256 consecutive rows per block, one k group per
+// blockIdx.y.  order 1 (k contiguous): each warp takes 8 rows x 4
+// consecutive k groups, so it writes one 512-byte line of each slice and
+// reads 256 contiguous bytes of each of its rows; blockIdx.y walks the
+// 8-row groups.
+template <int S>
 __global__ void k_oz_digits(const double* __restrict__ src, OzMap rm, OzMap km, int64_t rows, int64_t K,
-                            const double* __restrict__ kw, double mul, const int* __restrict__ exps, int S, int rt,
+                            const double* __restrict__ kw, double mul, const int* __restrict__ exps, int rt,
                             int64_t nrt, int64_t kg0, int64_t ngrp, int64_t kst, int order,
                             const int* __restrict__ ridx, __nv_bfloat16* __restrict__ tiles) {
   const int64_t rows_pad = nrt * rt;
-  const int64_t idx = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (idx >= rows_pad * ngrp) return;
-  int64_t r, kg;
   if (order == 0) {
-    r = idx % rows_pad;
-    kg = idx / rows_pad;
+    const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (r >= rows_pad) return;
+    for (int64_t g = blockIdx.y; g < ngrp; g += gridDim.y)
+      oz_digit_group<S>(src, rm, km, rows, K, kw, mul, exps, rt, kst, ridx, tiles, int(r), kg0 + g);
   } else {
-    kg = idx % ngrp;
-    r = idx / ngrp;
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4 + (lane >> 3);
+    if (g >= ngrp) return;
+    for (int64_t g8 = blockIdx.y; g8 * 8 < rows_pad; g8 += gridDim.y)
+      oz_digit_group<S>(src, rm, km, rows, K, kw, mul, exps, rt, kst, ridx, tiles, int(g8 * 8 + (lane & 7)),
+                        kg0 + g);
   }
-  kg += kg0;
-  long long X[8];
-  const int e = (r < rows) ? exps[r] : 0;
-  const int shift = 7 * S - e;
-  const double* row = src + ((r < rows) ? row_base(rm, ridx, r) : 0);
-  int64_t q = 0, rem = 0;  // kg * 8 = q km.in + rem
-  if (km.in) q = (kg * 8) / km.in, rem = (kg * 8) % km.in;
-#pragma unroll
-  for (int u = 0; u < 8; ++u) {
-    const int64_t k = kg * 8 + u;
-    const int64_t off = km.in ? q * km.so + rem * km.si : k * km.si;
-    if (km.in && ++rem == km.in) rem = 0, ++q;
-    double v = 0.0;
-    if (r < rows && k < K) {
-      v = row[off];
-      if (mul != 1.0) v *= mul;
-      if (kw) v *= kw[k];
-    }
-    X[u] = round_scaled(v, shift);
+}
+
+void launch_digits(const double* src, OzMap rm, OzMap km, const double* kw, double mul, const int* ridx,
+                   const OzOperand& op, int64_t kg0, int64_t ngrp, int order, cudaStream_t s) {
+  const int64_t rows_pad = op.nrt * op.rt;
+  dim3 grid;
+  if (order == 0) {
+    grid.x = unsigned((rows_pad + 255) / 256);
+    grid.y = unsigned(std::min<int64_t>(ngrp, 65535));
+  } else {
+    grid.x = unsigned(((ngrp + 3) / 4 + 7) / 8);
+    grid.y = unsigned(std::min<int64_t>(rows_pad / 8, 65535));
   }
-  const int64_t it = r / rt, rr = r % rt, jt = kg / (kBK / 8), kc = kg % (kBK / 8);
-  const int64_t tile_elems = int64_t(rt) * kBK;
-  __nv_bfloat16* base = tiles + ((it * kst + jt) * S) * tile_elems;
-  const int64_t inner = ((rr / 8) * (16 * kBK) + kc * 128 + (rr % 8) * 16) / 2;  // element offset in a tile
-  // digits from the least significant end (balanced, in [-64, 63]); top digit last
-  for (int s = S - 1; s >= 0; --s) {
-    __align__(16) __nv_bfloat16 d[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      long long dig;
-      if (s > 0) {
-        dig = ((X[u] + 64) & 127) - 64;
-        X[u] = (X[u] - dig) >> 7;
-      } else {
-        dig = X[u];
-      }
-      d[u] = __float2bfloat16_rn(float(dig));
-    }
-    *reinterpret_cast<uint4*>(base + int64_t(s) * tile_elems + inner) = *reinterpret_cast<const uint4*>(d);
-  }
+  __nv_bfloat16* t = static_cast<__nv_bfloat16*>(op.tiles);
+  if (op.S == 5)
+    k_oz_digits<5><<<grid, 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.rt, op.nrt, kg0, ngrp,
+                                        op.kst, order, ridx, t);
+  else if (op.S == 6)
+    k_oz_digits<6><<<grid, 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.rt, op.nrt, kg0, ngrp,
+                                        op.kst, order, ridx, t);
+  else
+    k_oz_digits<8><<<grid, 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.rt, op.nrt, kg0, ngrp,
+                                        op.kst, order, ridx, t);
 }
 
 // ---------------------------------------------------------------- GEMM
@@ -544,7 +698,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
                   rem[c0 + j] += uint32_t(x & 0x0FFFFFFFll);
                 }
               } else {
-                const long long x = __float2ll_rn(fmaf(fa, 128.0f, fb));  // levels 6, 7
+                const long long x = intf_to_ll(fmaf(fa, 128.0f, fb));  // levels 6, 7
                 th[c0 + j] += x >> 28;
                 rem[c0 + j] += uint32_t(x & 0x0FFFFFFFll);
               }
@@ -568,10 +722,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
         for (int j = 0; j < HC; ++j) {
           const int64_t n = n0 + half * HC + j;
           if (n >= P.N) continue;
-          const int e = ea + P.eb[n] - 14 - 21;
-          const double t = double(th[j]) + double(rem[j]) * 0x1p-28;  // one rounding
-          // t 2^e: exact power-of-two factor built from its bits in the normal range
-          double v = (e >= -1022 && e <= 1023) ? t * __longlong_as_double((long long)(e + 1023) << 52) : ldexp(t, e);
+          double v = fixed_to_double(th[j], rem[j], ea + P.eb[n] - 14 - 21);  // one rounding
           if (P.alpha != 1.0) v *= P.alpha;
           if (P.splits > 1)
             P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
@@ -692,19 +843,19 @@ void oz_free(OzOperand& op) {
   op.exps = nullptr;
 }
 
-void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s) {
+void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s,
+              const OzOperand* exps_of) {
   const bool rowwise = sr >= sk;  // k contiguous: one block per row
   const OzMap rm = oz_stride(sr), km = oz_stride(sk);
-  if (rowwise && op.K >= 4096) {
+  if (exps_of) {
+    cudaMemcpyAsync(op.exps, exps_of->exps, size_t(op.rows) * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  } else if (rowwise && op.K >= 4096) {
     k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, rm, km, op.K, kw, mul, nullptr, op.exps);
   } else {
     k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, nullptr,
                                                                         op.exps);
   }
-  const int64_t total = op.nrt * op.rt * op.nkt * (kBK / 8);
-  k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.S, op.rt,
-                                                             op.nrt, 0, op.nkt * (kBK / 8), op.kst, rowwise ? 1 : 0,
-                                                             nullptr, static_cast<__nv_bfloat16*>(op.tiles));
+  launch_digits(src, rm, km, kw, mul, nullptr, op, 0, op.nkt * (kBK / 8), rowwise ? 1 : 0, s);
   count_launches(2);
 }
 
@@ -722,10 +873,7 @@ void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzO
                                                                           ridx, op.exps);
     count_launches(1);
   }
-  const int64_t total = op.nrt * op.rt * (kg1 - kg0);
-  k_oz_digits<<<unsigned((total + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, nullptr, 1.0, op.exps, op.S,
-                                                             op.rt, op.nrt, kg0, kg1 - kg0, op.kst, rowwise ? 1 : 0,
-                                                             ridx, static_cast<__nv_bfloat16*>(op.tiles));
+  launch_digits(src, rm, km, nullptr, 1.0, ridx, op, kg0, kg1 - kg0, rowwise ? 1 : 0, s);
   count_launches(1);
 }
 

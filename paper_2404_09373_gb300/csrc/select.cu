@@ -981,15 +981,27 @@ __global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, St
       double dn;
       if (i >= lo && i < hi) {
         const int64_t t = i - lo;
+        const double bt = bcol[t];
+        const double di = __ldcg(P.d + i);
+        // the block's earlier columns, eight loads in flight, summed in column order
+        const double* fq = fac + int64_t(kb[l]) * nc + t;
         double s0 = 0.0;
-        for (int q = 0; q < nbk; ++q) s0 = fma(__ldcg(fac + int64_t(kb[l] + q) * nc + t), lp[q], s0);
-        double v = (bcol[t] - s0) / sq;
+        int q = 0;
+        for (; q + 8 <= nbk; q += 8) {
+          double f[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) f[u] = __ldcg(fq + int64_t(q + u) * nc);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) s0 = fma(f[u], lp[q + u], s0);
+        }
+        for (; q < nbk; ++q) s0 = fma(__ldcg(fq + int64_t(q) * nc), lp[q], s0);
+        double v = (bt - s0) / sq;
         if (t == tp) v = sq;
         facw[int64_t(col) * nc + t] = v;
         if (t == tp) {
           dn = 0.0;  // written as 0 in the next phase B
         } else {
-          dn = __ldcg(P.d + i) - v * v;
+          dn = di - v * v;
           P.d[i] = dn;
         }
       } else {
