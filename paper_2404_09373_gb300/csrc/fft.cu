@@ -19,6 +19,7 @@
 #include <cmath>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace isdf {
@@ -26,37 +27,6 @@ namespace {
 
 constexpr int kMaxN = 128;
 constexpr int kMaxStages = 8;
-
-struct DF {
-  float hi, lo;
-};
-
-// Error-free transformations with explicitly rounded operations (the
-// compiler must not contract them into FMAs or reassociate them).
-__device__ __forceinline__ DF two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
-}
-__device__ __forceinline__ DF quick_two_sum(float a, float b) {
-  const float s = __fadd_rn(a, b);
-  return {s, __fsub_rn(b, __fsub_rn(s, a))};
-}
-__device__ __forceinline__ DF df_add(DF x, DF y) {
-  DF s = two_sum(x.hi, y.hi);
-  s.lo = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
-  return quick_two_sum(s.hi, s.lo);
-}
-__device__ __forceinline__ DF df_neg(DF x) { return {-x.hi, -x.lo}; }
-__device__ __forceinline__ DF df_sub(DF x, DF y) { return df_add(x, df_neg(y)); }
-__device__ __forceinline__ DF df_mul(DF x, DF y) {
-  const float p = __fmul_rn(x.hi, y.hi);
-  float e = __fmaf_rn(x.hi, y.hi, -p);  // exact error of the product
-  e = __fmaf_rn(x.hi, y.lo, e);
-  e = __fmaf_rn(x.lo, y.hi, e);
-  return quick_two_sum(p, e);
-}
-__device__ __forceinline__ DF df_half(DF x) { return {__fmul_rn(0.5f, x.hi), __fmul_rn(0.5f, x.lo)}; }
 
 struct DC {
   DF re, im;
@@ -68,12 +38,6 @@ __device__ __forceinline__ DC dc_mul(DC a, DC b) {
 }
 __device__ __forceinline__ DC dc_mul_mi(DC a) { return {a.im, df_neg(a.re)}; }  // a * (-i)
 __device__ __forceinline__ DC dc_mul_pi(DC a) { return {df_neg(a.im), a.re}; }  // a * (+i)
-
-__device__ __forceinline__ DF df_from_double(double x) {
-  const float hi = __double2float_rn(x);
-  return {hi, __double2float_rn(x - double(hi))};
-}
-__device__ __forceinline__ double df_to_double(DF x) { return double(x.hi) + double(x.lo); }
 
 __device__ __forceinline__ float4 dc_pack(DC a) { return make_float4(a.re.hi, a.re.lo, a.im.hi, a.im.lo); }
 __device__ __forceinline__ DC dc_unpack(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }

@@ -25,6 +25,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "dfloat.cuh"
 #include "internal.cuh"
 
 namespace isdf {
@@ -350,7 +351,54 @@ struct BlkParams {
   SelParams P;
   const int* spos;                      // [ntot] position of a candidate in S's range of its level, -1 if not in S
   const double* bm[ISDF_MAX_LEVELS];    // [s_l][nc_l]
+  float2* bdf[ISDF_MAX_LEVELS];         // [s][nc_l] the block's columns so far, double-float
 };
+
+// Order-preserving key of a residual value: its bits when positive, else 0
+// (integer operations only).
+__device__ __forceinline__ unsigned long long dkey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b > 0 ? (unsigned long long)b : 0ull;
+}
+
+// Column entry of a block step for one candidate:
+//   v = (b - sum_q F_q lp_q) / sqrt(d_p),
+// F_q the block's earlier columns at this candidate (stride nc) and lp_q at
+// the pivot, all double-float; the products' errors and the partial sums'
+// rounding errors are gathered in one FP32 word.  FP32 pipes only.
+__device__ __forceinline__ DF blk_col_df(const float2* __restrict__ fq, int64_t nc, int nbk, const DF* lpd, double b,
+                                         DF inv_sq) {
+  float ah = 0.0f, al = 0.0f;
+  int q = 0;
+  for (; q + 4 <= nbk; q += 4) {
+    float2 c[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) c[u] = __ldcg(fq + int64_t(q + u) * nc);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const DF l = lpd[q + u];
+      const float pr = __fmul_rn(c[u].x, l.hi);
+      float e = __fmaf_rn(c[u].x, l.hi, -pr);
+      e = __fmaf_rn(c[u].x, l.lo, e);
+      e = __fmaf_rn(c[u].y, l.hi, e);
+      const DF t = two_sum(ah, pr);
+      ah = t.hi;
+      al = __fadd_rn(al, __fadd_rn(t.lo, e));
+    }
+  }
+  for (; q < nbk; ++q) {
+    const float2 c = __ldcg(fq + int64_t(q) * nc);
+    const DF l = lpd[q];
+    const float pr = __fmul_rn(c.x, l.hi);
+    float e = __fmaf_rn(c.x, l.hi, -pr);
+    e = __fmaf_rn(c.x, l.lo, e);
+    e = __fmaf_rn(c.y, l.hi, e);
+    const DF t = two_sum(ah, pr);
+    ah = t.hi;
+    al = __fadd_rn(al, __fadd_rn(t.lo, e));
+  }
+  return df_mul(df_sub(df_from_double(b), two_sum(ah, al)), inv_sq);
+}
 
 struct LmParams {
   const double* d;
@@ -676,26 +724,35 @@ __global__ void k_blk_pick(BlkParams B, SelState* st) {
 // column of this step from B and the block's earlier columns; residual update
 __global__ void __launch_bounds__(256) k_blk_col(BlkParams B, const SelState* st) {
   if (st->skip) return;
-  __shared__ double lp[256];  // L[p, kb..col) (a block has at most 256 steps)
+  __shared__ DF lp[256];  // L[p, kb..col) (a block has at most 256 steps)
   const SelParams& P = B.P;
   const int l = st->lev;
   const int col = st->col, kb = st->kb[l];
   const int nb = col - kb;
   const int64_t nc = P.nc[l], tp = st->tp;
-  const double* __restrict__ fac = P.fac[l];
-  for (int i = threadIdx.x; i < nb; i += blockDim.x) lp[i] = fac[int64_t(kb + i) * nc + tp];
+  float2* __restrict__ bdf = B.bdf[l];
+  __shared__ double sq_sh;
+  __shared__ DF inv_sh;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    const float2 c = bdf[int64_t(i) * nc + tp];
+    lp[i] = {c.x, c.y};
+  }
+  if (threadIdx.x == 0) {
+    sq_sh = sqrt(st->dp);
+    inv_sh = df_from_double(1.0 / sq_sh);
+  }
   __syncthreads();
-  const double sq = sqrt(st->dp);
+  const double sq = sq_sh;
+  const DF inv = inv_sh;
   const double* __restrict__ bcol = B.bm[l] + int64_t(st->jpos) * nc;
   double* __restrict__ facw = P.fac[l];
   double* __restrict__ d = P.d + P.coff[l];
   for (int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; t < nc; t += int64_t(gridDim.x) * blockDim.x) {
-    double s0 = 0.0;
-    for (int i = 0; i < nb; ++i) s0 = fma(fac[int64_t(kb + i) * nc + t], lp[i], s0);
-    double v = (bcol[t] - s0) / sq;
-    if (t == tp) v = sq;
-    facw[int64_t(col) * nc + t] = v;
-    d[t] = (t == tp) ? 0.0 : d[t] - v * v;
+    const DF v = (t == tp) ? df_from_double(sq) : blk_col_df(bdf + t, nc, nb, lp, bcol[t], inv);
+    const double vd = (t == tp) ? sq : df_to_double(v);
+    facw[int64_t(col) * nc + t] = vd;
+    bdf[int64_t(nb) * nc + t] = make_float2(v.hi, v.lo);
+    d[t] = (t == tp) ? 0.0 : fma(-vd, vd, d[t]);
   }
 }
 
@@ -897,9 +954,13 @@ __global__ void k_sync_init(StepSync* sy) {
 
 __global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, StepSync* sy, int smax) {
   const SelParams& P = B.P;
-  __shared__ double lp[256];
+  __shared__ DF lpd[256];  // the pivot's entries in the block's earlier columns
   __shared__ int kl_sh[ISDF_MAX_LEVELS];
   __shared__ unsigned long long red[32];
+  __shared__ int stop_sh;
+  __shared__ unsigned long long thr_sh;
+  __shared__ double sq_sh;
+  __shared__ DF inv_sh;
   const unsigned int nb = gridDim.x;
   const int tid = threadIdx.x;
   const int64_t gtid = int64_t(blockIdx.x) * blockDim.x + tid, gstride = int64_t(gridDim.x) * blockDim.x;
@@ -911,14 +972,15 @@ __global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, St
   __syncthreads();
   long long last = -1;  // global index of the previous step's pivot (its residual is zeroed next phase B)
   int bsteps = 0, reason = 0;  // reason: 0 running, 1 block end, 2 final, 3 timeout, 4 barrier failure
+  // Residual comparisons use the order-preserving integer keys of the values,
+  // and the per-step scalars are formed by one thread per CTA: the FP64 unit
+  // is left to the two operations per candidate that need it.
   // phase 0: d_max of the current residual into slot 0
   {
-    double m = 0.0;
-    for (int64_t i = gtid; i < P.ntot; i += gstride) m = fmax(m, __ldcg(P.d + i));
-    unsigned long long mb = block_reduce((unsigned long long)__double_as_longlong(m),
-                                         MaxU64(),
-                                         red);
-    if (tid == 0) atomicMax(&sy->dmax[0], mb);
+    unsigned long long mk = 0ull;
+    for (int64_t i = gtid; i < P.ntot; i += gstride) mk = max(mk, dkey(__ldcg(P.d + i)));
+    mk = block_reduce(mk, MaxU64(), red);
+    if (tid == 0) atomicMax(&sy->dmax[0], mk);
   }
   if (!grid_sync(sy, nb)) reason = 4;
   for (int j = 0; reason == 0; ++j) {
@@ -926,15 +988,27 @@ __global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, St
     // ---------------- phase B
     if (last >= 0 && gtid == 0) P.d[last] = 0.0;  // visible after the barrier
     const double dmax = __longlong_as_double((long long)*(volatile unsigned long long*)&sy->dmax[par]);
-    const double dz = (k == 0) ? dmax : d0;
-    if (j >= smax) { reason = 1; break; }
-    if (k >= P.nip || !(dmax > 0.0) || dmax < P.tol * dz) { reason = 2; break; }
-    const double thr = dmax - fmax(P.tie_rel * dmax, P.tie_abs * dz);
+    if (tid == 0) {
+      const double dz = (k == 0) ? dmax : d0;
+      int stop = 0;
+      if (j >= smax)
+        stop = 1;
+      else if (k >= P.nip || !(dmax > 0.0) || dmax < P.tol * dz)
+        stop = 2;
+      stop_sh = stop;
+      // d >= thr and d > 0  <=>  key(d) >= max(key(thr), 1)
+      thr_sh = max(dkey(dmax - fmax(P.tie_rel * dmax, P.tie_abs * dz)), 1ull);
+    }
+    __syncthreads();
+    if (stop_sh) {
+      reason = stop_sh;
+      break;
+    }
+    const unsigned long long tk = thr_sh;
     unsigned long long best = ULLONG_MAX;
     for (int64_t i = gtid; i < P.ntot; i += gstride) {
       if (i == last) continue;
-      const double v = __ldcg(P.d + i);
-      if (v >= thr && v > 0.0) {
+      if (dkey(__ldcg(P.d + i)) >= tk) {
         best = (unsigned long long)i;
         break;
       }
@@ -958,9 +1032,16 @@ __global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, St
     const int col = kl_sh[l];
     const int nbk = col - kb[l];
     const int64_t nc = P.nc[l];
-    const double* fac = P.fac[l];
+    float2* __restrict__ bdf = B.bdf[l];
     __syncthreads();
-    for (int i = tid; i < nbk; i += blockDim.x) lp[i] = __ldcg(fac + int64_t(kb[l] + i) * nc + tp);
+    for (int i = tid; i < nbk; i += blockDim.x) {
+      const float2 c = __ldcg(bdf + int64_t(i) * nc + tp);
+      lpd[i] = {c.x, c.y};
+    }
+    if (tid == 0) {
+      sq_sh = sqrt(dp);
+      inv_sh = df_from_double(1.0 / sq_sh);
+    }
     __syncthreads();
     if (k == 0) d0 = dmax;
     if (gtid == 0) {
@@ -972,47 +1053,35 @@ __global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, St
         st->t0 = globaltimer();
       }
     }
-    const double sq = sqrt(dp);
+    const double sq = sq_sh;
+    const DF inv = inv_sh;
     const double* __restrict__ bcol = B.bm[l] + int64_t(pos) * nc;
     double* __restrict__ facw = P.fac[l];
     const int64_t lo = P.coff[l], hi = P.coff[l + 1];
-    double m = 0.0;
+    unsigned long long mk = 0ull;
     for (int64_t i = gtid; i < P.ntot; i += gstride) {
-      double dn;
+      unsigned long long key;
       if (i >= lo && i < hi) {
         const int64_t t = i - lo;
-        const double bt = bcol[t];
         const double di = __ldcg(P.d + i);
-        // the block's earlier columns, eight loads in flight, summed in column order
-        const double* fq = fac + int64_t(kb[l]) * nc + t;
-        double s0 = 0.0;
-        int q = 0;
-        for (; q + 8 <= nbk; q += 8) {
-          double f[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) f[u] = __ldcg(fq + int64_t(q + u) * nc);
-#pragma unroll
-          for (int u = 0; u < 8; ++u) s0 = fma(f[u], lp[q + u], s0);
-        }
-        for (; q < nbk; ++q) s0 = fma(__ldcg(fq + int64_t(q) * nc), lp[q], s0);
-        double v = (bt - s0) / sq;
-        if (t == tp) v = sq;
-        facw[int64_t(col) * nc + t] = v;
+        const DF v = (t == tp) ? df_from_double(sq) : blk_col_df(bdf + t, nc, nbk, lpd, bcol[t], inv);
+        const double vd = (t == tp) ? sq : df_to_double(v);
+        facw[int64_t(col) * nc + t] = vd;
+        bdf[int64_t(nbk) * nc + t] = make_float2(v.hi, v.lo);
         if (t == tp) {
-          dn = 0.0;  // written as 0 in the next phase B
+          key = 0ull;  // written as 0 in the next phase B
         } else {
-          dn = di - v * v;
+          const double dn = fma(-vd, vd, di);
           P.d[i] = dn;
+          key = dkey(dn);
         }
       } else {
-        dn = (i == (long long)idx) ? 0.0 : __ldcg(P.d + i);
+        key = (i == (long long)idx) ? 0ull : dkey(__ldcg(P.d + i));
       }
-      m = fmax(m, dn);
+      mk = max(mk, key);
     }
-    unsigned long long mb = block_reduce((unsigned long long)__double_as_longlong(m),
-                                         MaxU64(),
-                                         red);
-    if (tid == 0) atomicMax(&sy->dmax[par ^ 1], mb);
+    mk = block_reduce(mk, MaxU64(), red);
+    if (tid == 0) atomicMax(&sy->dmax[par ^ 1], mk);
     // counters advance identically in every CTA
     __syncthreads();
     if (tid == 0) kl_sh[l] = col + 1;
@@ -1189,7 +1258,12 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
   BlkParams BP{};
   BP.P = P;
   BP.spos = spos;
-  for (int l = 0; l < nlev; ++l) BP.bm[l] = lb[l].cL;
+  for (int l = 0; l < nlev; ++l) {
+    BP.bm[l] = lb[l].cL;
+    // the factor product's output is free during the steps: it holds the
+    // double-float copy of the block's columns (s x nc values of 8 bytes)
+    BP.bdf[l] = reinterpret_cast<float2*>(lb[l].cF);
+  }
   TopSOut O{sidx, sg, stp, scount, spos};
 
   SelState h{};
