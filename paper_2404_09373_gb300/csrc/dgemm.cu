@@ -264,11 +264,37 @@ namespace {
 //   inv([A 0; C B]) = [A^-1 0; -B^-1 C A^-1  B^-1],  A: n1 x n1, B: n2 x n2,
 // with n1 a multiple of the 64-row diagonal blocks (already inverted).
 // T = C A^-1 goes to the scratch (n2 x n1), then Li[C] = -B^-1 T.
-void trtri_rec(const double* Lm, double* Li, int64_t ld, int64_t r0, int64_t n, double* scratch, cudaStream_t s) {
+// C (M x N, ldc) = alpha A B, A row-major (M x K, lda), B row-major (K x N,
+// ldb), as an 8-digit tensor-core product; false if its buffers could not be
+// allocated (the caller then takes the FP64 product)
+bool tc_product(Plan* p, const double* A, int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc, int64_t M,
+                int64_t N, int64_t K, double alpha, cudaStream_t s) {
+  OzOperand a, b;
+  const bool ok = oz_alloc(p, a, M, K, 128, 8, "triangular inverse slices") == ISDF_OK &&
+                  oz_alloc(p, b, N, K, oz_bn(8), 8, "triangular inverse slices") == ISDF_OK;
+  if (ok) {
+    oz_slice(A, lda, 1, nullptr, 1.0, a, s);
+    oz_slice(B, 1, ldb, nullptr, 1.0, b, s);  // row j of the B operand: column j of B
+    oz_gemm(a, b, C, ldc, 0, alpha, 0, 0, 1, nullptr, p->d_ozerr, s);
+  }
+  oz_free(a);
+  oz_free(b);
+  return ok;
+}
+
+constexpr int64_t kTcMin = 256;  // products with halves at least this large go to the tensor cores
+
+void trtri_rec(const double* Lm, double* Li, int64_t ld, int64_t r0, int64_t n, double* scratch, cudaStream_t s,
+               Plan* tc) {
   if (n <= CB) return;
   const int64_t n1 = ((n / 2 + CB - 1) / CB) * CB, n2 = n - n1;
-  trtri_rec(Lm, Li, ld, r0, n1, scratch, s);
-  trtri_rec(Lm, Li, ld, r0 + n1, n2, scratch, s);
+  trtri_rec(Lm, Li, ld, r0, n1, scratch, s, tc);
+  trtri_rec(Lm, Li, ld, r0 + n1, n2, scratch, s, tc);
+  if (tc && n2 >= kTcMin &&
+      tc_product(tc, Lm + (r0 + n1) * ld + r0, ld, Li + r0 * ld + r0, ld, scratch, n1, n2, n1, n1, 1.0, s) &&
+      tc_product(tc, Li + (r0 + n1) * ld + r0 + n1, ld, scratch, n1, Li + (r0 + n1) * ld + r0, ld, n2, n1, n2, -1.0,
+                 s))
+    return;
   GemmArgs g;  // T = C A^-1
   g.M = n2;
   g.N = n1;
@@ -301,11 +327,11 @@ void trtri_rec(const double* Lm, double* Li, int64_t ld, int64_t r0, int64_t n, 
 // one launch, then the off-diagonal blocks by recursive halving (products of
 // the size of the halves instead of 64-row strips).
 // scratch: (n / 2 + 64) * n doubles.
-void dtrtri_lower(const double* Lm, double* Li, int64_t n, double* scratch, cudaStream_t s) {
+void dtrtri_lower(const double* Lm, double* Li, int64_t n, double* scratch, cudaStream_t s, Plan* tc) {
   cudaMemsetAsync(Li, 0, sizeof(double) * n * n, s);
   const int64_t nb = (n + CB - 1) / CB;
   k_trtri_diag<<<unsigned(nb), 64, 0, s>>>(Lm, Li, n, n);
-  trtri_rec(Lm, Li, n, 0, n, scratch, s);
+  trtri_rec(Lm, Li, n, 0, n, scratch, s, tc);
 }
 
 }  // namespace isdf

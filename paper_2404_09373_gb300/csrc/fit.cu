@@ -245,7 +245,7 @@ isdf_status fit_run(Plan* p) {
     {
       const int64_t nb = (k + 63) / 64;
       Prof pr(p, "fit_trtri", double(k) * k * k / 3.0, "flop", 1 + 2 * (nb - 1));
-      dtrtri_lower(cc, li, k, scr, s);
+      dtrtri_lower(cc, li, k, scr, s, p->opt.precision == 1 ? p : nullptr);
     }
     if (factored) {
       // Coulomb and exchange need Xi only through V = W (ZC^T v ZC) W with

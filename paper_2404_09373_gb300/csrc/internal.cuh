@@ -160,8 +160,11 @@ void zc_gemm(int64_t k, int64_t ng, int nL, int nG, const double* phiP, const do
              cudaStream_t s);
 // lower Cholesky in place (row-major n x n, lda); breakdown column -> *err
 void dpotrf_lower(double* A, int64_t n, int64_t lda, int* err, double* scratch, cudaStream_t s);
-// inverse of a lower-triangular matrix: Li (n x n, zero-initialised by callee)
-void dtrtri_lower(const double* Lm, double* Li, int64_t n, double* scratch, cudaStream_t s);
+// inverse of a lower-triangular matrix: Li (n x n, zero-initialised by callee);
+// with a plan (tensor-core precision) the large off-diagonal products run as
+// FP64-grade 8-digit tensor-core products, their error flag the plan's
+struct Plan;
+void dtrtri_lower(const double* Lm, double* Li, int64_t n, double* scratch, cudaStream_t s, Plan* tc = nullptr);
 
 // FP64-accurate GEMM from sliced BF16 products on tcgen05 (ozgemm.cu).
 // An operand is rows x K, pre-sliced into S BF16 digit planes (S = 5 or 6)

@@ -471,6 +471,7 @@ struct OzGemmParams {
   const int* ea;
   const int* eb;
   int64_t M, N, nkt;
+  int64_t ntm, ntn;    // M tiles (of 128 rows) and N tiles (of BN rows)
   int64_t akst, bkst;  // k-tile strides of the A and B tile arrays (>= nkt)
   int tri;     // 0 dense; 1 B-side lower (k <= n); 2 B-side upper (k >= n)
   int sym;     // compute only tiles that touch the lower triangle (n <= m)
@@ -529,24 +530,37 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int64_t nt = blockIdx.x, mt = blockIdx.y;  // N tiles vary fastest: CTAs in flight share A
-  const int64_t m0 = mt * kBM, n0 = nt * BN;
-  if (P.sym && n0 > m0 + kBM - 1) return;  // tile entirely above the diagonal
-  // an earlier CTA failed: do nothing (one read, made uniform across the CTA)
+  // an earlier launch failed: do nothing (one read, made uniform across the CTA)
   if (__syncthreads_or(threadIdx.x == 0 ? *(volatile const int*)P.err : 0)) return;
 
-  // k-tile range of this CTA
-  int64_t kt_lo = 0, kt_hi = P.nkt;
-  if (P.tri == 1) kt_hi = min(P.nkt, (n0 + BN + kBK - 1) / kBK);
-  if (P.tri == 2) kt_lo = min(P.nkt, n0 / kBK);
-  {
-    const int64_t tot = kt_hi - kt_lo, per = (tot + P.splits - 1) / P.splits;
-    const int64_t a = kt_lo + per * blockIdx.z;
-    kt_lo = min(kt_hi, a);
-    kt_hi = min(kt_hi, a + per);
-  }
-  const int64_t nk = kt_hi - kt_lo;
-  const int64_t nchunks = (nk + Cfg::kc - 1) / Cfg::kc;
+  // Persistent tiles: tile t is (N tile t % NT, M tile (t / NT) % MT, split
+  // t / (NT MT)); N tiles vary fastest so that CTAs in flight share A.  Every
+  // role walks the same tile sequence; stage and chunk counters run on across
+  // tiles, so the ring of stages and the accumulator hand-off never restart
+  // and a tile's epilogue overlaps the next tile's copies and MMAs.
+  const int64_t NT = P.ntn, MT = P.ntm, ntiles = NT * MT * P.splits;
+  struct Tile {
+    int64_t nt, mt, m0, n0, kt_lo, nk;
+    int z;
+    bool skip;
+  };
+  auto tile_at = [&](int64_t t) {
+    Tile T;
+    T.nt = t % NT;
+    T.mt = (t / NT) % MT;
+    T.z = int(t / (NT * MT));
+    T.m0 = T.mt * kBM;
+    T.n0 = T.nt * BN;
+    T.skip = P.sym && T.n0 > T.m0 + kBM - 1;  // tile entirely above the diagonal
+    int64_t lo = 0, hi = P.nkt;
+    if (P.tri == 1) hi = min(P.nkt, (T.n0 + BN + kBK - 1) / kBK);
+    if (P.tri == 2) lo = min(P.nkt, T.n0 / kBK);
+    const int64_t tot = hi - lo, per = (tot + P.splits - 1) / P.splits;
+    const int64_t a = lo + per * T.z;
+    T.kt_lo = min(hi, a);
+    T.nk = min(hi, a + per) - T.kt_lo;
+    return T;
+  };
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < Cfg::nst; ++i) {
@@ -574,74 +588,91 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
     if (lane == 0) {
       const unsigned char* gA = reinterpret_cast<const unsigned char*>(P.A);
       const unsigned char* gB = reinterpret_cast<const unsigned char*>(P.B);
-      int64_t issued = 0;
-      for (int64_t it = 0; it < nk; ++it) {
-        const int st = int(it % Cfg::nst);
-        const int64_t round = it / Cfg::nst;
-        if (round > 0 && !mbar_wait(&empty[st], uint32_t((round - 1) & 1), P.err)) {
-          set_err(P.err, 11);
-          *(volatile int*)abort_flag = 1;
-          break;
+      int64_t g = 0;  // stages issued so far (all tiles)
+      for (int64_t t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x) {
+        const Tile T = tile_at(t);
+        if (T.skip) continue;
+        for (int64_t it = 0; it < T.nk; ++it, ++g) {
+          const int st = int(g % Cfg::nst);
+          const int64_t round = g / Cfg::nst;
+          if (round > 0 && !mbar_wait(&empty[st], uint32_t((round - 1) & 1), P.err)) {
+            set_err(P.err, 11);
+            *(volatile int*)abort_flag = 1;
+            break;
+          }
+          if (*(volatile int*)abort_flag) break;
+          const int64_t kt = T.kt_lo + it;
+          unsigned char* sA = smem + st * Cfg::stage;
+          unsigned char* sB = sA + Cfg::stageA;
+          mbar_expect_tx(&full[st], Cfg::stageA + Cfg::stageB);
+          bulk_g2s(sA, gA + (T.mt * P.akst + kt) * int64_t(Cfg::stageA), Cfg::stageA, &full[st]);
+          bulk_g2s(sB, gB + (T.nt * P.bkst + kt) * int64_t(Cfg::stageB), Cfg::stageB, &full[st]);
         }
-        if (*(volatile int*)abort_flag) break;
-        const int64_t kt = kt_lo + it;
-        unsigned char* sA = smem + st * Cfg::stage;
-        unsigned char* sB = sA + Cfg::stageA;
-        mbar_expect_tx(&full[st], Cfg::stageA + Cfg::stageB);
-        bulk_g2s(sA, gA + (mt * P.akst + kt) * int64_t(Cfg::stageA), Cfg::stageA, &full[st]);
-        bulk_g2s(sB, gB + (nt * P.bkst + kt) * int64_t(Cfg::stageB), Cfg::stageB, &full[st]);
-        issued = it + 1;
       }
       // copies that were issued but never consumed must land before exit
       if (*(volatile int*)abort_flag) {
-        const int64_t first = issued > Cfg::nst ? issued - Cfg::nst : 0;
-        for (int64_t it = first; it < issued; ++it) mbar_wait(&full[it % Cfg::nst], uint32_t((it / Cfg::nst) & 1), nullptr);
+        const int64_t first = g > Cfg::nst ? g - Cfg::nst : 0;
+        for (int64_t it = first; it < g; ++it) mbar_wait(&full[it % Cfg::nst], uint32_t((it / Cfg::nst) & 1), nullptr);
       }
     }
   } else if (warp == 1) {
     // ------------------------------------------------ MMA issuer
     if (lane == 0) {
-      for (int64_t it = 0; it < nk; ++it) {
-        const int st = int(it % Cfg::nst);
-        const int64_t round = it / Cfg::nst;
-        const int64_t cpos = it % Cfg::kc, chunk = it / Cfg::kc;
-        if (cpos == 0 && chunk > 0 && !mbar_wait(acc_empty, uint32_t((chunk - 1) & 1), P.err)) {
-          set_err(P.err, 12);
-          *(volatile int*)abort_flag = 1;
-          break;
-        }
-        if (!mbar_wait(&full[st], uint32_t(round & 1), P.err)) {
-          set_err(P.err, 13);
-          *(volatile int*)abort_flag = 1;
-          break;
-        }
-        if (*(volatile int*)abort_flag) break;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        const uint32_t sA = smem_u32(smem + st * Cfg::stage);
-        const uint32_t sB = sA + Cfg::stageA;
-        // For A digit s the products with B digits t = 0..S-1-s land in
-        // levels s..S-1, i.e. tensor-memory columns [s BN, S BN); the B
-        // digit tiles of a stage are contiguous, so B rows [0, (S-s) BN) are
-        // exactly digits 0..S-1-s and one MMA (N up to 256, else split)
-        // covers them all.  The first MMA of a chunk (s = 0) spans every
-        // level and initialises the accumulators.
+      int64_t g = 0, h = 0;  // stages consumed, accumulator chunks handed over (all tiles)
+      bool stop = false;
+      for (int64_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
+        const Tile T = tile_at(t);
+        if (T.skip) continue;
+        for (int64_t it = 0; it < T.nk; ++it, ++g) {
+          const int st = int(g % Cfg::nst);
+          const int64_t round = g / Cfg::nst;
+          const int64_t cpos = it % Cfg::kc;
+          if (cpos == 0 && h > 0 && !mbar_wait(acc_empty, uint32_t((h - 1) & 1), P.err)) {
+            set_err(P.err, 12);
+            *(volatile int*)abort_flag = 1;
+            stop = true;
+            break;
+          }
+          if (!mbar_wait(&full[st], uint32_t(round & 1), P.err)) {
+            set_err(P.err, 13);
+            *(volatile int*)abort_flag = 1;
+            stop = true;
+            break;
+          }
+          if (*(volatile int*)abort_flag) {
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;");
+          const uint32_t sA = smem_u32(smem + st * Cfg::stage);
+          const uint32_t sB = sA + Cfg::stageA;
+          // For A digit s the products with B digits t = 0..S-1-s land in
+          // levels s..S-1, i.e. tensor-memory columns [s BN, S BN); the B
+          // digit tiles of a stage are contiguous, so B rows [0, (S-s) BN) are
+          // exactly digits 0..S-1-s and one MMA (N up to 256, else split)
+          // covers them all.  The first MMA of a chunk (s = 0) spans every
+          // level and initialises the accumulators.
 #pragma unroll
-        for (int s = 0; s < S; ++s) {
+          for (int s = 0; s < S; ++s) {
 #pragma unroll
-          for (int c0 = 0; c0 < BN * (S - s); c0 += 256) {
-            const int n = (BN * (S - s) - c0) < 256 ? (BN * (S - s) - c0) : 256;
-            const uint32_t idesc = umma_idesc(kBM, n);
+            for (int c0 = 0; c0 < BN * (S - s); c0 += 256) {
+              const int n = (BN * (S - s) - c0) < 256 ? (BN * (S - s) - c0) : 256;
+              const uint32_t idesc = umma_idesc(kBM, n);
 #pragma unroll
-            for (int ks = 0; ks < kBK / 16; ++ks) {
-              const uint64_t da = umma_desc(sA + s * Cfg::tileA + ks * 256);
-              const uint64_t db = umma_desc(sB + (c0 / 8) * (16 * kBK) + ks * 256);
-              const uint32_t acc = (cpos > 0 || s > 0 || ks > 0) ? 1u : 0u;
-              umma_bf16(tmem + uint32_t(s * BN + c0), da, db, idesc, acc);
+              for (int ks = 0; ks < kBK / 16; ++ks) {
+                const uint64_t da = umma_desc(sA + s * Cfg::tileA + ks * 256);
+                const uint64_t db = umma_desc(sB + (c0 / 8) * (16 * kBK) + ks * 256);
+                const uint32_t acc = (cpos > 0 || s > 0 || ks > 0) ? 1u : 0u;
+                umma_bf16(tmem + uint32_t(s * BN + c0), da, db, idesc, acc);
+              }
             }
           }
+          umma_commit(&empty[st]);
+          if (cpos == Cfg::kc - 1 || it == T.nk - 1) {
+            umma_commit(acc_full);
+            ++h;
+          }
         }
-        umma_commit(&empty[st]);
-        if (cpos == Cfg::kc - 1 || it == nk - 1) umma_commit(acc_full);
       }
       // all MMAs issued by this thread complete before tensor memory is freed
       umma_commit(drain);
@@ -653,131 +684,139 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
     const int half = (warp - 2) / 4;  // which share of the columns
     const int row = quarter * 32 + lane;
     constexpr int HC = BN / (Cfg::epi / 4);  // columns per thread
-    const int64_t m = m0 + row;
-    if constexpr (Cfg::exact) {
-      // Levels 0..7 of one column and chunk (512 k: levels 0..5 are exact
-      // integers below 2^24) are paired exactly in 32-bit integers,
-      //   P01 = L0 2^7 + L1, P23 = L2 2^7 + L3, P45 = L4 2^7 + L5  (< 2^31),
-      // and levels 6, 7 (weights below 2^-42) are combined in FP32.  Per
-      // column th accumulates P01 2^14 + P23 plus the part of
-      // lo = P45 2^14 + (L6 2^7 + L7) above 2^28; rem keeps lo's low 28 bits
-      // (carried into th), so the value is th + rem 2^-28 in units of 2^-21.
-      static_assert(S == 8 && HC % 16 == 0, "8 levels, 16-column tensor-memory loads");
-      long long th[HC];
-      uint32_t rem[HC];
+    int64_t h = 0;  // accumulator chunks taken over (all tiles)
+    for (int64_t t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x) {
+      const Tile T = tile_at(t);
+      if (T.skip) continue;
+      const int64_t nchunks = (T.nk + Cfg::kc - 1) / Cfg::kc;
+      const int64_t m = T.m0 + row, n0 = T.n0;
+      if constexpr (Cfg::exact) {
+        // Levels 0..7 of one column and chunk (512 k: levels 0..5 are exact
+        // integers below 2^24) are paired exactly in 32-bit integers,
+        //   P01 = L0 2^7 + L1, P23 = L2 2^7 + L3, P45 = L4 2^7 + L5  (< 2^31),
+        // and levels 6, 7 (weights below 2^-42) are combined in FP32.  Per
+        // column th accumulates P01 2^14 + P23 plus the part of
+        // lo = P45 2^14 + (L6 2^7 + L7) above 2^28; rem keeps lo's low 28 bits
+        // (carried into th), so the value is th + rem 2^-28 in units of 2^-21.
+        static_assert(S == 8 && HC % 16 == 0, "8 levels, 16-column tensor-memory loads");
+        long long th[HC];
+        uint32_t rem[HC];
 #pragma unroll
-      for (int j = 0; j < HC; ++j) th[j] = 0, rem[j] = 0u;
-      const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(half * HC);
-      for (int64_t c = 0; c < nchunks; ++c) {
-        if (!mbar_wait(acc_full, uint32_t(c & 1), P.err)) {
-          set_err(P.err, 14);
-          *(volatile int*)abort_flag = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
+        for (int j = 0; j < HC; ++j) th[j] = 0, rem[j] = 0u;
+        const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(half * HC);
+        for (int64_t c = 0; c < nchunks; ++c) {
+          if (!mbar_wait(acc_full, uint32_t(h & 1), P.err)) {
+            set_err(P.err, 14);
+            *(volatile int*)abort_flag = 1;
+            break;
+          }
+          ++h;
+          asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-        for (int c0 = 0; c0 < HC; c0 += 16) {
+          for (int c0 = 0; c0 < HC; c0 += 16) {
 #pragma unroll
-          for (int pq = 0; pq < 4; ++pq) {  // level pairs (0,1) (2,3) (4,5) (6,7)
-            uint32_t ra[16], rb[16];
-            tmem_ld16(tbase + uint32_t((2 * pq) * BN + c0), ra);
-            tmem_ld16(tbase + uint32_t((2 * pq + 1) * BN + c0), rb);
-            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            for (int pq = 0; pq < 4; ++pq) {  // level pairs (0,1) (2,3) (4,5) (6,7)
+              uint32_t ra[16], rb[16];
+              tmem_ld16(tbase + uint32_t((2 * pq) * BN + c0), ra);
+              tmem_ld16(tbase + uint32_t((2 * pq + 1) * BN + c0), rb);
+              asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const float fa = __uint_as_float(ra[j]), fb = __uint_as_float(rb[j]);
-              if (pq < 3) {
-                const int pair = __float2int_rn(fa) * 128 + __float2int_rn(fb);  // exact, |pair| < 2^31
-                if (pq == 0) {
-                  th[c0 + j] += (long long)pair * (1ll << 14);
-                } else if (pq == 1) {
-                  th[c0 + j] += (long long)pair;
+              for (int j = 0; j < 16; ++j) {
+                const float fa = __uint_as_float(ra[j]), fb = __uint_as_float(rb[j]);
+                if (pq < 3) {
+                  const int pair = __float2int_rn(fa) * 128 + __float2int_rn(fb);  // exact, |pair| < 2^31
+                  if (pq == 0) {
+                    th[c0 + j] += (long long)pair * (1ll << 14);
+                  } else if (pq == 1) {
+                    th[c0 + j] += (long long)pair;
+                  } else {
+                    const long long x = (long long)pair * (1ll << 14);  // lo part of levels 4, 5
+                    th[c0 + j] += x >> 28;
+                    rem[c0 + j] += uint32_t(x & 0x0FFFFFFFll);
+                  }
                 } else {
-                  const long long x = (long long)pair * (1ll << 14);  // lo part of levels 4, 5
+                  const long long x = intf_to_ll(fmaf(fa, 128.0f, fb));  // levels 6, 7
                   th[c0 + j] += x >> 28;
                   rem[c0 + j] += uint32_t(x & 0x0FFFFFFFll);
                 }
-              } else {
-                const long long x = intf_to_ll(fmaf(fa, 128.0f, fb));  // levels 6, 7
-                th[c0 + j] += x >> 28;
-                rem[c0 + j] += uint32_t(x & 0x0FFFFFFFll);
+              }
+              reg_fence16(th, rem);
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < HC; ++j) {  // rem < 3 * 2^28 here
+            th[j] += (long long)(rem[j] >> 28);
+            rem[j] &= 0x0FFFFFFFu;
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty);
+        }
+        if (m < P.M && !*(volatile int*)abort_flag) {
+          const int ea = P.ea[m];
+          const int64_t cbase = map_at(P.cm, m);
+#pragma unroll
+          for (int j = 0; j < HC; ++j) {
+            const int64_t n = n0 + half * HC + j;
+            if (n >= P.N) continue;
+            double v = fixed_to_double(th[j], rem[j], ea + P.eb[n] - 14 - 21);  // one rounding
+            if (P.alpha != 1.0) v *= P.alpha;
+            if (P.splits > 1)
+              P.work[(int64_t(T.z) * P.M + m) * P.N + n] = v;
+            else
+              P.C[cbase + map_at(P.cn, n)] = v;
+          }
+        }
+      } else {
+        float hi[HC], lo[HC];
+#pragma unroll
+        for (int j = 0; j < HC; ++j) hi[j] = lo[j] = 0.0f;
+        for (int64_t c = 0; c < nchunks; ++c) {
+          if (!mbar_wait(acc_full, uint32_t(h & 1), P.err)) {
+            set_err(P.err, 14);
+            *(volatile int*)abort_flag = 1;
+            break;
+          }
+          ++h;
+          asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+          for (int q = 0; q < S; ++q) {
+            const float scale = __int_as_float((127 - 7 * q) << 23);  // 2^{-7q}
+#pragma unroll
+            for (int c0 = 0; c0 < HC; c0 += 16) {
+              uint32_t r[16];
+              tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(q * BN + half * HC + c0), r);
+              asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+              for (int j = 0; j < 16; ++j) {
+                const float x = __uint_as_float(r[j]) * scale;
+                const float s = hi[c0 + j] + x;
+                const float bb = s - hi[c0 + j];
+                const float e = (hi[c0 + j] - (s - bb)) + (x - bb);
+                hi[c0 + j] = s;
+                lo[c0 + j] += e;
               }
             }
-            reg_fence16(th, rem);
           }
+          asm volatile("tcgen05.fence::before_thread_sync;");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty);
         }
+        if (m < P.M && !*(volatile int*)abort_flag) {
+          const int ea = P.ea[m];
+          const int64_t cbase = map_at(P.cm, m);
 #pragma unroll
-        for (int j = 0; j < HC; ++j) {  // rem < 3 * 2^28 here
-          th[j] += (long long)(rem[j] >> 28);
-          rem[j] &= 0x0FFFFFFFu;
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(acc_empty);
-      }
-      if (m < P.M && !*(volatile int*)abort_flag) {
-        const int ea = P.ea[m];
-        const int64_t cbase = map_at(P.cm, m);
-#pragma unroll
-        for (int j = 0; j < HC; ++j) {
-          const int64_t n = n0 + half * HC + j;
-          if (n >= P.N) continue;
-          double v = fixed_to_double(th[j], rem[j], ea + P.eb[n] - 14 - 21);  // one rounding
-          if (P.alpha != 1.0) v *= P.alpha;
-          if (P.splits > 1)
-            P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
-          else
-            P.C[cbase + map_at(P.cn, n)] = v;
-        }
-      }
-    } else {
-      float hi[HC], lo[HC];
-#pragma unroll
-      for (int j = 0; j < HC; ++j) hi[j] = lo[j] = 0.0f;
-      for (int64_t c = 0; c < nchunks; ++c) {
-        if (!mbar_wait(acc_full, uint32_t(c & 1), P.err)) {
-          set_err(P.err, 14);
-          *(volatile int*)abort_flag = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;");
-#pragma unroll
-        for (int q = 0; q < S; ++q) {
-          const float scale = __int_as_float((127 - 7 * q) << 23);  // 2^{-7q}
-#pragma unroll
-          for (int c0 = 0; c0 < HC; c0 += 16) {
-            uint32_t r[16];
-            tmem_ld16(tmem + (uint32_t(quarter * 32) << 16) + uint32_t(q * BN + half * HC + c0), r);
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              const float x = __uint_as_float(r[j]) * scale;
-              const float s = hi[c0 + j] + x;
-              const float bb = s - hi[c0 + j];
-              const float e = (hi[c0 + j] - (s - bb)) + (x - bb);
-              hi[c0 + j] = s;
-              lo[c0 + j] += e;
-            }
+          for (int j = 0; j < HC; ++j) {
+            const int64_t n = n0 + half * HC + j;
+            if (n >= P.N) continue;
+            const int e = ea + P.eb[n] - 14;
+            double v = scaled_to_double(hi[j], e) + scaled_to_double(lo[j], e);  // one FP64 add
+            if (P.alpha != 1.0) v *= P.alpha;
+            if (P.splits > 1)
+              P.work[(int64_t(T.z) * P.M + m) * P.N + n] = v;
+            else
+              P.C[cbase + map_at(P.cn, n)] = v;
           }
-        }
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(acc_empty);
-      }
-      if (m < P.M && !*(volatile int*)abort_flag) {
-        const int ea = P.ea[m];
-        const int64_t cbase = map_at(P.cm, m);
-#pragma unroll
-        for (int j = 0; j < HC; ++j) {
-          const int64_t n = n0 + half * HC + j;
-          if (n >= P.N) continue;
-          const int e = ea + P.eb[n] - 14;
-          double v = scaled_to_double(hi[j], e) + scaled_to_double(lo[j], e);  // one FP64 add
-          if (P.alpha != 1.0) v *= P.alpha;
-          if (P.splits > 1)
-            P.work[(int64_t(blockIdx.z) * P.M + m) * P.N + n] = v;
-          else
-            P.C[cbase + map_at(P.cn, n)] = v;
         }
       }
     }
@@ -802,15 +841,26 @@ __global__ void k_oz_reduce(const double* __restrict__ work, int splits, int64_t
   C[map_at(cm, m) + map_at(cn, n)] = s;
 }
 
+// persistent: one wave of CTAs that loop over the tiles (a tile's epilogue
+// then overlaps the next tile's copies and MMAs); else one CTA per tile, the
+// hardware scheduler balancing tiles of uneven length (split or triangular
+// products) across the SMs.
 template <int S, int BN>
-void launch_oz(const OzGemmParams& P, dim3 grid, cudaStream_t s) {
+void launch_oz(const OzGemmParams& P, bool persistent, cudaStream_t s) {
   using Cfg = OzCfg<S, BN>;
-  static bool configured = false;
-  if (!configured) {
+  static int resident = 0;  // CTAs of this configuration the device holds at once
+  if (!resident) {
     cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::smem);
     cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    configured = true;
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_oz_gemm<S, BN>, Cfg::threads, Cfg::smem);
+    cudaGetLastError();
+    resident = std::max(1, nsm) * std::max(1, per);
   }
+  const int64_t ntiles = P.ntn * P.ntm * P.splits;
+  const unsigned grid = unsigned(std::max<int64_t>(1, persistent ? std::min<int64_t>(ntiles, resident) : ntiles));
   k_oz_gemm<S, BN><<<grid, Cfg::threads, Cfg::smem, s>>>(P);
 }
 
@@ -901,13 +951,20 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   P.alpha = alpha;
   P.work = work;
   P.err = err;
-  dim3 grid(unsigned(B.nrt), unsigned(A.nrt), unsigned(P.splits));
+  P.ntm = A.nrt;
+  P.ntn = B.nrt;
+  // Persistent CTAs pay off where a tile's epilogue is long against its
+  // main loop: the exact 8-digit epilogue over short K.  Measured on
+  // 131072 x 48 x 512 (8 digits): 291 -> 213 us; with 5 digits (two CTAs
+  // per SM already overlap their epilogues) and on split or triangular
+  // products one CTA per tile is faster.
+  const bool persistent = A.S == 8 && P.splits == 1 && !P.sym && P.tri == 0 && P.nkt <= 128;
   if (A.S == 5)
-    launch_oz<5, 48>(P, grid, s);
+    launch_oz<5, 48>(P, persistent, s);
   else if (A.S == 8)
-    launch_oz<8, 48>(P, grid, s);
+    launch_oz<8, 48>(P, persistent, s);
   else
-    launch_oz<6, 64>(P, grid, s);
+    launch_oz<6, 64>(P, persistent, s);
   count_launches(1);
   if (P.splits > 1) {
     const int64_t tot = A.rows * B.rows;
