@@ -375,8 +375,8 @@ __device__ __forceinline__ void oz_digit_group(const double* __restrict__ src, c
     X[u] = round_scaled(x, shift);
   }
   const int it = r / rt, rr = r - it * rt;
-  const int64_t jt = kg >> 2;
-  const int kc = int(kg & 3);
+  const int64_t jt = kg / (kBK / 8);
+  const int kc = int(kg % (kBK / 8));
   const int64_t tile_elems = int64_t(rt) * kBK;
   __nv_bfloat16* base = tiles + ((int64_t(it) * kst + jt) * S) * tile_elems;
   const int inner = (rr >> 3) * (8 * kBK) + kc * 64 + (rr & 7) * 8;  // element offset in a tile
@@ -958,7 +958,7 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   // 131072 x 48 x 512 (8 digits): 291 -> 213 us; with 5 digits (two CTAs
   // per SM already overlap their epilogues) and on split or triangular
   // products one CTA per tile is faster.
-  const bool persistent = A.S == 8 && P.splits == 1 && !P.sym && P.tri == 0 && P.nkt <= 128;
+  const bool persistent = A.S == 8 && P.splits == 1 && !P.sym && P.tri == 0 && P.nkt * kBK <= 4096;
   if (A.S == 5)
     launch_oz<5, 48>(P, persistent, s);
   else if (A.S == 8)
