@@ -205,9 +205,9 @@ TRAFFIC_PER_WORK = {"select_gemm": 2.2}
 
 
 # BF16 digit-pair products per FP64-equivalent flop: 5 digits (s + t <= 4) in
-# the fit and exchange products, 8 digits (s + t <= 7) in the selection and in
-# the Coulomb products of the factored fit
-TC_KERNELS = {"fit_zc": 15, "fit_solve": 15, "coulomb_V": 36, "exchange": 15, "select_gemm": 36, "coulomb_w": 36}
+# the fit and exchange products, 7 digits (s + t <= 6) in the Coulomb products
+# of the factored fit, 8 digits (s + t <= 7) in the selection and the W transform
+TC_KERNELS = {"fit_zc": 15, "fit_solve": 15, "coulomb_V": 28, "exchange": 15, "select_gemm": 36, "coulomb_w": 36}
 
 
 def roofline(kern, precision):

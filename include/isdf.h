@@ -288,14 +288,15 @@ isdf_status isdf_propose_residual(isdf_plan_t plan, const int64_t* quota, int64_
  * (the paper has no counterpart; it is this library's building block):
  *   C[m*ldc + n] = alpha * sum_k A[m*lda + k] * B[n*ldb + k]
  * A, B, C are DEVICE pointers (row-major FP64).  Each operand row is scaled
- * by a power of two and split into `slices` BF16 digit planes (5, 6 or 8,
+ * by a power of two and split into `slices` BF16 digit planes (5 to 8,
  * about 7 bits each).  With 5 or 6, digit-pair products accumulate in FP32
  * tensor memory per 1024-wide k chunk and are summed in double-float
  * registers; the error is below 2^-(7*slices-2) * K * max_k|A[m,k]| *
- * max_k|B[n,k]| per element.  With 8 (FP64-grade), the six leading digit
- * levels are summed exactly (512-wide chunks, integer accumulation) and the
- * two smallest, below 2^-42 of the result, in FP32; the error is below
- * 2^-52 * K * max_k|A[m,k]| * max_k|B[n,k]| + 2^-53 |C[m,n]|.
+ * max_k|B[n,k]| per element.  With 7 or 8, the six leading digit levels are
+ * summed exactly (512-wide chunks, integer accumulation) and the rest, below
+ * 2^-42 of the result, in FP32: with 7 the error is below 2^-47 * K *
+ * max_k|A[m,k]| * max_k|B[n,k]|, with 8 (FP64-grade) below 2^-52 * K *
+ * max_k|A[m,k]| * max_k|B[n,k]| + 2^-53 |C[m,n]|.
  * splits > 1 divides K over that many CTAs (needs splits*M*N*8 bytes of
  * scratch, allocated by the call).  Enqueued on `stream`; returns after the
  * stream is idle.  A pipeline wait that exceeds its bound returns

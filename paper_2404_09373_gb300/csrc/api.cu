@@ -724,7 +724,7 @@ isdf_status isdf_propose_residual(isdf_plan_t h, const int64_t* quota, int64_t* 
 isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
                           int64_t ldb, int64_t ldc, double alpha, int slices, int splits, void* stream) {
   if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N ||
-      (slices != 5 && slices != 6 && slices != 8) || splits < 1 || splits > 1024) {
+      (slices < 5 || slices > 8) || splits < 1 || splits > 1024) {
     g_plan_error = "invalid arguments to isdf_gemm_f64";
     return ISDF_ERR_ARG;
   }
@@ -767,7 +767,7 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
 
 isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K,
                                   int64_t lda, int64_t ldb, int64_t ldc, double alpha, int slices, void* stream) {
-  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || (slices != 5 && slices != 6 && slices != 8)) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || (slices < 5 || slices > 8)) {
     g_plan_error = "invalid arguments to isdf_gemm_f64_noalloc";
     return ISDF_ERR_ARG;
   }

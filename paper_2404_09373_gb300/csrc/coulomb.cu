@@ -145,9 +145,11 @@ __global__ void k_sqrt_inplace(int64_t n, double* w) {
 isdf_status coulomb_block_tc(Plan* p, const double2* left, const Level& la, const Level& lb, double* wt2, bool same,
                              double* Cblk) {
   cudaStream_t s = p->stream;
-  // 8 digits (FP64-grade) when the blocks are those of ZC: W = (CC^T)^-1 applied
-  // afterwards amplifies their error by up to cond(CC^T); else 5
-  const int S = (la.zct || lb.zct) ? 8 : 5;
+  // 7 digits (49 fraction bits, exact level sums) when the blocks are those of
+  // ZC: W = (CC^T)^-1 applied afterwards amplifies their error by up to
+  // cond(CC^T) (5 digits missed the 1e-6 Ha bar on the undisplaced cell by
+  // 600x, 7 digits take 2^14 off that); else 5
+  const int S = (la.zct || lb.zct) ? 7 : 5;
   const int64_t K2 = 2 * lb.nq;
   k_sqrt_inplace<<<unsigned((K2 + 255) / 256), 256, 0, s>>>(K2, wt2);
   count_launches(1);

@@ -452,7 +452,10 @@ void launch_digits(const double* src, OzMap rm, OzMap km, const double* kw, doub
     grid.y = unsigned(std::min<int64_t>(rows_pad / 8, 65535));
   }
   __nv_bfloat16* t = static_cast<__nv_bfloat16*>(op.tiles);
-  if (op.S == 5)
+  if (op.S == 7)
+    k_oz_digits<7><<<grid, 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.rt, op.nrt, kg0, ngrp,
+                                        op.kst, order, ridx, t);
+  else if (op.S == 5)
     k_oz_digits<5><<<grid, 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.rt, op.nrt, kg0, ngrp,
                                         op.kst, order, ridx, t);
   else if (op.S == 6)
@@ -509,7 +512,7 @@ struct OzCfg {
   // registers), one when two CTAs share the SM
   static constexpr int epi = exact ? 12 : dual ? 4 : 8;
   static constexpr int threads = 32 * (2 + epi);
-  static_assert(!exact || S == 8, "the integer epilogue splits the levels of exactly 8 digits");
+  static_assert(!exact || S == 7 || S == 8, "the integer epilogue pairs the levels of 7 or 8 digits");
   static_assert(cols <= 512, "levels x BN must fit in tensor memory");
   static_assert(nst >= 2, "need at least two pipeline stages");
   static_assert((BN / (epi / 4)) % 16 == 0, "each epilogue warp reads whole 16-column groups");
@@ -698,7 +701,8 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
         // column th accumulates P01 2^14 + P23 plus the part of
         // lo = P45 2^14 + (L6 2^7 + L7) above 2^28; rem keeps lo's low 28 bits
         // (carried into th), so the value is th + rem 2^-28 in units of 2^-21.
-        static_assert(S == 8 && HC % 16 == 0, "8 levels, 16-column tensor-memory loads");
+        // With 7 digits there is no level 7 (L7 = 0).
+        static_assert(HC % 16 == 0, "16-column tensor-memory loads");
         long long th[HC];
         uint32_t rem[HC];
 #pragma unroll
@@ -718,7 +722,12 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
             for (int pq = 0; pq < 4; ++pq) {  // level pairs (0,1) (2,3) (4,5) (6,7)
               uint32_t ra[16], rb[16];
               tmem_ld16(tbase + uint32_t((2 * pq) * BN + c0), ra);
-              tmem_ld16(tbase + uint32_t((2 * pq + 1) * BN + c0), rb);
+              if (2 * pq + 1 < S) {
+                tmem_ld16(tbase + uint32_t((2 * pq + 1) * BN + c0), rb);
+              } else {  // 7 digits: no level 7
+#pragma unroll
+                for (int j = 0; j < 16; ++j) rb[j] = 0u;
+              }
               asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
               for (int j = 0; j < 16; ++j) {
@@ -927,8 +936,8 @@ void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzO
   count_launches(1);
 }
 
-// S levels x BN columns of tensor memory: 5 x 48 (two CTAs per SM), 6 x 64, 8 x 48
-int oz_bn(int S) { return S == 5 ? 48 : S == 8 ? 48 : 64; }
+// S levels x BN columns of tensor memory: 5 x 48 (two CTAs per SM), 6 x 64, 7 x 48, 8 x 48
+int oz_bn(int S) { return S == 6 ? 64 : 48; }
 
 void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, double alpha, int tri, int sym,
              int splits, double* work, int* err, cudaStream_t s) {
@@ -958,11 +967,13 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   // 131072 x 48 x 512 (8 digits): 291 -> 213 us; with 5 digits (two CTAs
   // per SM already overlap their epilogues) and on split or triangular
   // products one CTA per tile is faster.
-  const bool persistent = A.S == 8 && P.splits == 1 && !P.sym && P.tri == 0 && P.nkt * kBK <= 4096;
+  const bool persistent = A.S >= 7 && P.splits == 1 && !P.sym && P.tri == 0 && P.nkt * kBK <= 4096;
   if (A.S == 5)
     launch_oz<5, 48>(P, persistent, s);
   else if (A.S == 8)
     launch_oz<8, 48>(P, persistent, s);
+  else if (A.S == 7)
+    launch_oz<7, 48>(P, persistent, s);
   else
     launch_oz<6, 64>(P, persistent, s);
   count_launches(1);

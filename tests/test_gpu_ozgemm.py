@@ -37,6 +37,8 @@ def _run(A, B, slices, splits, alpha=1.0):
         (257, 130, 2100, 2, 6),
         (40, 20, 5000, 1, 5),
         (1000, 64, 64, 1, 6),
+        (300, 200, 1500, 1, 7),
+        (129, 97, 700, 2, 7),
     ],
 )
 def test_ozgemm_within_bound(M, N, K, splits, slices):
