@@ -146,8 +146,17 @@ isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* E
                     2.0 * n2 * n2 * N + 2.0 * N * N * n2 + 2.0 * N * N * n;
   {
   Prof pr(p, "exchange", fl, "flop", 13);
-  dgemm(gemm(1, 0, nip, n, N, p->XL, nip, dC, n, yl, n), s);  // Y_L = X^L^T C
-  dgemm(gemm(1, 0, nip, n, N, p->XN, nip, dC, n, yn, n), s);  // Y_N = X^N^T C
+  if (p->opt.precision == 1) {
+    // Y_A[P][i] = sum_mu X^A[mu][P] C[mu][i]: rows P (stride 1, k stride nip) against rows i of C^T
+    if ((st = tc_product(p, p->XL, nip, 1, nip, dC, n, 1, n, N, yl, n, 0)) ||
+        (st = tc_product(p, p->XN, nip, 1, nip, dC, n, 1, n, N, yn, n, 0))) {
+      cleanup();
+      return st;
+    }
+  } else {
+    dgemm(gemm(1, 0, nip, n, N, p->XL, nip, dC, n, yl, n), s);  // Y_L = X^L^T C
+    dgemm(gemm(1, 0, nip, n, N, p->XN, nip, dC, n, yn, n), s);  // Y_N = X^N^T C
+  }
   k_add<<<unsigned((nip * n + 255) / 256), 256, 0, s>>>(nip * n, yl, yn, yg);
   if (p->opt.precision == 1) {
     if ((st = tc_product(p, yg, nip, n, 1, yg, nip, n, 1, n, rgg, nip, 1)) ||
@@ -174,7 +183,15 @@ isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* E
     dgemm(gemm(0, 1, n2, N, n2, W, n2, x2, n2, T, N), s);  // T = W X2^T
     dgemm(gemm(0, 0, N, N, n2, x2, n2, T, N, dK, N), s);   // K = X2 T
   }
-  dgemm(gemm(0, 0, N, n, N, dK, N, dC, n, kc, n), s);    // K C
+  if (p->opt.precision == 1) {
+    // (K C)[mu][i] = sum_nu K[mu][nu] C[nu][i]
+    if ((st = tc_product(p, dK, N, N, 1, dC, n, 1, n, N, kc, n, 0))) {
+      cleanup();
+      return st;
+    }
+  } else {
+    dgemm(gemm(0, 0, N, n, N, dK, N, dC, n, kc, n), s);  // K C
+  }
   const int nb = 512;  // partial sums of the E_x reduction
   k_dot_partial<<<nb, 256, 0, s>>>(N * n, dC, kc, part);
   k_sum_final<<<1, 256, 0, s>>>(nb, part, -1.0, dex);

@@ -908,7 +908,8 @@ void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, doubl
   const OzMap rm = oz_stride(sr), km = oz_stride(sk);
   if (exps_of) {
     cudaMemcpyAsync(op.exps, exps_of->exps, size_t(op.rows) * sizeof(int), cudaMemcpyDeviceToDevice, s);
-  } else if (rowwise && op.K >= 4096) {
+  } else if ((rowwise && op.K >= 4096) || (op.K >= 256 && op.rows <= 8192)) {
+    // few long rows: one block per row (a thread per row would stream its row alone)
     k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, rm, km, op.K, kw, mul, nullptr, op.exps);
   } else {
     k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, nullptr,
