@@ -200,8 +200,9 @@ def run_reference(args):
 # ncu capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum
 # over the algorithmic bytes of the captured launches); absent where no capture
 # of the current kernel exists.  select_gemm: three full-size launches of the
-# 2x2x2 selection, ratio 2.18-2.24 (16-byte digit planes streamed once).
-TRAFFIC_PER_WORK = {"select_gemm": 2.2}
+# 2x2x2 selection (persistent tile loop), ratio 2.21-2.29 (16-byte digit
+# planes streamed once).
+TRAFFIC_PER_WORK = {"select_gemm": 2.25}
 
 
 # BF16 digit-pair products per FP64-equivalent flop: 5 digits (s + t <= 4) in

@@ -916,7 +916,7 @@ void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, doubl
                                                                         op.exps);
   }
   launch_digits(src, rm, km, kw, mul, nullptr, op, 0, op.nkt * (kBK / 8), rowwise ? 1 : 0, s);
-  count_launches(2);
+  count_launches(exps_of ? 1 : 2);
 }
 
 void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzOperand& op, int64_t kg0, int64_t kg1,
