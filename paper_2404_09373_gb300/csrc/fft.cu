@@ -33,8 +33,22 @@ struct DC {
 };
 __device__ __forceinline__ DC dc_add(DC a, DC b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
 __device__ __forceinline__ DC dc_sub(DC a, DC b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+// x y + sgn u v in double-float as one error-free sum of the two leading
+// products, their exact rounding errors and the cross terms (the lo * lo
+// terms, below 2^-48 of the result, are dropped as in df_mul)
+__device__ __forceinline__ DF df_dot2(DF x, DF y, DF u, DF v, float sgn) {
+  const float p = __fmul_rn(x.hi, y.hi), q = __fmul_rn(sgn * u.hi, v.hi);
+  float e = __fmaf_rn(x.hi, y.hi, -p);
+  e = __fadd_rn(e, __fmaf_rn(sgn * u.hi, v.hi, -q));
+  e = __fmaf_rn(x.hi, y.lo, e);
+  e = __fmaf_rn(x.lo, y.hi, e);
+  e = __fmaf_rn(sgn * u.hi, v.lo, e);
+  e = __fmaf_rn(sgn * u.lo, v.hi, e);
+  const DF s = two_sum(p, q);
+  return quick_two_sum(s.hi, __fadd_rn(s.lo, e));
+}
 __device__ __forceinline__ DC dc_mul(DC a, DC b) {
-  return {df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)), df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+  return {df_dot2(a.re, b.re, a.im, b.im, -1.0f), df_dot2(a.re, b.im, a.im, b.re, 1.0f)};
 }
 __device__ __forceinline__ DC dc_mul_mi(DC a) { return {a.im, df_neg(a.re)}; }  // a * (-i)
 __device__ __forceinline__ DC dc_mul_pi(DC a) { return {df_neg(a.im), a.re}; }  // a * (+i)
