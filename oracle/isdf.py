@@ -437,7 +437,7 @@ def run(system, C, nip, tol=0.0, tie_rel=1e-9, tie_abs=1e-13, reg_rel=1e-14, piv
     """Selection -> fit -> Coulomb -> exchange, all FP64 on the CPU.
 
     If ``pivots`` is given the selection is skipped and those pivots are fitted
-    (used to judge the later steps on their own).
+    (used to check the later steps on their own).
     """
     funcs = expand_functions(system)
     levels = _level_data(system, funcs)

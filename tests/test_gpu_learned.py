@@ -3,7 +3,7 @@ against NumPy, exact top-K, and what the trained network gains.
 
 The gain test trains on seeded displaced cells (labels = the full greedy
 selection's picks), then selects on a held-out cell from 4 N_ip candidates.
-Judge: the oracle's exchange error |K - K_nofit| (exact no-fit exchange), for
+Measure: the oracle's exchange error |K - K_nofit| (exact no-fit exchange), for
 the learned selection against the full one; an untrained network must trip
 the fallback check instead.
 """
@@ -135,7 +135,7 @@ def test_propose_returns_exact_top_k_in_order():
     np.testing.assert_array_equal(got, np.concatenate(ref))
 
 
-def test_learned_proposer_gain_judged_by_oracle_exchange_error():
+def test_learned_proposer_gain_measured_by_oracle_exchange_error():
     per_cell = (24, 12, 6)
     cells = Lr.training_cells(12, per_cell=per_cell)
     stats = {}
