@@ -133,6 +133,7 @@ __global__ void k_potrf_diag(double* A, int64_t lda, int64_t kb, int b, int* err
   const int tid = threadIdx.x;
   for (int e = tid; e < b * b; e += blockDim.x) s[e / b][e % b] = A[(kb + e / b) * lda + kb + e % b];
   __syncthreads();
+  __shared__ double rpiv;
   for (int j = 0; j < b; ++j) {
     if (tid == 0) {
       double d = s[j][j];
@@ -141,10 +142,11 @@ __global__ void k_potrf_diag(double* A, int64_t lda, int64_t kb, int b, int* err
         d = 1.0;
       }
       s[j][j] = sqrt(d);
+      rpiv = 1.0 / s[j][j];  // one division per column; the column is scaled by the reciprocal
     }
     __syncthreads();
-    const double piv = s[j][j];
-    for (int i = j + 1 + tid; i < b; i += blockDim.x) s[i][j] /= piv;
+    const double rp = rpiv;
+    for (int i = j + 1 + tid; i < b; i += blockDim.x) s[i][j] *= rp;
     __syncthreads();
     for (int e = tid; e < (b - j - 1) * (b - j - 1); e += blockDim.x) {
       const int i = j + 1 + e / (b - j - 1), c = j + 1 + e % (b - j - 1);
@@ -161,12 +163,16 @@ __global__ void k_potrf_diag(double* A, int64_t lda, int64_t kb, int b, int* err
 // Rows i >= r0 of the panel: x L_kk^T = a  (forward substitution per row).
 __global__ __launch_bounds__(64) void k_trsm_panel(double* A, int64_t lda, int64_t n, int64_t kb, int b, int64_t r0) {
   __shared__ double l[CB][CB + 1];
+  __shared__ double rdiag[CB];
   for (int e = threadIdx.x; e < CB * CB; e += blockDim.x) {
     const int i = e / CB, c = e % CB;
     double v = (i == c) ? 1.0 : 0.0;
     if (i < b && c < b) v = A[(kb + i) * lda + kb + c];
     l[i][c] = v;
   }
+  __syncthreads();
+  // reciprocals of the diagonal once per CTA: the rows then multiply
+  for (int c = threadIdx.x; c < CB; c += blockDim.x) rdiag[c] = 1.0 / l[c][c];
   __syncthreads();
   const int64_t row = r0 + int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (row >= n) return;
@@ -178,7 +184,7 @@ __global__ __launch_bounds__(64) void k_trsm_panel(double* A, int64_t lda, int64
     double v = x[c];
 #pragma unroll
     for (int p = 0; p < c; ++p) v -= x[p] * l[c][p];
-    x[c] = v / l[c][c];
+    x[c] = v * rdiag[c];
   }
 #pragma unroll
   for (int c = 0; c < CB; ++c)
