@@ -33,17 +33,23 @@ __global__ void k_tab1d(int nG, int n, double Lax, const double* __restrict__ A,
 }
 
 // Phi[r][g] = tx[r][i] ty[r][j] tz[r][k], g = i + nx (j + ny k)
+// One warp per grid line (function r, y index j, z index k): the line's
+// factor ty * tz is formed once, the lanes walk x with coalesced stores, so
+// every value costs one FP64 multiply and no 64-bit division.
 __global__ void k_phi(int nG, int nx, int ny, int nz, const double* __restrict__ tx, const double* __restrict__ ty,
                       const double* __restrict__ tz, double* __restrict__ phi) {
-  const int64_t ng = int64_t(nx) * ny * nz;
-  const int64_t total = ng * nG;
-  for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total; e += int64_t(gridDim.x) * blockDim.x) {
-    const int r = int(e / ng);
-    const int64_t g = e - int64_t(r) * ng;
-    const int i = int(g % nx);
-    const int j = int((g / nx) % ny);
-    const int k = int(g / (int64_t(nx) * ny));
-    phi[e] = tx[int64_t(r) * nx + i] * ty[int64_t(r) * ny + j] * tz[int64_t(r) * nz + k];
+  const int lane = threadIdx.x & 31;
+  const int64_t nyz = int64_t(ny) * nz, nlines = nyz * nG;
+  const int64_t ng = nyz * nx;
+  const int64_t wstride = int64_t(gridDim.x) * (blockDim.x >> 5);
+  for (int64_t line = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); line < nlines; line += wstride) {
+    const int64_t r = line / nyz;
+    const int rem = int(line - r * nyz);
+    const int k = rem / ny, j = rem - k * ny;
+    const double yz = ty[r * ny + j] * tz[r * nz + k];
+    const double* __restrict__ xr = tx + r * nx;
+    double* __restrict__ out = phi + r * ng + (int64_t(k) * ny + j) * nx;
+    for (int i = lane; i < nx; i += 32) out[i] = xr[i] * yz;
   }
 }
 
