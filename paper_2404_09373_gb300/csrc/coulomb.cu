@@ -165,7 +165,10 @@ isdf_status coulomb_block_tc(Plan* p, const double2* left, const Level& la, cons
     // FP64 read twice (row scales, digits), S BF16 digits written per value
     Prof pr(p, "coulomb_slice", double(la.k + lb.k) * double(K2) * (16.0 + 2.0 * S), "byte", 4);
     oz_slice(reinterpret_cast<const double*>(left), K2, 1, wt2, 1.0, a, s);
-    oz_slice(reinterpret_cast<const double*>(lb.spec), K2, 1, wt2, 1.0, b, s, same ? &a : nullptr);
+    if (same)
+      oz_retile(a, b, s);  // same spectra and weights: B's digits are A's, re-tiled
+    else
+      oz_slice(reinterpret_cast<const double*>(lb.spec), K2, 1, wt2, 1.0, b, s);
   }
   int64_t tiles = a.nrt * b.nrt;
   if (same) tiles = (tiles + a.nrt) / 2;

@@ -201,6 +201,9 @@ void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, doubl
 // op.K is the current K (entries at k >= op.K are written as zero).
 // exps_ready: the row scales are already in op.exps (they must bound every
 // |x| the operand will ever hold).  Groups outside the window are untouched.
+// the same digits in another row-tile height (same rows, K, S and k tiles);
+// copies lines of 8 rows instead of slicing the FP64 source again
+void oz_retile(const OzOperand& from, OzOperand& to, cudaStream_t s);
 void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzOperand& op, int64_t kg0, int64_t kg1,
                  bool exps_ready, cudaStream_t s);
 // C = alpha * A B^T (A: M x K as the 128-row side, B: N x K); trans: C[n*ldc+m];

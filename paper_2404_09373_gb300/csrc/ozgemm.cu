@@ -440,6 +440,33 @@ __global__ void k_oz_digits(const double* __restrict__ src, OzMap rm, OzMap km, 
   }
 }
 
+// Re-tile an operand's digit planes to another row-tile height: rows of 8
+// (one 512-byte line of a slice for 32 k values) move as whole lines, so the
+// digits are copied, not recomputed.  Rows at or beyond the source's real rows
+// are written as zeros (padding).
+__global__ void k_oz_retile(const __nv_bfloat16* __restrict__ src, int src_rt, int64_t src_kst,
+                            __nv_bfloat16* __restrict__ dst, int dst_rt, int64_t dst_kst, int S, int64_t rows,
+                            int64_t rows_pad, int64_t nkt) {
+  const int lane = threadIdx.x & 31;
+  const int64_t units = (rows_pad / 8) * nkt * S;
+  for (int64_t u = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5; u < units;
+       u += (int64_t(gridDim.x) * blockDim.x) >> 5) {
+    const int s = int(u % S);
+    const int64_t kt = (u / S) % nkt, g8 = u / (int64_t(S) * nkt);
+    const int64_t r0 = g8 * 8;
+    const int64_t dt = r0 / dst_rt, drg = (r0 % dst_rt) / 8;
+    uint4* out = reinterpret_cast<uint4*>(dst + ((dt * dst_kst + kt) * S + s) * int64_t(dst_rt) * kBK + drg * 8 * kBK);
+    uint4 v = make_uint4(0u, 0u, 0u, 0u);
+    if (r0 < rows) {
+      const int64_t st = r0 / src_rt, srg = (r0 % src_rt) / 8;
+      const uint4* in =
+          reinterpret_cast<const uint4*>(src + ((st * src_kst + kt) * S + s) * int64_t(src_rt) * kBK + srg * 8 * kBK);
+      v = in[lane];
+    }
+    out[lane] = v;
+  }
+}
+
 void launch_digits(const double* src, OzMap rm, OzMap km, const double* kw, double mul, const int* ridx,
                    const OzOperand& op, int64_t kg0, int64_t ngrp, int order, cudaStream_t s) {
   const int64_t rows_pad = op.nrt * op.rt;
@@ -917,6 +944,17 @@ void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, doubl
   }
   launch_digits(src, rm, km, kw, mul, nullptr, op, 0, op.nkt * (kBK / 8), rowwise ? 1 : 0, s);
   count_launches(exps_of ? 1 : 2);
+}
+
+void oz_retile(const OzOperand& from, OzOperand& to, cudaStream_t s) {
+  const int64_t rows_pad = to.nrt * to.rt;
+  const int64_t units = (rows_pad / 8) * to.nkt * to.S;
+  const int64_t blocks = std::min<int64_t>((units * 32 + 255) / 256, 152 * 64);
+  k_oz_retile<<<unsigned(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(
+      static_cast<const __nv_bfloat16*>(from.tiles), from.rt, from.kst, static_cast<__nv_bfloat16*>(to.tiles), to.rt,
+      to.kst, to.S, from.rows, rows_pad, to.nkt);
+  cudaMemcpyAsync(to.exps, from.exps, size_t(to.rows) * sizeof(int), cudaMemcpyDeviceToDevice, s);
+  count_launches(1);
 }
 
 void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzOperand& op, int64_t kg0, int64_t kg1,
