@@ -192,10 +192,7 @@ int oz_bn(int S);
 isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, int S, const char* what);
 void oz_free(OzOperand& op);
 // X(r, k) = mul * kw[k] * src[r*sr + k*sk]  (kw nullable)
-// exps_of: an operand already sliced from the same rows (same values, kw and
-// mul): its row scales are copied instead of recomputed
-void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s,
-              const OzOperand* exps_of = nullptr);
+void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s);
 // Gathered rows (row r = source row ridx[r], ridx nullable) and a window
 // [kg0, kg1) of 8-wide k groups of an operand allocated for op.kst k tiles;
 // op.K is the current K (entries at k >= op.K are written as zero).

@@ -929,13 +929,10 @@ void oz_free(OzOperand& op) {
   op.exps = nullptr;
 }
 
-void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s,
-              const OzOperand* exps_of) {
+void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s) {
   const bool rowwise = sr >= sk;  // k contiguous: one block per row
   const OzMap rm = oz_stride(sr), km = oz_stride(sk);
-  if (exps_of) {
-    cudaMemcpyAsync(op.exps, exps_of->exps, size_t(op.rows) * sizeof(int), cudaMemcpyDeviceToDevice, s);
-  } else if ((rowwise && op.K >= 4096) || (op.K >= 256 && op.rows <= 8192)) {
+  if ((rowwise && op.K >= 4096) || (op.K >= 256 && op.rows <= 8192)) {
     // few long rows: one block per row (a thread per row would stream its row alone)
     k_oz_rowexp_block<<<unsigned(op.rows), 256, 0, s>>>(src, rm, km, op.K, kw, mul, nullptr, op.exps);
   } else {
@@ -943,7 +940,7 @@ void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, doubl
                                                                         op.exps);
   }
   launch_digits(src, rm, km, kw, mul, nullptr, op, 0, op.nkt * (kBK / 8), rowwise ? 1 : 0, s);
-  count_launches(exps_of ? 1 : 2);
+  count_launches(2);
 }
 
 void oz_retile(const OzOperand& from, OzOperand& to, cudaStream_t s) {
