@@ -110,3 +110,18 @@ def test_null_plan_calls_are_rejected():
     assert lib.isdf_coulomb(None, None) == B.ISDF_ERR_ARG
     assert lib.isdf_get_size(None, 0) == 0
     lib.isdf_destroy(None)
+
+
+@pytest.mark.parametrize("slices,accepted", [(4, False), (5, True), (6, True), (7, True), (8, True), (9, False)])
+def test_gemm_digit_counts(slices, accepted):
+    """isdf_gemm_f64 takes 5 to 8 digits; the argument check comes before the
+    device-pointer check, so host buffers show which counts pass it."""
+    lib = B.load_library()
+    a = np.zeros((4, 4))
+    st = lib.isdf_gemm_f64(a.ctypes.data, a.ctypes.data, a.ctypes.data, 4, 4, 4, 4, 4, 4, 1.0, slices, 1, None)
+    assert st == B.ISDF_ERR_ARG
+    msg = lib.isdf_last_error(None)
+    if accepted:
+        assert b"device pointers" in msg
+    else:
+        assert b"invalid arguments" in msg
