@@ -57,7 +57,135 @@ def parse():
     ap.add_argument("--no-profile", action="store_true", help="skip the separately profiled step")
     ap.add_argument("--workload", default="2x2x2", choices=["2x2x2", "1x1x1"],
                     help="1x1x1: one cell of the same family (small case for ncu captures)")
+    ap.add_argument("--probe", choices=["gemm", "fft"], default=None,
+                    help="time one building block on its own instead of the step: the tensor-core product "
+                         "(isdf_gemm_f64) or the double-float 3-D transform (isdf_rfft3, next to cuFFT)")
+    ap.add_argument("--M", type=int, default=131072)
+    ap.add_argument("--N", type=int, default=48)
+    ap.add_argument("--K", type=int, default=832)
+    ap.add_argument("--slices", type=int, default=8)
+    ap.add_argument("--nx", type=int, default=96)
+    ap.add_argument("--ny", type=int, default=96)
+    ap.add_argument("--nz", type=int, default=96)
+    ap.add_argument("--batch-vectors", type=int, default=37)
+    ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--launch-summary", default=None, metavar="CSV",
+                    help="summarise an ncu launch list (gpu__time_duration.sum, --csv) by kernel and exit")
     return ap.parse_args()
+
+
+# --------------------------------------------------------------------------- probes and launch lists
+
+
+def _timed_ms(fn, reps, stream):
+    import torch
+
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        stream.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return float(np.median(ts))
+
+
+def probe_gemm(a):
+    """One FP64-accurate tensor-core product through the C ABI (slicing of
+    both operands, then the tcgen05 product), CUDA events on its stream.
+    Seeded normal inputs with a spread of row scales; A is larger than L2 at
+    the default sizes."""
+    import torch
+
+    from paper_2404_09373_gb300 import isdf as B
+
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(1)
+    A = torch.randn((a.M, a.K), generator=g, device=dev, dtype=torch.float64)
+    A *= torch.exp2(torch.randint(-8, 8, (a.M, 1), generator=g, device=dev).to(torch.float64))
+    Bm = torch.randn((a.N, a.K), generator=g, device=dev, dtype=torch.float64)
+    C = torch.empty((a.M, a.N), device=dev, dtype=torch.float64)
+    s = torch.cuda.current_stream()
+    ms = _timed_ms(lambda: B.isdf_gemm_f64(A, Bm, C, slices=a.slices, stream=s.cuda_stream), a.reps, s)
+    ref = A[:256].cpu().numpy() @ Bm.cpu().numpy().T
+    err = float(np.max(np.abs(C[:256].cpu().numpy() - ref)) / np.max(np.abs(ref)))
+    print(json.dumps({"probe": "gemm", "M": a.M, "N": a.N, "K": a.K, "slices": a.slices, "ms_call": ms,
+                      "fp64_operand_gbs": 8.0 * a.M * a.K / ms / 1e6,
+                      "fp64eq_tflops": 2.0 * a.M * a.N * a.K / ms / 1e9, "max_rel_err_vs_numpy": err}))
+    return 0
+
+
+def probe_fft(a):
+    """The double-float 3-D transform (isdf_rfft3) next to torch.fft.rfftn
+    (cuFFT, FP64) on the same seeded grids: time per vector, effective traffic
+    (input and output once), largest difference relative to the grid's l1 norm."""
+    import torch
+
+    from paper_2404_09373_gb300 import isdf as B
+
+    dev = torch.device("cuda", 0)
+    g = torch.Generator(device=dev).manual_seed(1)
+    f = torch.randn((a.batch_vectors, a.nz, a.ny, a.nx), generator=g, device=dev, dtype=torch.float64)
+    S = torch.empty((a.batch_vectors, a.nz, a.ny, a.nx // 2 + 1), dtype=torch.complex128, device=dev)
+    s = torch.cuda.current_stream()
+    ms_df = _timed_ms(lambda: B.isdf_rfft3(f, S, stream=s.cuda_stream), a.reps, s)
+    out = {}
+    ms_cu = _timed_ms(lambda: out.__setitem__("ref", torch.fft.rfftn(f, dim=(1, 2, 3))), a.reps, s)
+    err = float(((S - out["ref"]).abs().amax(dim=(1, 2, 3)) / f.abs().sum(dim=(1, 2, 3))).max())
+    nb = a.batch_vectors * (8 * a.nx * a.ny * a.nz + 16 * (a.nx // 2 + 1) * a.ny * a.nz)
+    print(json.dumps({"probe": "fft", "shape": [a.nx, a.ny, a.nz], "batch": a.batch_vectors,
+                      "us_per_vector_double_float": 1e3 * ms_df / a.batch_vectors,
+                      "us_per_vector_cufft_fp64": 1e3 * ms_cu / a.batch_vectors,
+                      "effective_gbs_double_float": nb / ms_df / 1e6, "max_err_rel_l1": err}))
+    return 0
+
+
+def kernel_name(raw):
+    """Short kernel name with template arguments: k_oz_gemm<8, 48>."""
+    import re
+
+    for ns in ("(anonymous namespace)::", "<unnamed>::", "unnamed>::"):
+        raw = raw.replace(ns, "")
+    m = re.match(r"\s*(?:void\s+)?([\w:]+(?:<[^()]*>)?)", raw)
+    return m.group(1).split("::")[-1] if m else raw
+
+
+_UNIT_NS = {"nsecond": 1.0, "ns": 1.0, "usecond": 1e3, "us": 1e3, "msecond": 1e6, "ms": 1e6, "second": 1e9,
+            "s": 1e9}
+
+
+def launch_summary(path):
+    """Per kernel of an ncu --csv launch list: launches, total device time (ms)
+    and share of the total.  Returns [(name, launches, ms, share)], largest first."""
+    import collections
+    import csv
+
+    rows = list(csv.reader(open(path)))
+    hi = next(i for i, r in enumerate(rows) if "Kernel Name" in r)
+    h = rows[hi]
+    ik, iv, imn = h.index("Kernel Name"), h.index("Metric Value"), h.index("Metric Name")
+    iu = h.index("Metric Unit") if "Metric Unit" in h else None
+    agg = collections.defaultdict(lambda: [0, 0.0])
+    for r in rows[hi + 1:]:
+        if len(r) <= iv or r[imn] != "gpu__time_duration.sum":
+            continue
+        a = agg[kernel_name(r[ik])]
+        a[0] += 1
+        a[1] += float(r[iv].replace(",", "")) * (_UNIT_NS.get(r[iu].strip(), 1.0) if iu is not None else 1.0)
+    tot = sum(v[1] for v in agg.values()) or 1.0
+    return [(k, v[0], v[1] / 1e6, v[1] / tot) for k, v in sorted(agg.items(), key=lambda kv: -kv[1][1])]
+
+
+def print_launch_summary(path):
+    rows = launch_summary(path)
+    print(f"{'kernel':34s} {'launches':>9s} {'total ms':>12s} {'share':>7s}")
+    for k, n, ms, sh in rows:
+        print(f"{k:34s} {n:9d} {ms:12.2f} {100 * sh:6.2f}%")
+    print(f"{'total':34s} {sum(r[1] for r in rows):9d} {sum(r[2] for r in rows):12.2f}")
+    return 0
 
 
 # --------------------------------------------------------------------------- clocks
@@ -248,6 +376,12 @@ def roofline(kern, precision):
 
 def main():
     args = parse()
+    if args.launch_summary:
+        return print_launch_summary(args.launch_summary)
+    if args.probe == "gemm":
+        return probe_gemm(args)
+    if args.probe == "fft":
+        return probe_fft(args)
     if args.impl == "reference":
         return run_reference(args)
     import torch

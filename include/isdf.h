@@ -305,10 +305,11 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
                           int64_t ldb, int64_t ldc, double alpha, int slices, int splits, void* stream);
 
 /* The same product as isdf_gemm_f64 for callers that cannot allocate device
- * memory: code running while a stream capture is open, inside a framework
- * whose allocator owns the device's memory, or on a path where the implicit
- * synchronisation of cudaMalloc/cudaFree is not acceptable.  (The paper has
- * no counterpart; this is an interface of this library only.)
+ * memory: code inside a framework whose caching allocator owns the device's
+ * memory (a cudaMalloc there can fail or fragment the pool), and paths that
+ * cannot take the implicit device synchronisation of cudaMalloc/cudaFree
+ * (a solver loop that must not stall other streams).  (The paper has no
+ * counterpart; this is an interface of this library only.)
  * All scratch -- the BF16 digit planes of both operands, their row scales and
  * an error word -- lives in one static device array of
  * isdf_gemm_f64_noalloc_capacity() bytes (32 MiB), which every GPU that loads
@@ -321,8 +322,10 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
  * caches it; make that first call before any stream capture starts.  Every
  * call on a device shares the one array, so calls whose GPU work overlaps
  * (different streams or host threads) race and corrupt each other: serialise
- * them.  A, B, C are device pointers, same layout, slices and error behaviour
- * as isdf_gemm_f64; returns after `stream` is idle. */
+ * them.  A, B, C must be device pointers (a host pointer is refused with
+ * ISDF_ERR_ARG before anything is launched); same layout, slices and error
+ * behaviour as isdf_gemm_f64, and a launch that cannot start returns
+ * ISDF_ERR_CUDA.  Returns after `stream` is idle. */
 isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K,
                                   int64_t lda, int64_t ldb, int64_t ldc, double alpha, int slices, void* stream);
 int64_t isdf_gemm_f64_noalloc_capacity(void);

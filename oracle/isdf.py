@@ -15,8 +15,7 @@ every step follows the paper's definitions in the paper's order:
   * Section III.A: the four-term multigrid THC form of the ERIs, Eq. 8, used to
     build the exchange matrix.
 
-Readings of places where the paper is silent or garbled (each also listed in
-the design notes):
+Readings of places where the paper is silent or garbled:
   R1 levels: a function of exponent a lives on level l = #{edges e : a < e};
      level 0 is the finest grid.  Level l holds the pairs whose sharper factor
      is on level l: L_l = {mu: l(mu)=l}, N_l = {mu: l(mu)>l}, G_l = L_l u N_l.
@@ -288,19 +287,26 @@ def split_pivots(pivots, nlev):
     return [g[lev == l] for l in range(nlev)]
 
 
-def fit(levels, pivots, reg_rel=1e-14):
+def fit(levels, pivots, reg_rel=1e-14, col_batch=None):
     """Xi_l = (ZC^T)_l (CC^T + lambda I)^-1 on every level (Eq. 3).
 
     With Z the pair densities of level l (pairs x grid) and C = Z[:, P], the
     normal equations of min || Z - C Xi^T || give (ZC^T)_l = M_l[:, P] and
     (CC^T)_l = M_l[P, P].  Solved with an FP64 Cholesky (LAPACK).
+    ``col_batch`` only bounds memory: the columns of (ZC^T)_l are formed that
+    many at a time, each by the same expression as all at once.
     """
     out = []
     for ld, P in zip(levels, split_pivots(pivots, len(levels))):
         if P.size == 0:
             out.append(np.zeros((ld["PhiL"].shape[1], 0)))
             continue
-        ZCt = m_columns(ld, P)
+        if col_batch is None or P.size <= col_batch:
+            ZCt = m_columns(ld, P)
+        else:
+            ZCt = np.empty((ld["PhiL"].shape[1], P.size))
+            for c0 in range(0, P.size, col_batch):
+                ZCt[:, c0:c0 + col_batch] = m_columns(ld, P[c0:c0 + col_batch])
         CCt = ZCt[P, :]
         lam = reg_rel * np.trace(CCt) / P.size
         cf = scipy.linalg.cho_factor(CCt + lam * np.eye(P.size), lower=True)
@@ -357,24 +363,39 @@ def coulomb_pair(Fa, grid_a, Fb, grid_b, edges):
     return V
 
 
-def coulomb(system, Xi):
+def coulomb(system, Xi, col_batch=None):
     """V = (xi_P | xi_Q) over all levels, in global pivot order per level blocks.
 
     Returns the full symmetric matrix ordered level by level (level 0 pivots
-    first, each level's pivots in selection order).
+    first, each level's pivots in selection order).  ``col_batch`` only bounds
+    memory: the Fourier coefficients are taken that many columns at a time and
+    V is filled block by block; every entry is the same sum as without it.
     """
     nlev = len(Xi)
-    F = [fourier_coeffs(Xi[l], system["grids"][l]) for l in range(nlev)]
     sizes = [x.shape[1] for x in Xi]
     off = np.concatenate([[0], np.cumsum(sizes)])
     V = np.zeros((off[-1], off[-1]))
+    if col_batch is None:
+        F = [fourier_coeffs(Xi[l], system["grids"][l]) for l in range(nlev)]
+        for a in range(nlev):
+            for b in range(a, nlev):
+                if sizes[a] == 0 or sizes[b] == 0:
+                    continue
+                blk = coulomb_pair(F[a], system["grids"][a], F[b], system["grids"][b], system["edges"])
+                V[off[a]:off[a + 1], off[b]:off[b + 1]] = blk
+                V[off[b]:off[b + 1], off[a]:off[a + 1]] = blk.T
+        return V
     for a in range(nlev):
-        for b in range(a, nlev):
-            if sizes[a] == 0 or sizes[b] == 0:
-                continue
-            blk = coulomb_pair(F[a], system["grids"][a], F[b], system["grids"][b], system["edges"])
-            V[off[a]:off[a + 1], off[b]:off[b + 1]] = blk
-            V[off[b]:off[b + 1], off[a]:off[a + 1]] = blk.T
+        for a0 in range(0, sizes[a], col_batch):
+            a1 = min(a0 + col_batch, sizes[a])
+            Fa = fourier_coeffs(Xi[a][:, a0:a1], system["grids"][a])
+            for b in range(a, nlev):
+                for b0 in range(a0 if b == a else 0, sizes[b], col_batch):
+                    b1 = min(b0 + col_batch, sizes[b])
+                    Fb = Fa if (b == a and b0 == a0) else fourier_coeffs(Xi[b][:, b0:b1], system["grids"][b])
+                    blk = coulomb_pair(Fa, system["grids"][a], Fb, system["grids"][b], system["edges"])
+                    V[off[a] + a0:off[a] + a1, off[b] + b0:off[b] + b1] = blk
+                    V[off[b] + b0:off[b] + b1, off[a] + a0:off[a] + a1] = blk.T
     return V
 
 

@@ -23,9 +23,11 @@ namespace isdf {
 
 static thread_local std::string g_plan_error;  // failures before a plan exists
 std::atomic<long long> g_launches{0};
+thread_local long long t_launches = 0;
 
 Prof::Prof(Plan* p_, const char* name, double work, const char* unit, int64_t launches) : p(p_) {
-  count_launches(launches);
+  if (launches > 0) count_launches(launches);
+  t0 = t_launches;
   if (!p || !p->opt.profile) return;
   e.name = name;
   e.work = work;
@@ -38,6 +40,7 @@ Prof::Prof(Plan* p_, const char* name, double work, const char* unit, int64_t la
 
 Prof::~Prof() {
   if (!p || !p->opt.profile || !e.a) return;
+  if (e.launches == kLaunchesInside) e.launches = t_launches - t0;
   cudaEventRecord(e.b, p->stream);
   p->pend.push_back(e);
 }
@@ -746,8 +749,11 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
     oz_slice(A, lda, 1, nullptr, 1.0, a, s);
     oz_slice(B, ldb, 1, nullptr, 1.0, b, s);
     oz_gemm(a, b, C, ldc, 0, alpha, 0, 0, splits, work, err, s);
-    cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
-    const cudaError_t e = cudaStreamSynchronize(s);
+    cudaError_t e = cudaGetLastError();  // a launch that could not start
+    if (e == cudaSuccess) {
+      cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+      e = cudaStreamSynchronize(s);
+    }
     if (e != cudaSuccess) {
       g_plan_error = std::string("isdf_gemm_f64: ") + cudaGetErrorString(e);
       st = ISDF_ERR_CUDA;
@@ -769,6 +775,12 @@ isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, i
                                   int64_t lda, int64_t ldb, int64_t ldc, double alpha, int slices, void* stream) {
   if (!A || !B || !C || M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N || (slices < 5 || slices > 8)) {
     g_plan_error = "invalid arguments to isdf_gemm_f64_noalloc";
+    return ISDF_ERR_ARG;
+  }
+  // a host or stale pointer would reach the kernels as an address: refuse it
+  // here, before anything is launched
+  if (!is_device_ptr(A) || !is_device_ptr(B) || !is_device_ptr(C)) {
+    g_plan_error = "isdf_gemm_f64_noalloc takes device pointers";
     return ISDF_ERR_ARG;
   }
   std::string why;

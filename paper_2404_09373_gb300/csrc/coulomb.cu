@@ -180,7 +180,7 @@ isdf_status coulomb_block_tc(Plan* p, const double2* left, const Level& la, cons
   }
   {
     const double work_fl = same ? double(la.k) * double(la.k + 1) * double(K2) : 2.0 * la.k * double(lb.k) * K2;
-    Prof pr(p, "coulomb_V", work_fl, "flop", 0);
+    Prof pr(p, "coulomb_V", work_fl, "flop", kLaunchesInside);
     oz_gemm(a, b, Cblk, p->nip, 0, 1.0, 0, same ? 1 : 0, int(splits), work, p->d_ozerr, s);
   }
   st = oz_check(p);
@@ -228,7 +228,7 @@ isdf_status apply_w(Plan* p) {
   for (int l = 0; l < p->nlev; ++l) flop += 2.0 * std::pow(double(p->lev[l].k), 3.0);
   for (int x = 0; x < p->nlev; ++x)
     for (int y = x; y < p->nlev; ++y) flop += 2.0 * 2.0 * double(p->lev[x].k) * p->lev[y].k * (p->lev[x].k + p->lev[y].k) / 2.0;
-  Prof pr(p, "coulomb_w", flop, "flop", 0);
+  Prof pr(p, "coulomb_w", flop, "flop", kLaunchesInside);
   // W_l[m][n] = sum_kk R^-1[kk][m] R^-1[kk][n]
   for (int l = 0; l < p->nlev; ++l) {
     const int k = p->lev[l].k;

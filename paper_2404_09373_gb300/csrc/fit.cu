@@ -76,7 +76,7 @@ isdf_status fit_products_tc(Plan* p, Level& lv, int k, const double* phiP, doubl
   oz_slice(lv.phi, 1, ng, nullptr, 1.0, aL, s);
   oz_slice(phiP, 1, k, nullptr, 1.0, bL, s);
   {
-    Prof pr(p, "fit_zc", 2.0 * double(k) * double(ng) * double(lv.nL), "flop", 0);
+    Prof pr(p, "fit_zc", 2.0 * double(k) * double(ng) * double(lv.nL), "flop", kLaunchesInside);
     oz_gemm(aL, bL, zct, ng, 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
   }
   oz_free(aL);
@@ -89,7 +89,7 @@ isdf_status fit_products_tc(Plan* p, Level& lv, int k, const double* phiP, doubl
     count_launches(1);
     oz_slice(lv.phi, 1, ng, nullptr, 1.0, aG, s);
     oz_slice(phiP, 1, k, kw, 1.0, bG, s);
-    Prof pr(p, "fit_zc", 2.0 * double(k) * double(ng) * double(lv.nG), "flop", 0);
+    Prof pr(p, "fit_zc", 2.0 * double(k) * double(ng) * double(lv.nG), "flop", kLaunchesInside);
     oz_gemm(aG, bG, y, ng, 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
     oz_free(aG);
     oz_free(bG);
@@ -110,7 +110,7 @@ isdf_status fit_solve_tc(Plan* p, int k, const double* zct, double* y, const dou
   const int S = 5;
   OzOperand a, b;
   isdf_status st;
-  Prof pr(p, "fit_solve", (xi_out ? 2.0 : 1.0) * double(k) * double(k + 1) * double(ng), "flop", 0);
+  Prof pr(p, "fit_solve", (xi_out ? 2.0 : 1.0) * double(k) * double(k + 1) * double(ng), "flop", kLaunchesInside);
   // Y^T[g][j] = sum_kk Z^T[g][kk] R^-1[j][kk]   (R^-1 lower: kk <= j)
   if ((st = oz_alloc(p, a, ng, k, 128, S, "solve slices")) || (st = oz_alloc(p, b, k, k, oz_bn(S), S, "solve slices")))
     return oz_free(a), oz_free(b), st;

@@ -60,7 +60,11 @@ struct KStat {
 };
 
 extern std::atomic<long long> g_launches;
-inline void count_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+extern thread_local long long t_launches;  // this host thread's share of g_launches
+inline void count_launches(long long n) {
+  g_launches.fetch_add(n, std::memory_order_relaxed);
+  t_launches += n;
+}
 
 struct Plan {
   cudaStream_t stream = nullptr;
@@ -104,10 +108,14 @@ struct Plan {
   std::string prof_json;
 };
 
-// RAII timer of one launch group on the plan's stream (no-op unless profiling)
+// RAII timer of one launch group on the plan's stream (no-op unless profiling).
+// launches >= 0: the group's launches, counted here; kLaunchesInside: the
+// group's kernels count themselves and the timer records how many ran.
+constexpr int64_t kLaunchesInside = -1;
 struct Prof {
   Plan* p;
   ProfEvent e;
+  long long t0 = 0;
   Prof(Plan* p_, const char* name, double work, const char* unit, int64_t launches);
   ~Prof();
 };

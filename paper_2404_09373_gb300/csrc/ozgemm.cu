@@ -30,6 +30,7 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 
@@ -37,6 +38,8 @@
 
 namespace isdf {
 namespace {
+
+constexpr int kMaxDevices = 64;  // per-device launch set-up and scratch addresses
 
 constexpr int kBM = 128;  // A rows per CTA = TMEM lanes
 constexpr int kBK = kOzBK;  // k values per tile / pipeline stage
@@ -884,19 +887,27 @@ __global__ void k_oz_reduce(const double* __restrict__ work, int splits, int64_t
 template <int S, int BN>
 void launch_oz(const OzGemmParams& P, bool persistent, cudaStream_t s) {
   using Cfg = OzCfg<S, BN>;
-  static int resident = 0;  // CTAs of this configuration the device holds at once
-  if (!resident) {
+  // the shared-memory attributes belong to the current device: set them, and
+  // count the CTAs of this configuration the device holds at once, per device
+  static std::atomic<int> resident[kMaxDevices];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    dev = 0;
+  }
+  int res = resident[dev].load(std::memory_order_acquire);
+  if (!res) {
     cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::smem);
     cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    int dev = 0, nsm = 0, per = 0;
-    cudaGetDevice(&dev);
+    int nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_oz_gemm<S, BN>, Cfg::threads, Cfg::smem);
     cudaGetLastError();
-    resident = std::max(1, nsm) * std::max(1, per);
+    res = std::max(1, nsm) * std::max(1, per);
+    resident[dev].store(res, std::memory_order_release);
   }
   const int64_t ntiles = P.ntn * P.ntm * P.splits;
-  const unsigned grid = unsigned(std::max<int64_t>(1, persistent ? std::min<int64_t>(ntiles, resident) : ntiles));
+  const unsigned grid = unsigned(std::max<int64_t>(1, persistent ? std::min<int64_t>(ntiles, res) : ntiles));
   k_oz_gemm<S, BN><<<grid, Cfg::threads, Cfg::smem, s>>>(P);
 }
 
@@ -1032,7 +1043,7 @@ static __device__ __align__(256) unsigned char g_gemm_static_scratch[kStaticScra
 namespace {
 
 std::mutex g_static_mu;
-void* g_static_addr[64] = {nullptr};
+void* g_static_addr[kMaxDevices] = {nullptr};
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
@@ -1042,8 +1053,17 @@ size_t gemm_noalloc_capacity() { return kStaticScratchBytes; }
 
 isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
                          int64_t ldb, int64_t ldc, double alpha, int slices, cudaStream_t s, std::string& why) {
+  // bound every extent by the array before any size arithmetic: with each of
+  // M, N, K at most the array's byte count the products below cannot overflow
+  const int64_t cap = int64_t(kStaticScratchBytes);
+  if (M > cap || N > cap || K > cap || M * K > cap || N * K > cap) {
+    why = "isdf_gemm_f64_noalloc: operands of " + std::to_string(M) + " x " + std::to_string(K) + " and " +
+          std::to_string(N) + " x " + std::to_string(K) + " exceed what the static array holds (" +
+          std::to_string(kStaticScratchBytes) + " bytes)";
+    return ISDF_ERR_ARG;
+  }
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
     cudaGetLastError();
     why = "no current CUDA device";
     return ISDF_ERR_CUDA;
@@ -1084,7 +1104,9 @@ isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M,
   b.exps = reinterpret_cast<int*>(base + ta + ea + tb);
   int* err = reinterpret_cast<int*>(base + ta + ea + tb + eb);
   // the array keeps the previous call's contents: the error word must start at
-  // zero; every slice byte and every scale read below is rewritten first
+  // zero; every slice byte and every scale read below is rewritten first.
+  // Clear any stale launch error so the check after the launches sees ours.
+  cudaGetLastError();
   if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) {
     cudaGetLastError();
     why = "cudaMemsetAsync of the error word failed";
@@ -1093,8 +1115,15 @@ isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M,
   oz_slice(A, lda, 1, nullptr, 1.0, a, s);
   oz_slice(B, ldb, 1, nullptr, 1.0, b, s);
   oz_gemm(a, b, C, ldc, 0, alpha, 0, 0, 1, nullptr, err, s);
+  // a launch that could not start (configuration, resources) is reported here
+  // and nowhere else: the copy below would succeed with C unwritten
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    why = std::string("isdf_gemm_f64_noalloc: launch failed: ") + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  }
   int herr = 0;
-  cudaError_t e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     why = std::string("isdf_gemm_f64_noalloc: ") + cudaGetErrorString(e);

@@ -49,3 +49,32 @@ def test_fp64_simt_family_on_the_plain_path(monkeypatch):
     _, roof = bench.roofline(kern, 0)
     assert roof["bound"] == "alu" and roof["peak"] == 1.25
     assert roof["achieved"] == pytest.approx(1.0e11 / 50.0e-3 / 1e12)
+
+
+def _write_launches(path, rows):
+    import csv
+
+    with open(path, "w", newline="") as f:
+        w = csv.writer(f)
+        w.writerow(["ID", "Kernel Name", "Metric Name", "Metric Unit", "Metric Value"])
+        for r in rows:
+            w.writerow(r)
+
+
+def test_kernel_name_short_form():
+    assert bench.kernel_name("void (anonymous namespace)::k_oz_gemm<8, 48>(OzGemmParams)") == "k_oz_gemm<8, 48>"
+    assert bench.kernel_name("<unnamed>::k_fft_pass<16>(FftPass)") == "k_fft_pass<16>"
+    assert bench.kernel_name("k_phi(int, int)") == "k_phi"
+
+
+def test_launch_summary_sums_units_and_shares(tmp_path):
+    p = tmp_path / "launches.csv"
+    _write_launches(p, [
+        [0, "void (anonymous namespace)::k_oz_gemm<8, 48>(P)", "gpu__time_duration.sum", "ms", "1.5"],
+        [1, "void (anonymous namespace)::k_oz_gemm<8, 48>(P)", "gpu__time_duration.sum", "us", "500"],
+        [2, "k_phi(int)", "gpu__time_duration.sum", "ns", "2,000,000"],
+        [3, "k_phi(int)", "dram__bytes_read.sum", "byte", "123"],
+    ])
+    rows = {r[0]: r for r in bench.launch_summary(str(p))}
+    assert rows["k_oz_gemm<8, 48>"][1:] == (2, pytest.approx(2.0), pytest.approx(0.5))
+    assert rows["k_phi"][1:] == (1, pytest.approx(2.0), pytest.approx(0.5))

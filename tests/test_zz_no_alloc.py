@@ -68,3 +68,38 @@ def test_noalloc_rejects_operands_beyond_the_static_array():
                                    ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == B_.ISDF_ERR_ARG
     assert b"static array holds" in lib.isdf_last_error(None)
+
+
+def test_noalloc_refuses_host_pointers_and_huge_extents_before_any_launch():
+    """A host pointer (here a NumPy buffer) would reach the kernels as an
+    address; the call refuses it on the host.  Extents whose products would
+    overflow the size arithmetic are refused before that arithmetic."""
+    import torch
+
+    from paper_2404_09373_gb300 import isdf as B_
+
+    lib = B_.load_library()
+    dev = torch.device("cuda:0")
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    M, N, K = 64, 48, 96
+    A = np.ones((M, K))
+    a = torch.from_numpy(A).to(dev)
+    b = torch.ones((N, K), dtype=torch.float64, device=dev)
+    c = torch.zeros((M, N), dtype=torch.float64, device=dev)
+    for pa, pb, pc in ((A.ctypes.data, b.data_ptr(), c.data_ptr()),
+                       (a.data_ptr(), b.data_ptr(), np.zeros((M, N)).ctypes.data)):
+        st = lib.isdf_gemm_f64_noalloc(pa, pb, pc, M, N, K, K, K, N, 1.0, 5, stream)
+        assert st == B_.ISDF_ERR_ARG
+        assert b"device pointers" in lib.isdf_last_error(None)
+    huge = 1 << 40
+    st = lib.isdf_gemm_f64_noalloc(a.data_ptr(), b.data_ptr(), c.data_ptr(), huge, N, huge, huge, huge, N, 1.0, 5,
+                                   stream)
+    assert st == B_.ISDF_ERR_ARG
+    assert b"static array" in lib.isdf_last_error(None)
+    torch.cuda.synchronize()
+    assert float(c.abs().max()) == 0.0  # nothing ran
+    # the entry point still works afterwards
+    st = lib.isdf_gemm_f64_noalloc(a.data_ptr(), b.data_ptr(), c.data_ptr(), M, N, K, K, K, N, 1.0, 5, stream)
+    assert st == B_.ISDF_OK, lib.isdf_last_error(None)
+    torch.cuda.synchronize()
+    assert np.array_equal(c.cpu().numpy(), np.full((M, N), float(K)))
