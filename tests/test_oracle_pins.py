@@ -399,3 +399,123 @@ def test_mlp_closed_form_with_zero_hidden_weights():
     assert abs(g[-1] - ref_b3) <= 1e-14
     ref_L = -np.sum(w * (y * np.log(p) + (1 - y) * np.log(1 - p))) / np.sum(w)
     assert abs(L - ref_L) <= 1e-14
+
+
+# --------------------------------------------------------------------------- normalisation, levels, Adam
+
+
+def _norm_integrals(funcs_hook=None):
+    """sum_g phi(r_g)^2 dV for isolated s and p Gaussians in a large cell.
+
+    The normalisation is defined by int phi^2 dr = 1.  On a periodic grid fine
+    enough that the aliased Fourier terms of phi^2 are below 1e-12 (spacing
+    0.125 bohr for exponents up to 6.4) and a cell large enough that images do
+    not overlap (edge 16 bohr for exponents down to 0.4), the grid sum is the
+    integral to far better than 1e-10: an independent check of the factors
+    (2a/pi)^(3/4) and 2 sqrt(a)."""
+    sysd = S.make_system((1, 1, 1), 0.0, None, ((128, 128, 128),), (), a=16.0, sites=np.array([[0.43, 0.51, 0.47]]),
+                         s_exps=(0.4, 1.6, 6.4), p_exps=(0.6, 2.4), image_tol=1e-16)
+    f = O.expand_functions(sysd)
+    if funcs_hook is not None:
+        funcs_hook(f)
+    phi = O.basis_on_level(sysd, f, np.arange(f["level"].size), 0)
+    dV = 16.0 ** 3 / 128 ** 3
+    return np.sum(phi * phi, axis=1) * dV
+
+
+def test_basis_normalisation_is_unit_norm_on_a_fine_grid():
+    ints = _norm_integrals()
+    assert ints.size == 3 + 2 * 3
+    assert np.max(np.abs(ints - 1.0)) <= 1e-10
+
+
+def test_planted_mistake_in_p_normalisation_breaks_unit_norm():
+    """Dropping the 2 of the p factor 2 sqrt(a) (a plausible slip) is caught."""
+
+    def slip(f):
+        p = np.sum(f["lvec"], axis=1) == 1
+        f["norm"][p] *= 0.5
+
+    ints = _norm_integrals(slip)
+    assert np.max(np.abs(ints - 1.0)) > 0.5
+
+
+# Level of each exponent of the 2x2x2 diamond workload: fine grid for
+# exponents >= 1.6, mid grid for 0.4 <= a < 1.6, coarse grid below 0.4 (the
+# split the workload prescribes; the paper's rule is by exponent, Section II.B).
+LEVEL_TABLE = {0.1: 2, 0.15: 2, 0.4: 1, 0.6: 1, 1.6: 0, 2.4: 0, 6.4: 0}
+
+
+def _levels_of(level_fn):
+    sysd = S.make_system((1, 1, 1), 0.0, None, ((8, 8, 8), (4, 4, 4), (2, 2, 2)), S.LEVEL_EDGES_3)
+    f = level_fn(sysd)
+    return {float(a): int(l) for a, l in zip(f["alpha"], f["level"])}
+
+
+def test_level_rule_matches_the_exponent_table_including_edges():
+    assert _levels_of(O.expand_functions) == LEVEL_TABLE
+    # the L / N / G sets of the 2x2x2 workload: |L| = 320 / 256 / 256, |G| = 832 / 512 / 256
+    sysd = S.make_system((2, 2, 2), 0.0, None, ((8, 8, 8), (4, 4, 4), (2, 2, 2)), S.LEVEL_EDGES_3)
+    f = O.expand_functions(sysd)
+    sizes = [tuple(x.size for x in O.level_sets(f, l)) for l in range(3)]
+    assert sizes == [(320, 512, 832), (256, 256, 512), (256, 0, 256)]
+
+
+def test_planted_mistake_in_level_edges_is_caught():
+    """'a <= e' instead of 'a < e' moves the edge exponents 1.6 and 0.4 down a level."""
+
+    def slip(sysd):
+        f = O.expand_functions(sysd)
+        edges = np.asarray(sysd["level_min_exp"])
+        f["level"] = np.array([int(np.sum(a <= edges)) for a in f["alpha"]])
+        return f
+
+    assert _levels_of(slip) != LEVEL_TABLE
+
+
+def _adam_pin_ok(step):
+    """Closed forms of bias-corrected Adam (Kingma & Ba, Algorithm 1).
+    (i) Constant gradient g: the corrected moments are exactly g and g^2 at
+    every step, so each step moves theta by lr g / (|g| + eps).
+    (ii) Gradients g1 then g2: m_hat_2 = (b1 g1 + g2) / (1 + b1) and
+    v_hat_2 = (b2 g1^2 + g2^2) / (1 + b2)."""
+    lr, eps, b1, b2 = 1e-2, 1e-8, 0.9, 0.999
+    g = np.array([3.0, -0.5, 1e-3, -2e-6])
+    th0 = np.array([0.1, -0.2, 0.3, 0.4])
+    th, m, v = th0.copy(), np.zeros(4), np.zeros(4)
+    ok = True
+    for t in range(1, 6):
+        th, m, v = step(th, m, v, g, t, lr)
+        ok &= np.allclose(th, th0 - t * lr * g / (np.abs(g) + eps), rtol=0, atol=1e-13)
+    g1, g2 = np.array([1.0, -2.0, 0.5, 4.0]), np.array([-0.5, 1.0, 0.25, 3.0])
+    th, m, v = step(th0.copy(), np.zeros(4), np.zeros(4), g1, 1, lr)
+    th1 = th.copy()
+    th, m, v = step(th, m, v, g2, 2, lr)
+    mh = (b1 * g1 + g2) / (1 + b1)
+    vh = (b2 * g1 ** 2 + g2 ** 2) / (1 + b2)
+    ok &= np.allclose(th, th1 - lr * mh / (np.sqrt(vh) + eps), rtol=0, atol=1e-13)
+    return bool(ok)
+
+
+def test_adam_step_matches_closed_forms():
+    from oracle import mlp
+
+    assert _adam_pin_ok(mlp.adam_step)
+
+
+def test_planted_mistakes_in_adam_are_caught():
+    from oracle import mlp
+
+    def no_bias_correction(theta, m, v, grad, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+        m = b1 * m + (1 - b1) * grad
+        v = b2 * v + (1 - b2) * grad * grad
+        return theta - lr * m / (np.sqrt(v) + eps), m, v
+
+    def off_by_one(theta, m, v, grad, t, lr):
+        return mlp.adam_step(theta, m, v, grad, t + 1, lr)
+
+    def betas_swapped(theta, m, v, grad, t, lr):
+        return mlp.adam_step(theta, m, v, grad, t, lr, b1=0.999, b2=0.9)
+
+    for wrong in (no_bias_correction, off_by_one, betas_swapped):
+        assert not _adam_pin_ok(wrong)
