@@ -31,6 +31,8 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstdlib>
+#include <cstring>
 #include <mutex>
 #include <string>
 
@@ -75,9 +77,13 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Bounded wait: gives up after kWaitNs of device time, after kWaitLimit polls,
-// or as soon as any CTA of the launch has recorded an error in *err.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, const int* err) {
+// Bounded wait: gives up after wait_ns of device time, after kWaitLimit polls,
+// or as soon as any CTA of the launch has recorded an error in *err.  The
+// pipeline waits take the launch's limit (kWaitNs unless a host-side fault
+// injection shortens it); the drain waits for copies and MMAs in flight
+// always take kWaitNs.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, const int* err,
+                                          unsigned long long wait_ns = kWaitNs) {
   const uint32_t addr = smem_u32(bar);
   unsigned long long t0 = 0;
   for (long long i = 0; i < kWaitLimit; ++i) {
@@ -91,7 +97,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, const i
     if ((i & 255) == 0) {
       const unsigned long long now = globaltimer_ns();
       if (i == 0) t0 = now;
-      else if (now - t0 > kWaitNs) return false;
+      else if (now - t0 > wait_ns) return false;
       if (err && *(volatile const int*)err) return false;
     }
   }
@@ -514,6 +520,7 @@ struct OzGemmParams {
   double alpha;
   double* work;  // split-K partials [z][M][N]
   int* err;
+  unsigned long long wait_ns;  // limit of each pipeline wait (device time)
 };
 
 template <int S, int BN>
@@ -628,7 +635,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
         for (int64_t it = 0; it < T.nk; ++it, ++g) {
           const int st = int(g % Cfg::nst);
           const int64_t round = g / Cfg::nst;
-          if (round > 0 && !mbar_wait(&empty[st], uint32_t((round - 1) & 1), P.err)) {
+          if (round > 0 && !mbar_wait(&empty[st], uint32_t((round - 1) & 1), P.err, P.wait_ns)) {
             set_err(P.err, 11);
             *(volatile int*)abort_flag = 1;
             break;
@@ -660,13 +667,13 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
           const int st = int(g % Cfg::nst);
           const int64_t round = g / Cfg::nst;
           const int64_t cpos = it % Cfg::kc;
-          if (cpos == 0 && h > 0 && !mbar_wait(acc_empty, uint32_t((h - 1) & 1), P.err)) {
+          if (cpos == 0 && h > 0 && !mbar_wait(acc_empty, uint32_t((h - 1) & 1), P.err, P.wait_ns)) {
             set_err(P.err, 12);
             *(volatile int*)abort_flag = 1;
             stop = true;
             break;
           }
-          if (!mbar_wait(&full[st], uint32_t(round & 1), P.err)) {
+          if (!mbar_wait(&full[st], uint32_t(round & 1), P.err, P.wait_ns)) {
             set_err(P.err, 13);
             *(volatile int*)abort_flag = 1;
             stop = true;
@@ -739,7 +746,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
         for (int j = 0; j < HC; ++j) th[j] = 0, rem[j] = 0u;
         const uint32_t tbase = tmem + (uint32_t(quarter * 32) << 16) + uint32_t(half * HC);
         for (int64_t c = 0; c < nchunks; ++c) {
-          if (!mbar_wait(acc_full, uint32_t(h & 1), P.err)) {
+          if (!mbar_wait(acc_full, uint32_t(h & 1), P.err, P.wait_ns)) {
             set_err(P.err, 14);
             *(volatile int*)abort_flag = 1;
             break;
@@ -811,7 +818,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_block
 #pragma unroll
         for (int j = 0; j < HC; ++j) hi[j] = lo[j] = 0.0f;
         for (int64_t c = 0; c < nchunks; ++c) {
-          if (!mbar_wait(acc_full, uint32_t(h & 1), P.err)) {
+          if (!mbar_wait(acc_full, uint32_t(h & 1), P.err, P.wait_ns)) {
             set_err(P.err, 14);
             *(volatile int*)abort_flag = 1;
             break;
@@ -1007,6 +1014,12 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   P.alpha = alpha;
   P.work = work;
   P.err = err;
+  // host-side fault injection (ISDF_FAULT=oz_wait): every pipeline wait gives
+  // up at once, so the launch takes its error path (error code, copies and
+  // MMAs in flight completed, tensor memory freed) and the call reports
+  // ISDF_ERR_TIMEOUT; nothing faults or hangs
+  const char* fault = std::getenv("ISDF_FAULT");
+  P.wait_ns = (fault && std::strcmp(fault, "oz_wait") == 0) ? 0ull : kWaitNs;
   P.ntm = A.nrt;
   P.ntn = B.nrt;
   // Persistent CTAs pay off where a tile's epilogue is long against its

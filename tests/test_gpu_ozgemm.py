@@ -72,3 +72,26 @@ def test_ozgemm_zero_rows_and_alpha():
     assert np.all(C[5] == 0.0) and np.all(C[:, 7] == 0.0)
     bound = 2.5 * 2.0 ** -33 * 64 * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=1)[None, :]
     assert np.all(np.abs(C - ref) <= bound)
+
+
+@pytest.mark.parametrize("slices", [5, 8])
+def test_expired_pipeline_wait_reports_timeout_and_the_next_call_succeeds(monkeypatch, slices):
+    """Failure detection without a GPU fault: ISDF_FAULT=oz_wait makes every
+    pipeline wait of the tensor-core kernel give up at once (the host passes
+    a zero limit).  The launch records an error code, lets its copies and
+    MMAs in flight finish, frees tensor memory and exits; the call returns
+    ISDF_ERR_TIMEOUT.  The context stays usable: the same product without
+    the injection is correct."""
+    from paper_2404_09373_gb300 import isdf as B_
+
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((1024, 4096))
+    B = rng.standard_normal((96, 4096))
+    monkeypatch.setenv("ISDF_FAULT", "oz_wait")
+    with pytest.raises(B_.IsdfError) as e:
+        _run(A, B, slices, 1)
+    assert e.value.status == B_.ISDF_ERR_TIMEOUT
+    monkeypatch.delenv("ISDF_FAULT")
+    C = _run(A, B, slices, 1)
+    bound = 2.0 ** -(7 * slices - 2) * 4096 * np.abs(A).max(axis=1)[:, None] * np.abs(B).max(axis=1)[None, :]
+    assert np.all(np.abs(C - A @ B.T) <= bound)

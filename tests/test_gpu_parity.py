@@ -217,12 +217,11 @@ def test_exact_prefilter_equals_full_greedy():
 def test_tensor_core_path_small(small):
     """options.precision = 1: fit, Coulomb products on tcgen05 with sliced BF16
     digits.  Selection is unchanged (FP64), so pivots match exactly; K and E_x
-    meet max|dK| <= 1e-6 Ha and |dE_x| <= 1e-6 Ha/atom.  Xi and V are not
-    compared elementwise: they carry the conditioning of CC^T (see
-    assert_parity), K does not."""
+    meet max|dK| <= 1e-6 Ha and |dE_x| <= 1e-6 Ha/atom; Xi and V meet the
+    conditioning-aware bounds of assert_tc_parity."""
     sysd, C, o = small
     g = gpu_run(sysd, C, 300, opts={"precision": 1})
-    dK = assert_parity(g, o, natom=8, k_tol=1e-6, v_rel=None, xi_rel=None)
+    dK = assert_parity(g, o, natom=8, k_tol=1e-6, tc=True)
     assert dK <= 1e-6
 
 
@@ -232,11 +231,11 @@ def test_tensor_core_path_ragged_and_workload1():
     C = S.make_orbitals(sysd, 12, rng)
     o = oracle.run(sysd, C, 350)
     g = gpu_run(sysd, C, 350, opts={"precision": 1})
-    assert_parity(g, o, natom=16, k_tol=1e-6, v_rel=None, xi_rel=None)
+    assert_parity(g, o, natom=16, k_tol=1e-6, tc=True)
     sysd, C, nip = S.config(1)
     o = oracle.run(sysd, C, nip)
     g = gpu_run(sysd, C, nip, opts={"precision": 1})
-    assert_parity(g, o, natom=8, k_tol=1e-6, v_rel=None, xi_rel=None)
+    assert_parity(g, o, natom=8, k_tol=1e-6, tc=True)
 
 
 # --------------------------------------------------------------------------- full size

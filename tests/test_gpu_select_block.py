@@ -81,7 +81,7 @@ def test_blocked_selection_ragged_prefilter_and_ties():
     sysd, C, nip = S.config(1)
     o = oracle.run(sysd, C, nip)
     g = gpu_run(sysd, C, nip, opts={"select_block": 64, "precision": 1})
-    assert_parity(g, o, natom=8, k_tol=1e-6, v_rel=None, xi_rel=None)
+    assert_parity(g, o, natom=8, k_tol=1e-6, tc=True)
 
 
 def test_blocked_selection_candidates_and_tol_stop():
