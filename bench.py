@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 SCF_CHARGE = 7.0  # ISDF charged at 1/7 per SCF iteration
+# threshold-driven plan (Section III, Eq. 6 and the eps_ISDF stop): eps_K puts
+# the finest grid of the 2x2x2 cell at 96 points per axis (exponent 6.4)
+EPS_K = 1e-8
+EPS_ISDF = 1e-5
 METRIC = "ISDF+exchange s/iter (T_ISDF/7 + T_K), 2x2x2 diamond multigrid, max|dK|<=1e-6 Ha"
 WORKLOAD = "diamond 2x2x2 (64 C), N=832, n=128, grids 96^3/48^3/24^3, N_ip=6N=4992"
 
@@ -249,32 +253,45 @@ def peaks():
         return {}
 
 
-def cpu_baseline_sample():
-    """The FP64 oracle as it stands on a bounded sample of the workload: one
-    1x1x1 cell of the same family (8 atoms, same basis, same per-cell grid
-    resolution 48^3/24^3/12^3, N_ip = 6N = 624, n = 16).  Returns s/iter."""
-    import oracle
+GOLDEN = os.path.join(ROOT, "tests", "golden", "diamond2x2x2_oracle")
+
+
+def oracle_full_run():
+    """The oracle's full run of the workload, recorded by
+    tests/golden/make_diamond2x2x2.py (stage times, host, threads), or None."""
+    try:
+        return json.load(open(GOLDEN + ".json"))
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_baseline_sample(reps=1):
+    """The FP64 oracle as it stands on a bounded sample of the workload itself
+    (same system, orbitals and grids; oracle/sample.py: basis values of every
+    8th function, the first 8 greedy steps over all grid points, then fit,
+    Coulomb, pivot factors and exchange on those pivots), timed on this host.
+    The full run's s/iter on this host is estimated as the recorded full run
+    times (this host's sample time / the recording host's sample time)."""
+    from oracle import sample as OS
     from paper_2404_09373_gb300 import systems as S
 
-    rng = np.random.default_rng(S.SEED_BASE + 2)
-    sysd = S.make_system((1, 1, 1), 0.05, rng, ((48, 48, 48), (24, 24, 24), (12, 12, 12)), S.LEVEL_EDGES_3)
-    C = S.make_orbitals(sysd, 16, rng)
-    nip = 6 * S.nbasis(sysd)
-    funcs = oracle.expand_functions(sysd)
-    t0 = time.perf_counter()
-    levels = oracle.isdf._level_data(sysd, funcs)
-    sel = oracle.select_points(levels, nip)
-    Xi = oracle.fit(levels, sel["pivots"], 0.0)
-    V = oracle.coulomb(sysd, Xi)
-    XL, XN = oracle.isdf.pivot_factors(sysd, funcs, sel["pivots"])
-    t1 = time.perf_counter()
-    oracle.exchange(XL, XN, V, C)
-    t2 = time.perf_counter()
-    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
-    return {"value": (t1 - t0) / SCF_CHARGE + (t2 - t1), "unit": "s/iter", "cores": cores, "kind": "oracle",
-            "sample": "FP64 NumPy/SciPy oracle, 1x1x1 cell of the same family (8 C, N=104, n=16, grids "
-                      "48^3/24^3/12^3, N_ip=624), 1/8 of the workload's atoms; BLAS threads = host cores",
-            "T_isdf_s": t1 - t0, "T_exchange_s": t2 - t1}
+    sysd, C, _ = S.config(2)
+    smp = OS.Sample(sysd, C)
+    t = OS.median_seconds(smp, reps)
+    full = oracle_full_run()
+    out = {"unit": "s/iter", "cores": OS.threads(), "kind": "oracle", "sample_s": t,
+           "sample": "FP64 NumPy/SciPy oracle on the 2x2x2 workload's own inputs: basis values of every 8th "
+                     "function on its levels, the first 8 greedy selection steps over all 1,009,152 grid points, "
+                     "fit, Coulomb matrix, pivot factors and exchange build on those 8 pivots; value = the "
+                     "recorded full oracle run's s/iter x (this host's sample time / the recording host's); "
+                     "BLAS threads = host cores"}
+    if full and full.get("sample_s"):
+        out["value"] = full["s_iter"] * t / full["sample_s"]
+        out["full_run"] = {"s_iter": full["s_iter"], "stages_s": full["stages"], "host": full["host"],
+                           "threads": full["cpu_threads"], "sample_s": full["sample_s"]}
+    else:
+        out["value"] = None
+    return out
 
 
 def aggregate_over_ranks(s_iter, ms_step, world, device):
@@ -302,24 +319,51 @@ def dist_env():
 
 
 def run_reference(args):
+    """The oracle on the host cores, on the GPU arm's workload (config,
+    metric, unit): every step is one bounded sample of the workload, scaled
+    to the full run as in cpu_baseline_sample."""
     world, rank, _ = dist_env()
     if rank != 0:
         return 0
-    vals = []
+    from oracle import sample as OS
+    from paper_2404_09373_gb300 import systems as S
+
+    sysd, C, _ = S.config(2)
+    smp = OS.Sample(sysd, C)
     for _ in range(args.warmup):
-        cpu_baseline_sample()
-    for _ in range(args.steps):
-        vals.append(cpu_baseline_sample())
-    v = statistics.mean(x["value"] for x in vals)
+        smp.run()
+    ts = [smp.run() for _ in range(args.steps)]
+    full = oracle_full_run()
+    if not full or not full.get("sample_s"):
+        print(json.dumps({"impl": "reference", "unavailable": "no recorded full oracle run of the workload "
+                                                              "(tests/golden/diamond2x2x2_oracle.json)"}))
+        return 0
+    scale = full["s_iter"] / full["sample_s"]
+    v = statistics.mean(ts) * scale
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s/iter", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(
-                x["T_isdf_s"] + x["T_exchange_s"] for x in vals), "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "sample of: " + WORKLOAD, "sample": vals[0]["sample"]},
-            "cpu_baseline": {k: vals[0][k] for k in ("kind", "cores", "sample")} | {"value": v, "unit": "s/iter"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(ts),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": gpu_config(args, WORKLOAD, 1),
+            "cpu_baseline": {"kind": "oracle", "cores": OS.threads(), "value": v, "unit": "s/iter",
+                             "sample": "each step: the oracle on the workload's own inputs (basis values of every "
+                                       "8th function, 8 greedy steps over all grid points, fit, Coulomb, pivot "
+                                       "factors and exchange on those pivots); value = mean step time x the "
+                                       "recorded full run / sample ratio "
+                                       f"({full['s_iter']:.2f} s/iter / {full['sample_s']:.2f} s on "
+                                       f"{full['host']}, {full['cpu_threads']} threads)",
+                             "full_run": {"s_iter": full["s_iter"], "host": full["host"],
+                                          "threads": full["cpu_threads"]}},
             "e2e": {"value": v, "unit": "s/iter", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def gpu_config(args, workload, world):
+    return {"workload": workload, "precision": "plain FP64" if args.precision == 0 else
+            "tensor-core sliced BF16 (FP64-accurate) contractions, FP64 pivot decisions/Cholesky/E_x",
+            "prefilter": args.prefilter, "select_block": args.select_block,
+            "l2": "inputs larger than L2 (basis values 6.4 GB, interpolation vectors > 15 GB)",
+            "parallelism": f"replicas x{world}"}
 
 
 # --------------------------------------------------------------------------- GPU arm
@@ -414,26 +458,37 @@ def main():
     piv_dev = torch.empty(nip, dtype=torch.int64, device=dev)
     opts = {"precision": args.precision, "prefilter": args.prefilter, "select_block": args.select_block}
 
-    def step(profile=False, o=None):
+    KC_dev = torch.empty((N, n), dtype=torch.float64, device=dev)
+    K_aux = torch.empty((N, N), dtype=torch.float64, device=dev)  # exchange of the threshold-driven plan
+
+    def step(profile=False, o=None, sysx=None, nipx=None, tol=0.0, occ=False):
+        """One pass of the path; sysx / nipx / tol: another system, pivot cap
+        and eps_ISDF stop (the threshold-driven plan); occ: also time the
+        occ-RI output isdf_exchange_occ after the exchange."""
         o = opts if o is None else o
-        ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+        main = sysx is None
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(7)]
         with torch.cuda.stream(stream):
             ev[0].record(stream)
-            plan = B.isdf_plan(sysd, dict(o, profile=int(profile)), stream=stream.cuda_stream)
+            plan = B.isdf_plan(sysd if main else sysx, dict(o, profile=int(profile)), stream=stream.cuda_stream)
             ev[1].record(stream)
-            p, _ = B.isdf_select_points(plan, nip, piv_out=piv_dev)
+            p, _ = B.isdf_select_points(plan, nip if main else nipx, tol, piv_out=piv_dev if main else None)
             ev[2].record(stream)
             B.isdf_fit(plan, p)
             ev[3].record(stream)
-            B.isdf_coulomb(plan, V_dev)
+            B.isdf_coulomb(plan, V_dev if main else None)
             ev[4].record(stream)
-            _, ex = B.isdf_exchange(plan, C_dev, K_dev)
+            _, ex = B.isdf_exchange(plan, C_dev, K_dev if main else K_aux)
             ev[5].record(stream)
+            ex_occ = B.isdf_exchange_occ(plan, C_dev, KC_dev)[1] if occ else None
+            ev[6].record(stream)
         stream.synchronize()
         prof = B.isdf_profile_json(plan) if profile else None
+        nip_level = B.isdf_get(plan, B.GET_NIP_LEVEL).tolist()
         plan.close()
-        t = [ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(5)]
-        return {"plan": t[0], "select": t[1], "fit": t[2], "coulomb": t[3], "exchange": t[4], "Ex": ex, "prof": prof}
+        t = [ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(6)]
+        return {"plan": t[0], "select": t[1], "fit": t[2], "coulomb": t[3], "exchange": t[4], "Ex": ex, "prof": prof,
+                "exchange_occ": t[5] if occ else None, "Ex_occ": ex_occ, "nip_level": nip_level}
 
     def barrier():
         if world > 1:
@@ -470,6 +525,27 @@ def main():
                  "pivots_equal_to_fast": bool(torch.equal(piv_dev, piv_fast)),
                  "max_abs_dK_vs_fast_Ha": float((K_dev - K_fast).abs().max()),
                  "dEx_per_atom_vs_fast_Ha": abs(r0["Ex"] - res[-1]["Ex"]) / sysd["xyz"].shape[0]}
+
+    # ---- occ-RI output (K C without K) on the same workload, beside the exchange
+    r_occ = step(occ=True)
+    occ_ri = {"exchange_s": r_occ["exchange"], "exchange_occ_s": r_occ["exchange_occ"],
+              "s_iter_occ": (r_occ["plan"] + r_occ["select"] + r_occ["fit"] + r_occ["coulomb"]) / SCF_CHARGE +
+              r_occ["exchange_occ"],
+              "max_abs_dKC_vs_KC_Ha": float((KC_dev - K_dev @ C_dev).abs().max()),
+              "dEx_per_atom_Ha": abs(r_occ["Ex_occ"] - r_occ["Ex"]) / sysd["xyz"].shape[0]}
+
+    # ---- threshold-driven plan: grids from eps_K (Section III, Eq. 6), N_ip from eps_ISDF
+    thr = None
+    if args.workload == "2x2x2":
+        sys_t = dict(sysd)
+        sys_t["grids"] = B.isdf_grids_for_threshold(sysd, EPS_K).astype(np.int64)
+        cap = int(1.25 * nip)
+        rt = step(sysx=sys_t, nipx=cap, tol=EPS_ISDF)
+        thr = {"eps_K": EPS_K, "eps_isdf": EPS_ISDF, "grids": sys_t["grids"].tolist(), "nip_cap": cap,
+               "nip_level": rt["nip_level"], "nip": int(sum(rt["nip_level"])),
+               "s_iter": (rt["plan"] + rt["select"] + rt["fit"] + rt["coulomb"]) / SCF_CHARGE + rt["exchange"],
+               "stages_s": {k: rt[k] for k in ("plan", "select", "fit", "coulomb", "exchange")},
+               "Ex_per_atom": rt["Ex"] / sysd["xyz"].shape[0]}
 
     # ---- learned point proposal (trained here; reported beside the main number)
     learned = None
@@ -555,22 +631,17 @@ def main():
             torch.distributed.destroy_process_group()
         return 0
     cpu = None
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.workload == "2x2x2":
         cpu = cpu_baseline_sample()
-        cpu = {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")}
     line = {
         "metric": METRIC, "value": value, "unit": "s/iter", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "bf16-sliced(f64-accurate)",
         "data": "synthetic",
-        "config": {"workload": workload, "precision": "plain FP64" if args.precision == 0 else
-                   "tensor-core sliced BF16 (FP64-accurate) contractions, FP64 pivot decisions/Cholesky/E_x",
-                   "prefilter": args.prefilter, "select_block": args.select_block,
-                   "l2": "inputs larger than L2 (basis values 6.4 GB, interpolation vectors > 15 GB)",
-                   "parallelism": f"replicas x{world}"},
+        "config": gpu_config(args, workload, world),
         "stages_s": {k: statistics.mean(r[k] for r in res) for k in ("plan", "select", "fit", "coulomb", "exchange")},
         "Ex_per_atom": res[-1]["Ex"] / sysd["xyz"].shape[0],
-        "plain_fp64_gpu": plain, "learned": learned, "batch": batch,
+        "plain_fp64_gpu": plain, "occ_ri": occ_ri, "threshold_plan": thr, "learned": learned, "batch": batch,
         "speedup_vs_plain_fp64_gpu": (plain["s_iter"] / s_iter) if plain else None,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk, "wall_s_timed": wall, "kernels": kern,

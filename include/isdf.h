@@ -194,6 +194,21 @@ isdf_status isdf_coulomb(isdf_plan_t plan, double* V_out);
  *   Ex_out nullable host double                                            */
 isdf_status isdf_exchange(isdf_plan_t plan, const double* C, int n, double* K_out, double* Ex_out);
 
+/* occ-RI output of the exchange build (Section III.A: only the occupied
+ * block of the exchange matrix is needed; Section II.A: K_ip with real
+ * orbitals):
+ *   KC_{mu i} = sum_nu K_{mu nu} C_{nu i} = sum_j (mu j | j i),
+ * with (mu lam|sig nu) from Eq. 8 as in isdf_exchange, and E_x =
+ * -sum_{mu i} C_{mu i} KC_{mu i} = -Tr(D K).  K itself is never formed: with
+ * Y_A = X^A^T C and W as in isdf_exchange, KC = [X^L X^N] (W [Y_L; Y_N]),
+ * contracted over the nonzero (function level x pivot level) blocks of X^L
+ * and X^N only (the block structure of (mu|xi) in the paper's figure).
+ *   C       N x n row-major FP64 occupied-orbital coefficients (host/device)
+ *   KC_out  nullable N x n row-major FP64 (host or device)
+ *   Ex_out  nullable host double
+ * Same call order and errors as isdf_exchange; may be repeated. */
+isdf_status isdf_exchange_occ(isdf_plan_t plan, const double* C, int n, double* KC_out, double* Ex_out);
+
 /* Copy plan data out (host or device destination) for tests and tools.
  * isdf_get_size returns the number of elements (0 if not available yet). */
 enum {
@@ -329,6 +344,24 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
 isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K,
                                   int64_t lda, int64_t ldb, int64_t ldc, double alpha, int slices, void* stream);
 int64_t isdf_gemm_f64_noalloc_capacity(void);
+
+/* Threshold-driven grids (Section III, Eq. 6; the paper's eps_K of its
+ * threshold table).  A Gaussian exp(-a r^2) has the Fourier transform
+ * exp(-G^2 / 4a), which falls to eps_K at G_max = sqrt(-4 a ln eps_K); a
+ * grid of n points over an edge L carries wave numbers up to pi n / L.  For
+ * every level l this writes, per axis, the smallest even 2^i 3^j count with
+ * pi n / L >= G_max, a being the largest exponent among the functions of
+ * level l (or, if it has none, among the coarser ones); then, from the
+ * coarsest level up, a finer level's count is raised to the next admissible
+ * size where it does not exceed the coarser level's (isdf_plan needs the
+ * counts to fall from level to level).  Reads sys->lattice (diagonal),
+ * nlevel, nshell, shell_exp and level_min_exp only (sys->grid may be NULL);
+ * grid_out: HOST int array of nlevel x 3.  0 < eps_K < 1, else
+ * ISDF_ERR_ARG; more than 4096 points per axis gives ISDF_ERR_ARG.  Host
+ * computation only.  The number of interpolation points then follows the
+ * paper's eps_ISDF through isdf_select_points' tol (stop once the largest
+ * residual falls below tol * d_0). */
+isdf_status isdf_grids_for_threshold(const isdf_system* sys, double eps_K, int* grid_out);
 
 /* Batched 3-D real-to-half-complex DFT -- the transform behind the Coulomb
  * integrals of Section II, Eq. 1 (the half spectra that isdf_coulomb builds

@@ -167,6 +167,57 @@ def basis_direct(system, funcs, idx, lev):
     return out
 
 
+def fft_sizes(limit=4096):
+    """Even grid sizes of the form 2^a 3^b (a >= 1), ascending."""
+    out = []
+    for a in range(1, 13):
+        for b in range(0, 8):
+            n = (2 ** a) * (3 ** b)
+            if n <= limit:
+                out.append(n)
+    return sorted(out)
+
+
+def grid_for_threshold(length, alpha, eps_K):
+    """Points per axis that resolve exp(-alpha r^2) to eps_K in Fourier space
+    (Section III, Eq. 6): the function's Fourier transform exp(-G^2/4 alpha)
+    falls to eps_K at G_max = sqrt(-4 alpha ln eps_K), and a grid of n points
+    over ``length`` carries wave numbers up to pi n / length (Nyquist).
+    Smallest even 2^a 3^b size with pi n / length >= G_max."""
+    gmax = math.sqrt(-4.0 * alpha * math.log(eps_K))
+    for n in fft_sizes():
+        if math.pi * n / length >= gmax:
+            return n
+    raise ValueError("threshold needs more than 4096 points per axis")
+
+
+def grids_for_threshold(system, eps_K):
+    """Grid of every level from eps_K (Section III, Eq. 6): level l must
+    resolve its sharpest function -- the largest exponent among the functions
+    of level l (reading R1), or, when it has none, among the coarser ones.
+    Per axis the counts must then fall strictly from level to level (a
+    coarser level's mode set inside every finer one): going from the coarsest
+    level up, a level's count is raised to the next size above the coarser
+    level's where needed.  Returns an int array (nlevel, 3)."""
+    edges = np.asarray(system["level_min_exp"], dtype=np.float64)
+    nlev = edges.size + 1
+    exps = np.asarray(system["shell_exp"], dtype=np.float64)
+    lev_of = np.array([int(np.sum(e < edges)) for e in exps])
+    sizes = fft_sizes()
+    out = np.zeros((nlev, 3), dtype=np.int64)
+    for lev in range(nlev):
+        own = exps[lev_of == lev]
+        coarser = exps[lev_of > lev]
+        alpha = own.max() if own.size else (coarser.max() if coarser.size else None)
+        for ax in range(3):
+            out[lev, ax] = 2 if alpha is None else grid_for_threshold(system["edges"][ax], alpha, eps_K)
+    for lev in range(nlev - 2, -1, -1):
+        for ax in range(3):
+            if out[lev, ax] <= out[lev + 1, ax]:
+                out[lev, ax] = next(n for n in sizes if n > out[lev + 1, ax])
+    return out
+
+
 def level_weight(system, lev):
     """w_l = dV_l = Omega / N_g,l (reading R2)."""
     n = system["grids"][lev]

@@ -499,11 +499,44 @@ isdf_status isdf_exchange(isdf_plan_t h, const double* C, int n, double* K_out, 
     }
   }
   double ex = 0.0;
-  if (!st) st = exchange_run(p, dC, n, dK, &ex);
+  if (!st) st = exchange_run(p, dC, n, dK, nullptr, &ex);
   if (!st && K_out && own_k) st = from_device(p, K_out, dK, nk, true);
   if (!st && Ex_out) *Ex_out = ex;
   dfree(stageC);
   if (own_k) dfree(dK);
+  return st;
+}
+
+isdf_status isdf_exchange_occ(isdf_plan_t h, const double* C, int n, double* KC_out, double* Ex_out) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (p->state < 3) return fail(p, ISDF_ERR_STATE, "isdf_exchange_occ needs isdf_coulomb first");
+  if (!C || n < 1) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_exchange_occ");
+  const size_t nc = size_t(p->nfun) * n;
+  const double* dC = C;
+  double* stageC = nullptr;
+  double* dKC = nullptr;
+  bool own = false;
+  isdf_status st = ISDF_OK;
+  if (!is_device_ptr(C)) {
+    if ((st = dalloc_t(p, &stageC, nc, "C staging"))) return st;
+    st = cuda_check(p, cudaMemcpyAsync(stageC, C, nc * sizeof(double), cudaMemcpyHostToDevice, p->stream), "copy C");
+    dC = stageC;
+  }
+  if (!st) {
+    if (KC_out && is_device_ptr(KC_out)) {
+      dKC = KC_out;
+    } else {
+      own = true;
+      st = dalloc_t(p, &dKC, nc, "K C");
+    }
+  }
+  double ex = 0.0;
+  if (!st) st = exchange_run(p, dC, n, nullptr, dKC, &ex);
+  if (!st && KC_out && own) st = from_device(p, KC_out, dKC, nc, true);
+  if (!st && Ex_out) *Ex_out = ex;
+  dfree(stageC);
+  if (own) dfree(dKC);
   return st;
 }
 
@@ -791,6 +824,77 @@ isdf_status isdf_gemm_f64_noalloc(const double* A, const double* B, double* C, i
 }
 
 int64_t isdf_gemm_f64_noalloc_capacity(void) { return int64_t(gemm_noalloc_capacity()); }
+
+isdf_status isdf_grids_for_threshold(const isdf_system* sys, double eps_K, int* grid_out) {
+  // Section III, Eq. 6: a Gaussian exp(-a r^2) has the Fourier transform
+  // exp(-G^2 / 4a), which falls to eps_K at G_max = sqrt(-4 a ln eps_K); a
+  // grid of n points over an edge L carries wave numbers up to pi n / L.
+  if (!sys || !grid_out || !(eps_K > 0.0 && eps_K < 1.0) || sys->nlevel < 1 || sys->nlevel > ISDF_MAX_LEVELS ||
+      sys->nshell < 1 || !sys->shell_exp || (sys->nlevel > 1 && !sys->level_min_exp)) {
+    g_plan_error = "invalid arguments to isdf_grids_for_threshold (0 < eps_K < 1, 1 <= nlevel <= 4, shells)";
+    return ISDF_ERR_ARG;
+  }
+  double L[3];
+  for (int a = 0; a < 3; ++a) {
+    L[a] = sys->lattice[4 * a];
+    if (!(L[a] > 0.0) || !std::isfinite(L[a])) {
+      g_plan_error = "isdf_grids_for_threshold: the lattice must be diagonal with positive edges";
+      return ISDF_ERR_ARG;
+    }
+  }
+  for (int l = 0; l + 1 < sys->nlevel; ++l)
+    if (!(sys->level_min_exp[l] > 0.0) || (l > 0 && !(sys->level_min_exp[l] < sys->level_min_exp[l - 1]))) {
+      g_plan_error = "isdf_grids_for_threshold: level edges must be positive and decreasing";
+      return ISDF_ERR_ARG;
+    }
+  // admissible sizes: even 2^a 3^b, ascending
+  std::vector<int> sizes;
+  for (long long p2 = 2; p2 <= 4096; p2 *= 2)
+    for (long long n = p2; n <= 4096; n *= 3) sizes.push_back(int(n));
+  std::sort(sizes.begin(), sizes.end());
+  // sharpest exponent of each level (its own functions, else the coarser ones)
+  double own[ISDF_MAX_LEVELS] = {0, 0, 0, 0};
+  for (int i = 0; i < sys->nshell; ++i) {
+    const double e = sys->shell_exp[i];
+    if (!(e > 0.0) || !std::isfinite(e)) {
+      g_plan_error = "isdf_grids_for_threshold: shell exponents must be > 0";
+      return ISDF_ERR_ARG;
+    }
+    int lev = 0;
+    for (int l = 0; l + 1 < sys->nlevel; ++l) lev += (e < sys->level_min_exp[l]) ? 1 : 0;
+    own[lev] = std::max(own[lev], e);
+  }
+  int out[ISDF_MAX_LEVELS][3];
+  for (int l = 0; l < sys->nlevel; ++l) {
+    double alpha = own[l];
+    for (int m = l + 1; m < sys->nlevel && alpha == 0.0; ++m) alpha = std::max(alpha, own[m]);
+    for (int a = 0; a < 3; ++a) {
+      if (alpha == 0.0) {
+        out[l][a] = 2;
+        continue;
+      }
+      const double gmax = std::sqrt(-4.0 * alpha * std::log(eps_K));
+      int n = 0;
+      for (int c : sizes)
+        if (M_PI * double(c) / L[a] >= gmax) {
+          n = c;
+          break;
+        }
+      if (!n) {
+        g_plan_error = "isdf_grids_for_threshold: the threshold needs more than 4096 points per axis";
+        return ISDF_ERR_ARG;
+      }
+      out[l][a] = n;
+    }
+  }
+  // strictly decreasing from level to level: raise a finer level where needed
+  for (int l = sys->nlevel - 2; l >= 0; --l)
+    for (int a = 0; a < 3; ++a)
+      if (out[l][a] <= out[l + 1][a]) out[l][a] = *std::upper_bound(sizes.begin(), sizes.end(), out[l + 1][a]);
+  for (int l = 0; l < sys->nlevel; ++l)
+    for (int a = 0; a < 3; ++a) grid_out[3 * l + a] = out[l][a];
+  return ISDF_OK;
+}
 
 isdf_status isdf_rfft3(const double* f, int nx, int ny, int nz, int64_t batch, double* S, void* stream) {
   if (!f || !S || batch < 1 || !rfft3_df_supported(nx, ny, nz)) {

@@ -140,7 +140,8 @@ isdf_status fit_run(Plan* p);                                        // fit.cu
 isdf_status fit_residual_run(Plan* p);  // fit.cu: residual statistics on request (precision 1)
 isdf_status fit_xi_run(Plan* p, int level);  // fit.cu: Xi^T of a level on request (precision 1)
 isdf_status coulomb_run(Plan* p);                                    // coulomb.cu
-isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* Ex);  // exchange.cu
+// dK (N x N) and dKC (N x n, K C) are nullable; exchange.cu
+isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* dKC, double* Ex);
 isdf_status gather_pivot_factors(Plan* p);                           // basis.cu
 
 // FP64 SIMT GEMM (dgemm.cu):

@@ -50,6 +50,8 @@ EXPORTED = [
     "isdf_gemm_f64_noalloc",
     "isdf_gemm_f64_noalloc_capacity",
     "isdf_rfft3",
+    "isdf_grids_for_threshold",
+    "isdf_exchange_occ",
 ]
 
 
@@ -150,6 +152,10 @@ def load_library(build_if_missing: bool = True):
     lib.isdf_gemm_f64_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64,
                                           c_int64, c_double, c_int, c_void_p]
     lib.isdf_gemm_f64_noalloc.restype = c_int
+    lib.isdf_exchange_occ.argtypes = [c_void_p, c_void_p, c_int, c_void_p, POINTER(c_double)]
+    lib.isdf_exchange_occ.restype = c_int
+    lib.isdf_grids_for_threshold.argtypes = [POINTER(isdf_system), c_double, POINTER(c_int)]
+    lib.isdf_grids_for_threshold.restype = c_int
     lib.isdf_gemm_f64_noalloc_capacity.argtypes = []
     lib.isdf_gemm_f64_noalloc_capacity.restype = c_int64
     _lib = lib
@@ -220,19 +226,18 @@ class Plan:
             raise IsdfError(st, self._lib.isdf_last_error(self.handle).decode())
 
 
-def isdf_plan(system: dict, options=None, stream=None) -> Plan:
-    lib = load_library()
-    if options is None:
-        options = default_options()
-    elif isinstance(options, dict):
-        options = default_options(**options)
+def _system_struct(system: dict, need_grid=True):
+    """isdf_system for a system dict; returns (struct, arrays kept alive)."""
     edges = np.asarray(system["edges"], dtype=np.float64)
     xyz = np.ascontiguousarray(system["xyz"], dtype=np.float64)
     sa = np.ascontiguousarray(system["shell_atom"], dtype=np.int32)
     sl = np.ascontiguousarray(system["shell_l"], dtype=np.int32)
     se = np.ascontiguousarray(system["shell_exp"], dtype=np.float64)
-    grid = np.ascontiguousarray(system["grids"], dtype=np.int32).reshape(-1, 3)
     lme = np.ascontiguousarray(system["level_min_exp"], dtype=np.float64)
+    if need_grid:
+        grid = np.ascontiguousarray(system["grids"], dtype=np.int32).reshape(-1, 3)
+    else:
+        grid = np.zeros((lme.size + 1, 3), dtype=np.int32)
     s = isdf_system()
     for i in range(9):
         s.lattice[i] = 0.0
@@ -248,12 +253,34 @@ def isdf_plan(system: dict, options=None, stream=None) -> Plan:
     s.grid = grid.ctypes.data_as(POINTER(c_int))
     s.level_min_exp = lme.ctypes.data_as(POINTER(c_double)) if lme.size else None
     s.image_tol = float(system["image_tol"])
+    return s, (xyz, sa, sl, se, grid, lme)
+
+
+def isdf_plan(system: dict, options=None, stream=None) -> Plan:
+    lib = load_library()
+    if options is None:
+        options = default_options()
+    elif isinstance(options, dict):
+        options = default_options(**options)
+    s, keep = _system_struct(system)
     h = c_void_p()
     st = lib.isdf_plan(ctypes.byref(s), ctypes.byref(options), c_void_p(_default_stream() if stream is None else stream),
                        ctypes.byref(h))
     if st != ISDF_OK:
         raise IsdfError(st, lib.isdf_last_error(None).decode())
     return Plan(h.value, lib, system)
+
+
+def isdf_grids_for_threshold(system: dict, eps_K: float):
+    """Grid points per axis of every level from the accuracy threshold eps_K
+    (host computation in the library).  Returns an int array (nlevel, 3)."""
+    lib = load_library()
+    s, keep = _system_struct(system, need_grid=False)
+    out = np.zeros((s.nlevel, 3), dtype=np.int32)
+    st = lib.isdf_grids_for_threshold(ctypes.byref(s), c_double(eps_K), out.ctypes.data_as(POINTER(c_int)))
+    if st != ISDF_OK:
+        raise IsdfError(st, lib.isdf_last_error(None).decode())
+    return out
 
 
 def isdf_select_points(plan: Plan, nip: int, tol: float = 0.0, cand=None, piv_out=None, dval_out=None):
@@ -294,6 +321,18 @@ def isdf_exchange(plan: Plan, C, K_out=None):
     plan._check(plan._lib.isdf_exchange(plan.handle, _addr(C, np.float64), int(C.shape[1]), _addr(K, np.float64),
                                         ctypes.byref(ex)))
     return K, ex.value
+
+
+def isdf_exchange_occ(plan: Plan, C, KC_out=None):
+    """occ-RI output K C (N x n) and E_x, without forming K."""
+    if isinstance(C, np.ndarray):
+        C = np.ascontiguousarray(C, dtype=np.float64)
+    N, n = int(C.shape[0]), int(C.shape[1])
+    KC = np.zeros((N, n)) if KC_out is None else KC_out
+    ex = c_double(0.0)
+    plan._check(plan._lib.isdf_exchange_occ(plan.handle, _addr(C, np.float64), n, _addr(KC, np.float64),
+                                            ctypes.byref(ex)))
+    return KC, ex.value
 
 
 def isdf_get(plan: Plan, what: int, dst=None):

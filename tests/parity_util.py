@@ -20,6 +20,7 @@ def gpu_run(sysd, C, nip, tol=0.0, piv=None, cand=None, opts=None, want_xi=True)
         V = np.zeros((npiv, npiv))
         B.isdf_coulomb(plan, V)
         K, Ex = B.isdf_exchange(plan, C)
+        KC, Ex_occ = B.isdf_exchange_occ(plan, C)
         N = S.nbasis(sysd)
         out = {
             "pivots": np.asarray(piv),
@@ -29,6 +30,9 @@ def gpu_run(sysd, C, nip, tol=0.0, piv=None, cand=None, opts=None, want_xi=True)
             "V": V,
             "K": K,
             "Ex": Ex,
+            "KC": KC,
+            "Ex_occ": Ex_occ,
+            "C": np.asarray(C),
             "XL": B.isdf_get(plan, B.GET_XL).reshape(N, npiv),
             "XN": B.isdf_get(plan, B.GET_XN).reshape(N, npiv),
         }
@@ -120,4 +124,10 @@ def assert_parity(g, o, natom, k_tol=1e-8, v_rel=1e-6, xi_rel=1e-6, tc=False):
     dK = np.max(np.abs(g["K"] - o["K"]))
     assert dK <= k_tol, dK
     assert abs(g["Ex"] - o["Ex"]) / natom <= k_tol
+    if "KC" in g:
+        # occ-RI output K C: |d(K C)| <= max|dK| * max_i sum_nu |C_nu i|
+        C = g["C"]
+        dKC = np.max(np.abs(g["KC"] - o["K"] @ C))
+        assert dKC <= k_tol * np.max(np.sum(np.abs(C), axis=0)), dKC
+        assert abs(g["Ex_occ"] - o["Ex"]) / natom <= k_tol
     return dK

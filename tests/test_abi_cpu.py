@@ -125,3 +125,29 @@ def test_gemm_digit_counts(slices, accepted):
         assert b"device pointers" in msg
     else:
         assert b"invalid arguments" in msg
+
+
+@pytest.mark.parametrize("reps,eps", [((1, 1, 1), 1e-8), ((2, 2, 1), 1e-8), ((1, 2, 3), 1e-3), ((2, 2, 2), 0.5),
+                                      ((1, 1, 1), 1e-14)])
+def test_grids_for_threshold_match_the_oracle(reps, eps):
+    """Host logic of the library: the threshold-driven grid of every level
+    (Section III, Eq. 6) equals the oracle's, bit for bit."""
+    from oracle import isdf as O
+    from paper_2404_09373_gb300 import isdf as B
+    from paper_2404_09373_gb300 import systems as S
+
+    sysd = S.make_system(reps, 0.0, None, ((8, 8, 8), (4, 4, 4), (2, 2, 2)), S.LEVEL_EDGES_3)
+    np.testing.assert_array_equal(B.isdf_grids_for_threshold(sysd, eps), O.grids_for_threshold(sysd, eps))
+    two = S.make_system(reps, 0.0, None, ((8, 8, 8), (4, 4, 4)), (0.5,), s_exps=(0.3, 2.0), p_exps=(0.7,))
+    np.testing.assert_array_equal(B.isdf_grids_for_threshold(two, eps), O.grids_for_threshold(two, eps))
+
+
+def test_grids_for_threshold_rejects_bad_thresholds():
+    from paper_2404_09373_gb300 import isdf as B
+    from paper_2404_09373_gb300 import systems as S
+
+    sysd = S.make_system((1, 1, 1), 0.0, None, ((8, 8, 8),), ())
+    for eps in (0.0, 1.0, -1e-3, float("nan")):
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_grids_for_threshold(sysd, eps)
+        assert e.value.status == B.ISDF_ERR_ARG

@@ -309,3 +309,21 @@ def test_workload2_full_size_sampled_and_properties(workload2):
         assert Ex < 0.0
     finally:
         plan.close()
+
+
+def test_threshold_driven_grids_and_isdf_tolerance():
+    """The paper's thresholds instead of fixed sizes (Section III, Eq. 6 and
+    the eps_ISDF stop of the selection): every level's grid from eps_K, then
+    pivots until the largest residual falls below eps_ISDF d_0.  The whole
+    path against the oracle run on the same derived grids and tolerance."""
+    rng = np.random.default_rng(21)
+    sysd = S.make_system((1, 1, 1), 0.05, rng, ((8, 8, 8), (4, 4, 4), (2, 2, 2)), S.LEVEL_EDGES_3)
+    sysd["grids"] = B.isdf_grids_for_threshold(sysd, 1e-2).astype(np.int64)
+    np.testing.assert_array_equal(sysd["grids"], O.grids_for_threshold(sysd, 1e-2))
+    C = S.make_orbitals(sysd, 16, rng)
+    cap = 3000
+    for prec in (0, 1):
+        o = oracle.run(sysd, C, cap, tol=1e-4)
+        g = gpu_run(sysd, C, cap, tol=1e-4, opts={"precision": prec, "prefilter": 1, "select_block": 64})
+        assert 0 < o["pivots"].size < cap
+        assert_parity(g, o, natom=8, k_tol=1e-8 if prec == 0 else 1e-6, tc=prec == 1)

@@ -519,3 +519,43 @@ def test_planted_mistakes_in_adam_are_caught():
 
     for wrong in (no_bias_correction, off_by_one, betas_swapped):
         assert not _adam_pin_ok(wrong)
+
+
+# --------------------------------------------------------------------------- threshold-driven grids (Eq. 6)
+
+
+@pytest.mark.parametrize("length,alpha,eps", [(6.74, 6.4, 1e-8), (13.48, 0.6, 1e-8), (13.48, 0.15, 1e-3),
+                                              (5.0, 2.4, 1e-2), (20.0, 0.1, 1e-12)])
+def test_grid_for_threshold_is_the_smallest_resolving_size(length, alpha, eps):
+    """By definition (Section III, Eq. 6): at the grid's largest wave number
+    pi n / L the Gaussian's Fourier transform exp(-G^2 / 4 alpha) is at most
+    eps_K, and at the next smaller admissible size it is not."""
+    n = O.grid_for_threshold(length, alpha, eps)
+    sizes = O.fft_sizes()
+    assert n in sizes and n % 2 == 0
+    ft = lambda m: math.exp(-((math.pi * m / length) ** 2) / (4.0 * alpha))  # noqa: E731
+    assert ft(n) <= eps
+    smaller = [m for m in sizes if m < n]
+    if smaller:
+        assert ft(smaller[-1]) > eps
+
+
+def test_grid_for_threshold_worked_case():
+    """a = 6.74 bohr, alpha = 6.4, eps_K = 1e-8: G_max = sqrt(4 * 6.4 * ln 1e8)
+    = 21.72 bohr^-1, so n >= 6.74 * 21.72 / pi = 46.6 -> 48 (= 2^4 3)."""
+    assert O.grid_for_threshold(6.74, 6.4, 1e-8) == 48
+    assert O.fft_sizes()[:10] == [2, 4, 6, 8, 12, 16, 18, 24, 32, 36]
+
+
+def test_level_grids_for_threshold_follow_the_sharpest_function_and_nest():
+    sysd = S.make_system((2, 2, 1), 0.0, None, ((8, 8, 8), (4, 4, 4), (2, 2, 2)), S.LEVEL_EDGES_3)
+    g = O.grids_for_threshold(sysd, 1e-8)
+    E = sysd["edges"]
+    for ax in range(3):
+        assert g[0, ax] == O.grid_for_threshold(E[ax], 6.4, 1e-8)
+        assert g[1, ax] == O.grid_for_threshold(E[ax], 0.6, 1e-8)
+        assert g[2, ax] == O.grid_for_threshold(E[ax], 0.15, 1e-8)
+        assert g[0, ax] > g[1, ax] > g[2, ax]
+    # a loose threshold that gives two levels the same size: the finer one is raised
+    g = O.grids_for_threshold(sysd, 0.5)
+    assert np.all(g[:-1] > g[1:])
