@@ -150,6 +150,18 @@ void isdf_options_default(isdf_options* opt);
  * On success *out receives the plan; on failure *out is NULL. */
 isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* stream, isdf_plan_t* out);
 
+/* Plans for a batch of independent cells (cells of uneven size, each with
+ * its own grids): isdf_plan for every systems[i] (plan i on streams[i]; a
+ * NULL `streams` puts every plan on the legacy default stream), except that
+ * the basis values of all cells and all levels are evaluated by one launch
+ * of each basis kernel (1-D image-sum factors, then their outer products) on
+ * streams[0], after which the call returns.  out: ncells plan handles.  On
+ * any failure every plan already made is destroyed, out[] is all NULL and
+ * isdf_last_error(NULL) names the cell.  The plans are independent
+ * afterwards (select, fit, Coulomb, exchange per plan, on their streams). */
+isdf_status isdf_plan_batch(const isdf_system* systems, int ncells, const isdf_options* opt, void* const* streams,
+                            isdf_plan_t* out);
+
 /* Select up to nip interpolation points (Section II.A, Eq. 2): greedy
  * pivoted Cholesky on the block-diagonal matrix (+)_l w_l M_l, with
  * M_l = A_L o A_L + 2 A_L o A_N, A_X(g,g') = sum_{mu in X} phi_mu(g)phi_mu(g'),
@@ -208,6 +220,55 @@ isdf_status isdf_exchange(isdf_plan_t plan, const double* C, int n, double* K_ou
  *   Ex_out  nullable host double
  * Same call order and errors as isdf_exchange; may be repeated. */
 isdf_status isdf_exchange_occ(isdf_plan_t plan, const double* C, int n, double* KC_out, double* Ex_out);
+
+/* Captured exchange builds of many cells (the batched workload: the exchange
+ * is the per-SCF-iteration part, with shapes fixed once the ISDF is done).
+ * isdf_exchange_graph runs one exchange build per plan (each after
+ * isdf_coulomb; n_occ[i] orbitals), then captures them on `stream` into one
+ * CUDA graph in which every plan's build is an independent branch: isdf_exchange
+ * (occ = 0, K outputs N x N) or isdf_exchange_occ (occ = 1, K C outputs N x n).
+ * The graph owns device buffers for every plan's C, output and E_x.
+ * isdf_exchange_graph_run copies C[i] (host or device, N_i x n_i row-major)
+ * into them, launches the graph once, copies the outputs to out[i] (host or
+ * device, nullable entries or NULL array) and E_x to Ex_out[i] (host,
+ * nullable), and returns when `stream` is idle.  Replays may repeat with new
+ * orbitals.  The plans must not be used elsewhere while a replay runs and must
+ * outlive the graph; destroy the graph with isdf_exchange_graph_destroy.  A
+ * tensor-core pipeline wait that expired during a replay returns
+ * ISDF_ERR_TIMEOUT.  (The selection, fit and Coulomb stages are host-driven
+ * loops with data-dependent shapes and are not captured.) */
+typedef struct isdf_exchange_graph_s* isdf_exchange_graph_t;
+isdf_status isdf_exchange_graph(isdf_plan_t* plans, int nplans, const int* n_occ, int occ, void* stream,
+                                isdf_exchange_graph_t* out);
+isdf_status isdf_exchange_graph_run(isdf_exchange_graph_t graph, const double* const* C, double* const* out,
+                                    double* Ex_out);
+void isdf_exchange_graph_destroy(isdf_exchange_graph_t graph);
+
+/* Split-K autotuner of the tensor-core products (the launch shape the
+ * library picks by measurement; not in the paper): the first product of a
+ * shape outside any graph capture times every admissible split-K factor on
+ * its own operands (CUDA events) and keeps the fastest for the process
+ * (setting ISDF_NO_AUTOTUNE in the environment keeps the built-in
+ * heuristic).  This returns the table so far as JSON text, one object per
+ * shape {M, N, k_tiles, digits, sym, splits, ms}; valid until the next call
+ * on this thread. */
+const char* isdf_autotune_table(void);
+
+/* Checkpoint and resume.  The ISDF runs once, before the SCF iterations
+ * (Section II.B: the fit is charged once, the exchange every iteration); the
+ * exchange build needs only the pivots, X^L, X^N and V.
+ * isdf_save writes them to `path` (after isdf_coulomb, else ISDF_ERR_STATE):
+ * "ISDFCKP1", int32 nfun, nlevel, nip, int32 grid[nlevel][3], double cell
+ * edges[3], int64 pivot codes [nip] (level order), double X^L [nfun][nip],
+ * X^N [nfun][nip], V [nip][nip], native byte order.
+ * isdf_load reads such a file into a plan made for the same system (same
+ * basis size, levels, grids and cell, else ISDF_ERR_ARG and the plan is
+ * unchanged); afterwards isdf_exchange and isdf_exchange_occ run as after
+ * isdf_coulomb, and the interpolation vectors are not available.  A missing,
+ * truncated or malformed file gives ISDF_ERR_ARG.  `path` is a host string;
+ * both calls return after the data are written / on the device. */
+isdf_status isdf_save(isdf_plan_t plan, const char* path);
+isdf_status isdf_load(isdf_plan_t plan, const char* path);
 
 /* Copy plan data out (host or device destination) for tests and tools.
  * isdf_get_size returns the number of elements (0 if not available yet). */

@@ -1,11 +1,19 @@
 """Batched execution of many independent cells (host orchestration).
 
-Each cell runs the whole path (plan -> select -> fit -> Coulomb -> exchange)
-on its own CUDA stream; a pool of host threads keeps ``n_streams`` cells in
-flight so that small cells, whose kernels cannot fill the GPU, overlap with
-each other and with the large ones.  A device-memory budget bounds how many
-cells are in flight at once.  Results are the same as running the cells one
-by one: every cell has its own plan and stream, and no kernel is shared.
+1. ``isdf_plan_batch``: one plan per cell; the basis values of every cell
+   and every level are evaluated by one launch of each basis kernel.
+2. ISDF per cell (selection, fit, Coulomb matrix), every cell on its own
+   CUDA stream: a pool of ``n_streams`` host threads keeps cells in flight so that
+   small cells, whose kernels cannot fill the GPU, overlap with each other
+   and with the large ones; a device-memory budget bounds how many are in
+   flight at once.
+3. The exchange builds of all cells -- the per-SCF-iteration part -- are
+   captured once into one CUDA graph (``isdf_exchange_graph``, one branch per
+   cell) and replayed with each iteration's orbitals.
+
+Every cell keeps its own plan, so results are those of running the cells one
+by one up to the rounding of the exchange products (the captured build uses
+the same kernels and shapes).
 """
 from __future__ import annotations
 
@@ -19,16 +27,16 @@ from . import isdf as B
 
 
 def peak_bytes(system, nip):
-    """Rough device-memory peak of one cell (basis values, selection factor,
-    fit buffers and digit planes, spectra), used only for admission."""
+    """Rough device-memory peak of one cell's ISDF (selection factor and digit
+    planes, fit buffers, spectra), used only for admission."""
     grids = np.asarray(system["grids"]).reshape(-1, 3)
     ng = [int(np.prod(g)) for g in grids]
-    nfun = int(sum(1 if l == 0 else 3 for l in system["shell_l"]))
     k = max(1, nip // len(ng))
-    return int(8 * nfun * sum(ng) + 8 * 2 * k * ng[0] + 8 * 2 * nip * ng[0] + 2 * 10 * k * ng[0] + 2 ** 30)
+    return int(8 * 2 * k * ng[0] + 8 * 2 * nip * ng[0] + 2 * 10 * k * ng[0] + 2 ** 30)
 
 
 def run_cell(system, C, nip, opts, stream):
+    """One cell alone: plan, ISDF, exchange (the reference for the batch)."""
     t0 = time.perf_counter()
     plan = B.isdf_plan(system, opts, stream=stream)
     try:
@@ -43,39 +51,64 @@ def run_cell(system, C, nip, opts, stream):
     return {"pivots": piv, "K": K, "Ex": ex, "t_isdf_s": t1 - t0, "t_exchange_s": t2 - t1}
 
 
-def run_batch(cells, opts=None, n_streams=4, mem_budget=200 * 2 ** 30):
-    """Run every (system, C, nip) cell; returns (results in input order, wall s)."""
+def run_batch(cells, opts=None, n_streams=4, mem_budget=160 * 2 ** 30, iterations=1):
+    """Run every (system, C, nip) cell.  Returns (results in input order,
+    timings): per cell pivots, K, E_x; timings of the batch plan, the ISDF
+    stages, the graph capture and each exchange replay (``iterations`` SCF
+    iterations with the cells' orbitals)."""
     import torch
 
     opts = opts or {"precision": 1, "prefilter": 1}
     dev = torch.cuda.current_device()
-    streams = [torch.cuda.Stream(device=dev) for _ in range(n_streams)]
-    free = list(range(n_streams))
+    streams = [torch.cuda.Stream(device=dev) for _ in cells]  # one per cell: cells in flight never share one
+    t0 = time.perf_counter()
+    plans = B.isdf_plan_batch([c[0] for c in cells], opts, streams=[st.cuda_stream for st in streams])
+    t_plan = time.perf_counter() - t0
     lock = threading.Condition()
     state = {"bytes": 0}
+    piv = [None] * len(cells)
 
-    def work(i):
+    def isdf(i):
         sysd, C, nip = cells[i]
         need = min(peak_bytes(sysd, nip), mem_budget)
         with lock:
             while state["bytes"] + need > mem_budget and state["bytes"] > 0:
                 lock.wait()
             state["bytes"] += need
-            sid = free.pop()
         try:
             torch.cuda.set_device(dev)
-            return run_cell(sysd, C, nip, opts, streams[sid].cuda_stream)
+            p, _ = B.isdf_select_points(plans[i], nip)
+            B.isdf_fit(plans[i], p)
+            B.isdf_coulomb(plans[i])
+            piv[i] = p
         finally:
             with lock:
                 state["bytes"] -= need
-                free.append(sid)
                 lock.notify_all()
 
-    # largest cells first, so the small ones fill the gaps at the end
-    order = sorted(range(len(cells)), key=lambda i: -peak_bytes(cells[i][0], cells[i][2]))
-    t0 = time.perf_counter()
-    with ThreadPoolExecutor(max_workers=n_streams) as ex:
-        futs = {i: ex.submit(work, i) for i in order}
-        res = {i: f.result() for i, f in futs.items()}
-    torch.cuda.synchronize()
-    return [res[i] for i in range(len(cells))], time.perf_counter() - t0
+    try:
+        # largest cells first, so the small ones fill the gaps at the end
+        order = sorted(range(len(cells)), key=lambda i: -peak_bytes(cells[i][0], cells[i][2]))
+        t1 = time.perf_counter()
+        with ThreadPoolExecutor(max_workers=n_streams) as ex:
+            for f in [ex.submit(isdf, i) for i in order]:
+                f.result()
+        torch.cuda.synchronize()
+        t_isdf = time.perf_counter() - t1
+        t2 = time.perf_counter()
+        graph = B.ExchangeGraph(plans, [c[1].shape[1] for c in cells])
+        t_capture = time.perf_counter() - t2
+        try:
+            reps = []
+            for _ in range(max(1, iterations)):
+                t3 = time.perf_counter()
+                Ks, exs = graph.run([c[1] for c in cells])
+                reps.append(time.perf_counter() - t3)
+        finally:
+            graph.close()
+    finally:
+        for p in plans:
+            p.close()
+    res = [{"pivots": piv[i], "K": Ks[i], "Ex": exs[i]} for i in range(len(cells))]
+    return res, {"plan_s": t_plan, "isdf_s": t_isdf, "capture_s": t_capture, "exchange_replay_s": reps,
+                 "wall_s": t_plan + t_isdf + t_capture + reps[0]}

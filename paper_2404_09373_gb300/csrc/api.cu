@@ -183,6 +183,8 @@ void free_plan(Plan* p) {
   dfree(p->V);
   dfree(p->d_err);
   dfree(p->d_ozerr);
+  dfree(p->d_perm);
+  p->d_perm = nullptr;
   p->d_ozerr = nullptr;
   p->d_diag = nullptr;
   p->d_selstate = nullptr;
@@ -295,7 +297,12 @@ void isdf_options_default(isdf_options* o) {
   o->select_block = 0;
 }
 
-isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* stream, isdf_plan_t* out) {
+namespace {
+
+// Plan creation; with defer_basis the basis buffers are allocated but not
+// evaluated (isdf_plan_batch evaluates every plan's basis in one launch).
+isdf_status plan_create(const isdf_system* sys, const isdf_options* opt, void* stream, bool defer_basis,
+                        isdf_plan_t* out) {
   if (!out) {
     g_plan_error = "out is NULL";
     return ISDF_ERR_ARG;
@@ -374,7 +381,7 @@ isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* str
   if (!st) st = dalloc_t(p, &p->d_err, 1, "error word");
   if (!st) st = dalloc_t(p, &p->d_ozerr, 1, "error word");
   if (!st) st = cuda_check(p, cudaMemsetAsync(p->d_ozerr, 0, sizeof(int), p->stream), "memset");
-  if (!st) st = basis_build(p);
+  if (!st) st = defer_basis ? basis_alloc(p) : basis_build(p);
   if (!st) st = cuda_check(p, cudaStreamSynchronize(p->stream), "plan");
   if (st) {
     g_plan_error = p->err;
@@ -383,6 +390,47 @@ isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* str
     return st;
   }
   *out = h;
+  return ISDF_OK;
+}
+
+}  // namespace
+
+isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* stream, isdf_plan_t* out) {
+  return plan_create(sys, opt, stream, false, out);
+}
+
+isdf_status isdf_plan_batch(const isdf_system* systems, int ncells, const isdf_options* opt, void* const* streams,
+                            isdf_plan_t* out) {
+  if (!systems || !out || ncells < 1) {
+    g_plan_error = "invalid arguments to isdf_plan_batch";
+    return ISDF_ERR_ARG;
+  }
+  for (int i = 0; i < ncells; ++i) out[i] = nullptr;
+  std::vector<Plan*> plans;
+  auto undo = [&](isdf_status st) {
+    const std::string why = g_plan_error;
+    for (int i = 0; i < ncells; ++i) {
+      isdf_destroy(out[i]);
+      out[i] = nullptr;
+    }
+    g_plan_error = why;
+    return st;
+  };
+  for (int i = 0; i < ncells; ++i) {
+    isdf_status st = plan_create(&systems[i], opt, streams ? streams[i] : nullptr, true, &out[i]);
+    if (st) {
+      g_plan_error = "cell " + std::to_string(i) + ": " + g_plan_error;
+      return undo(st);
+    }
+    plans.push_back(&out[i]->p);
+  }
+  // every plan's buffers exist (each plan synchronised its stream); one
+  // k_tab1d and one k_phi launch evaluate the basis of all cells and levels
+  isdf_status st = basis_eval(plans.data(), ncells, plans[0]->stream);
+  if (st) {
+    g_plan_error = plans[0]->err;
+    return undo(st);
+  }
   return ISDF_OK;
 }
 
@@ -538,6 +586,299 @@ isdf_status isdf_exchange_occ(isdf_plan_t h, const double* C, int n, double* KC_
   dfree(stageC);
   if (own) dfree(dKC);
   return st;
+}
+
+// ---------------------------------------------------------------- captured exchange builds
+
+struct isdf_exchange_graph_s {
+  std::vector<Plan*> plans;
+  std::vector<int> n;
+  int occ = 0;
+  std::vector<double*> dC, dOut;
+  double* dEx = nullptr;
+  cudaStream_t stream = nullptr;
+  std::vector<cudaStream_t> branch;
+  std::vector<cudaEvent_t> ev;
+  cudaGraphExec_t exec = nullptr;
+  long long launches = 0;  // kernels per replay
+};
+
+void isdf_exchange_graph_destroy(isdf_exchange_graph_t g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  if (g->exec) cudaGraphExecDestroy(g->exec);
+  for (double* q : g->dC) cudaFree(q);
+  for (double* q : g->dOut) cudaFree(q);
+  cudaFree(g->dEx);
+  for (cudaStream_t b : g->branch) cudaStreamDestroy(b);
+  for (cudaEvent_t e : g->ev) cudaEventDestroy(e);
+  delete g;
+}
+
+isdf_status isdf_exchange_graph(isdf_plan_t* plans, int nplans, const int* n_occ, int occ, void* stream,
+                                isdf_exchange_graph_t* out) {
+  if (!out || !plans || !n_occ || nplans < 1 || (occ != 0 && occ != 1)) {
+    g_plan_error = "invalid arguments to isdf_exchange_graph";
+    return ISDF_ERR_ARG;
+  }
+  *out = nullptr;
+  for (int i = 0; i < nplans; ++i)
+    if (!plans[i] || plans[i]->p.state < 3 || n_occ[i] < 1) {
+      g_plan_error = "isdf_exchange_graph: plan " + std::to_string(i) + " needs isdf_coulomb first and n >= 1";
+      return plans[i] ? ISDF_ERR_STATE : ISDF_ERR_ARG;
+    }
+  auto* g = new (std::nothrow) isdf_exchange_graph_s();
+  if (!g) return ISDF_ERR_OOM;
+  g->occ = occ;
+  g->stream = static_cast<cudaStream_t>(stream);
+  auto undo = [&](isdf_status st, const std::string& why) {
+    for (Plan* p : g->plans) p->capturing = false, p->d_ex_slot = nullptr;
+    isdf_exchange_graph_destroy(g);
+    g_plan_error = why;
+    return st;
+  };
+  cudaError_t e = cudaMalloc(&g->dEx, sizeof(double) * size_t(nplans));
+  for (int i = 0; i < nplans && e == cudaSuccess; ++i) {
+    Plan* p = &plans[i]->p;
+    g->plans.push_back(p);
+    g->n.push_back(n_occ[i]);
+    double *c = nullptr, *o = nullptr;
+    const size_t nc = size_t(p->nfun) * n_occ[i], no = occ ? nc : size_t(p->nfun) * p->nfun;
+    e = cudaMalloc(&c, sizeof(double) * nc);
+    if (e == cudaSuccess) e = cudaMalloc(&o, sizeof(double) * no);
+    if (e == cudaSuccess) e = cudaMemset(c, 0, sizeof(double) * nc);
+    g->dC.push_back(c);
+    g->dOut.push_back(o);
+    cudaStream_t b = nullptr;
+    cudaEvent_t ev = nullptr;
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking);
+    g->branch.push_back(b);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    g->ev.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return undo(ISDF_ERR_OOM, std::string("isdf_exchange_graph: buffers: ") + cudaGetErrorString(e));
+  }
+  cudaEvent_t fork = nullptr;
+  cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+  g->ev.push_back(fork);
+  // one exchange per plan outside the capture: uploads each plan's level
+  // order and leaves every device-side state the captured run relies on
+  for (size_t i = 0; i < g->plans.size(); ++i) {
+    Plan* p = g->plans[i];
+    double ex = 0.0;
+    const cudaStream_t keep = p->stream;
+    p->stream = g->branch[i];
+    const isdf_status st = exchange_run(p, g->dC[i], g->n[i], occ ? nullptr : g->dOut[i], occ ? g->dOut[i] : nullptr, &ex);
+    p->stream = keep;
+    if (st) return undo(st, "isdf_exchange_graph: plan " + std::to_string(i) + ": " + p->err);
+  }
+  // capture: the stream forks into one branch per plan (every plan's exchange
+  // build is an independent chain of the graph) and joins again
+  cudaGraph_t graph = nullptr;
+  const long long l0 = g_launches.load();
+  isdf_status st = ISDF_OK;
+  std::string why;
+  e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, g->stream);
+  for (size_t i = 0; i < g->plans.size() && e == cudaSuccess && !st; ++i) {
+    Plan* p = g->plans[i];
+    e = cudaStreamWaitEvent(g->branch[i], fork, 0);
+    if (e != cudaSuccess) break;
+    const cudaStream_t keep = p->stream;
+    const int prof = p->opt.profile;
+    p->stream = g->branch[i];
+    p->opt.profile = 0;
+    p->capturing = true;
+    p->d_ex_slot = g->dEx + i;
+    double ex = 0.0;
+    st = exchange_run(p, g->dC[i], g->n[i], occ ? nullptr : g->dOut[i], occ ? g->dOut[i] : nullptr, &ex);
+    if (st) why = "plan " + std::to_string(i) + ": " + p->err;
+    p->capturing = false;
+    p->d_ex_slot = nullptr;
+    p->stream = keep;
+    p->opt.profile = prof;
+    if (!st) e = cudaEventRecord(g->ev[i], g->branch[i]);
+    if (!st && e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->ev[i], 0);
+  }
+  const cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+  if (e == cudaSuccess) e = e2;
+  g->launches = g_launches.load() - l0;
+  if (!st && e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (st || e != cudaSuccess) {
+    cudaGetLastError();
+    return undo(st ? st : ISDF_ERR_CUDA,
+                st ? "isdf_exchange_graph: " + why : std::string("isdf_exchange_graph: capture: ") + cudaGetErrorString(e));
+  }
+  *out = g;
+  return ISDF_OK;
+}
+
+isdf_status isdf_exchange_graph_run(isdf_exchange_graph_t g, const double* const* C, double* const* out,
+                                    double* Ex_out) {
+  if (!g || !C) {
+    g_plan_error = "invalid arguments to isdf_exchange_graph_run";
+    return ISDF_ERR_ARG;
+  }
+  cudaError_t e = cudaSuccess;
+  for (size_t i = 0; i < g->plans.size() && e == cudaSuccess; ++i) {
+    if (!C[i]) {
+      g_plan_error = "isdf_exchange_graph_run: C[" + std::to_string(i) + "] is NULL";
+      return ISDF_ERR_ARG;
+    }
+    const size_t nc = size_t(g->plans[i]->nfun) * g->n[i];
+    e = cudaMemcpyAsync(g->dC[i], C[i], sizeof(double) * nc, cudaMemcpyDefault, g->stream);
+  }
+  if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, g->stream);
+  count_launches(g->launches);
+  for (size_t i = 0; i < g->plans.size() && e == cudaSuccess; ++i) {
+    if (!out || !out[i]) continue;
+    const Plan* p = g->plans[i];
+    const size_t no = g->occ ? size_t(p->nfun) * g->n[i] : size_t(p->nfun) * p->nfun;
+    e = cudaMemcpyAsync(out[i], g->dOut[i], sizeof(double) * no, cudaMemcpyDefault, g->stream);
+  }
+  std::vector<double> ex(g->plans.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(ex.data(), g->dEx, sizeof(double) * ex.size(), cudaMemcpyDeviceToHost, g->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    g_plan_error = std::string("isdf_exchange_graph_run: ") + cudaGetErrorString(e);
+    return ISDF_ERR_CUDA;
+  }
+  for (Plan* p : g->plans) {
+    int h = 0;
+    if (cudaMemcpy(&h, p->d_ozerr, sizeof(int), cudaMemcpyDeviceToHost) == cudaSuccess && h) {
+      cudaMemset(p->d_ozerr, 0, sizeof(int));
+      g_plan_error = "isdf_exchange_graph_run: a tensor-core pipeline wait expired (code " + std::to_string(h) + ")";
+      return ISDF_ERR_TIMEOUT;
+    }
+  }
+  if (Ex_out)
+    for (size_t i = 0; i < ex.size(); ++i) Ex_out[i] = ex[i];
+  return ISDF_OK;
+}
+
+// ---------------------------------------------------------------- checkpoint
+//
+// File: "ISDFCKP1", int32 nfun, nlev, nip, int32 grid[nlev][3], double
+// edges[3], int64 pivot codes (level order) [nip], double X^L [nfun][nip],
+// X^N [nfun][nip], V [nip][nip]; native byte order.
+
+namespace {
+constexpr char kCkpMagic[8] = {'I', 'S', 'D', 'F', 'C', 'K', 'P', '1'};
+}
+
+const char* isdf_autotune_table(void) {
+  static thread_local std::string t;
+  t = oz_tune_json();
+  return t.c_str();
+}
+
+isdf_status isdf_save(isdf_plan_t h, const char* path) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (p->state < 3) return fail(p, ISDF_ERR_STATE, "isdf_save needs isdf_coulomb first");
+  if (!path) return fail(p, ISDF_ERR_ARG, "isdf_save: path is NULL");
+  const size_t nx = size_t(p->nfun) * p->nip, nv = size_t(p->nip) * p->nip;
+  std::vector<double> xl(nx), xn(nx), v(nv);
+  isdf_status st;
+  if ((st = from_device(p, xl.data(), p->XL, nx, false)) || (st = from_device(p, xn.data(), p->XN, nx, false)) ||
+      (st = from_device(p, v.data(), p->V, nv, true)))
+    return st;
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(p, ISDF_ERR_ARG, std::string("isdf_save: cannot open ") + path);
+  const int32_t hdr[3] = {p->nfun, p->nlev, p->nip};
+  int32_t grid[3 * ISDF_MAX_LEVELS];
+  for (int l = 0; l < p->nlev; ++l)
+    for (int a = 0; a < 3; ++a) grid[3 * l + a] = p->lev[l].n[a];
+  bool ok = std::fwrite(kCkpMagic, 1, 8, f) == 8 && std::fwrite(hdr, sizeof(int32_t), 3, f) == 3 &&
+            std::fwrite(grid, sizeof(int32_t), size_t(3 * p->nlev), f) == size_t(3 * p->nlev) &&
+            std::fwrite(p->edge, sizeof(double), 3, f) == 3 &&
+            std::fwrite(p->piv_lo.data(), sizeof(int64_t), p->piv_lo.size(), f) == p->piv_lo.size() &&
+            std::fwrite(xl.data(), sizeof(double), nx, f) == nx && std::fwrite(xn.data(), sizeof(double), nx, f) == nx &&
+            std::fwrite(v.data(), sizeof(double), nv, f) == nv;
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(p, ISDF_ERR_ARG, std::string("isdf_save: write failed: ") + path);
+  return ISDF_OK;
+}
+
+isdf_status isdf_load(isdf_plan_t h, const char* path) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (!path) return fail(p, ISDF_ERR_ARG, "isdf_load: path is NULL");
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(p, ISDF_ERR_ARG, std::string("isdf_load: cannot open ") + path);
+  auto bad = [&](const char* why) {
+    std::fclose(f);
+    return fail(p, ISDF_ERR_ARG, std::string("isdf_load: ") + why + ": " + path);
+  };
+  char magic[8];
+  int32_t hdr[3];
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kCkpMagic, 8) != 0) return bad("not a checkpoint");
+  if (std::fread(hdr, sizeof(int32_t), 3, f) != 3) return bad("truncated header");
+  if (hdr[0] != p->nfun || hdr[1] != p->nlev || hdr[2] < 1) return bad("basis or levels differ from the plan's");
+  const int nip = hdr[2];
+  int32_t grid[3 * ISDF_MAX_LEVELS];
+  double edge[3];
+  if (std::fread(grid, sizeof(int32_t), size_t(3 * p->nlev), f) != size_t(3 * p->nlev) ||
+      std::fread(edge, sizeof(double), 3, f) != 3)
+    return bad("truncated header");
+  for (int l = 0; l < p->nlev; ++l)
+    for (int a = 0; a < 3; ++a)
+      if (grid[3 * l + a] != p->lev[l].n[a]) return bad("grids differ from the plan's");
+  for (int a = 0; a < 3; ++a)
+    if (edge[a] != p->edge[a]) return bad("cell differs from the plan's");
+  std::vector<int64_t> piv(nip);
+  const size_t nx = size_t(p->nfun) * nip, nv = size_t(nip) * nip;
+  std::vector<double> xl(nx), xn(nx), v(nv);
+  if (std::fread(piv.data(), sizeof(int64_t), size_t(nip), f) != size_t(nip) ||
+      std::fread(xl.data(), sizeof(double), nx, f) != nx || std::fread(xn.data(), sizeof(double), nx, f) != nx ||
+      std::fread(v.data(), sizeof(double), nv, f) != nv)
+    return bad("truncated data");
+  char extra;
+  if (std::fread(&extra, 1, 1, f) != 0) return bad("trailing data");
+  std::fclose(f);
+  // pivots: in range, level-ordered, no duplicates
+  std::vector<std::vector<int64_t>> per(p->nlev);
+  std::set<int64_t> seen;
+  int64_t last_level = 0;
+  for (int64_t c : piv) {
+    const int64_t l = c >> kPivShift, g = c & kPivMask;
+    if (c < 0 || l >= p->nlev || g >= p->lev[l].ng || l < last_level || !seen.insert(c).second)
+      return fail(p, ISDF_ERR_ARG, std::string("isdf_load: invalid pivot codes: ") + path);
+    last_level = l;
+    per[l].push_back(g);
+  }
+  // the plan now holds the loaded factors; nothing of an earlier fit survives
+  isdf_status st;
+  p->state = 0;
+  for (int l = 0; l < p->nlev; ++l) {
+    Level& lv = p->lev[l];
+    dfree(lv.xiT), dfree(lv.zct), dfree(lv.rinv), dfree(lv.spec), dfree(lv.resid), dfree(lv.d_pg);
+    lv.xiT = nullptr, lv.zct = nullptr, lv.rinv = nullptr, lv.spec = nullptr, lv.resid = nullptr, lv.d_pg = nullptr;
+    lv.pg = per[l];
+    lv.k = int(per[l].size());
+  }
+  p->resid_ready = false;
+  p->nip = nip;
+  p->piv_lo = piv;
+  p->poff[0] = 0;
+  for (int l = 0; l < p->nlev; ++l) p->poff[l + 1] = p->poff[l] + p->lev[l].k;
+  dfree(p->XL), dfree(p->XN), dfree(p->V);
+  p->XL = p->XN = p->V = nullptr;
+  if ((st = dalloc_t(p, &p->XL, nx, "X^L")) || (st = dalloc_t(p, &p->XN, nx, "X^N")) ||
+      (st = dalloc_t(p, &p->V, nv, "V")))
+    return st;
+  if ((st = cuda_check(p, cudaMemcpyAsync(p->XL, xl.data(), nx * 8, cudaMemcpyHostToDevice, p->stream), "load X^L")) ||
+      (st = cuda_check(p, cudaMemcpyAsync(p->XN, xn.data(), nx * 8, cudaMemcpyHostToDevice, p->stream), "load X^N")) ||
+      (st = cuda_check(p, cudaMemcpyAsync(p->V, v.data(), nv * 8, cudaMemcpyHostToDevice, p->stream), "load V")) ||
+      (st = cuda_check(p, cudaStreamSynchronize(p->stream), "load")))
+    return st;
+  p->state = 3;
+  return ISDF_OK;
 }
 
 int64_t isdf_get_size(isdf_plan_t h, int what) {

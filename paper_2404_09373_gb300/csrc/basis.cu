@@ -7,49 +7,86 @@
 // k_tab1d evaluates the 1-D factors (the only exp work); k_phi expands them
 // into the basis matrix Phi[f][g] of a level, an HBM-write-bound outer product.
 #include <cmath>
+#include <cstring>
+#include <vector>
 
 #include "internal.cuh"
 
 namespace isdf {
 namespace {
 
+// One descriptor per (plan, level, axis) of a batch of plans: the 1-D factors
 // tab[r * n + i] = scale[r] * sum_{t = tlo[r]}^{thi[r]} u^l exp(-alpha u^2),
-// u = i L / n - A[r] - t L
-__global__ void k_tab1d(int nG, int n, double Lax, const double* __restrict__ A, const double* __restrict__ alpha,
-                        const int* __restrict__ lpow, const int* __restrict__ tlo, const int* __restrict__ thi,
-                        const double* __restrict__ scale, double* __restrict__ tab) {
+// u = i L / n - A[r] - t L, for the level's nG functions; the per-function
+// data sit at offset `fo` of the batch's staging arrays.
+struct TabDesc {
+  int64_t e0;  // first element of this descriptor in the batch's enumeration
+  int nG, n;
+  double L;
+  int64_t fo;
+  double* tab;
+};
+
+// Every element of every descriptor of the batch: one launch for all cells,
+// levels and axes (the only exp work of the basis).
+__global__ void k_tab1d(const TabDesc* __restrict__ D, int nd, int64_t total, const double* __restrict__ A,
+                        const double* __restrict__ alpha, const int* __restrict__ lpow, const int* __restrict__ tlo,
+                        const int* __restrict__ thi, const double* __restrict__ scale) {
   const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (e >= int64_t(nG) * n) return;
-  const int r = int(e / n), i = int(e % n);
-  const double x = double(i) * (Lax / double(n));
-  const double a = alpha[r];
-  double s = 0.0;
-  for (int t = tlo[r]; t <= thi[r]; ++t) {
-    const double u = x - A[r] - double(t) * Lax;
-    const double g = exp(-a * u * u);
-    s += (lpow[r] ? u * g : g);
+  if (e >= total) return;
+  int lo = 0, hi = nd - 1;  // last descriptor with e0 <= e
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (D[mid].e0 <= e) lo = mid;
+    else hi = mid - 1;
   }
-  tab[e] = scale[r] * s;
+  const TabDesc d = D[lo];
+  const int64_t le = e - d.e0;
+  const int r = int(le / d.n), i = int(le % d.n);
+  const int64_t f = d.fo + r;
+  const double x = double(i) * (d.L / double(d.n));
+  const double a = alpha[f];
+  double s = 0.0;
+  for (int t = tlo[f]; t <= thi[f]; ++t) {
+    const double u = x - A[f] - double(t) * d.L;
+    const double g = exp(-a * u * u);
+    s += (lpow[f] ? u * g : g);
+  }
+  d.tab[le] = scale[f] * s;
 }
 
-// Phi[r][g] = tx[r][i] ty[r][j] tz[r][k], g = i + nx (j + ny k)
-// One warp per grid line (function r, y index j, z index k): the line's
-// factor ty * tz is formed once, the lanes walk x with coalesced stores, so
-// every value costs one FP64 multiply and no 64-bit division.
-__global__ void k_phi(int nG, int nx, int ny, int nz, const double* __restrict__ tx, const double* __restrict__ ty,
-                      const double* __restrict__ tz, double* __restrict__ phi) {
+// One descriptor per (plan, level): Phi[r][g] = tx[r][i] ty[r][j] tz[r][k],
+// g = i + nx (j + ny k).
+struct PhiDesc {
+  int64_t l0;  // first grid line of this descriptor in the batch's enumeration
+  int nG, nx, ny, nz;
+  const double *tx, *ty, *tz;
+  double* phi;
+};
+
+// One warp per grid line (function r, y index j, z index k) of any
+// descriptor: the line's factor ty * tz is formed once, the lanes walk x with
+// coalesced stores, so every value costs one FP64 multiply.  One launch
+// expands the basis of every level of every plan of a batch.
+__global__ void k_phi(const PhiDesc* __restrict__ D, int nd, int64_t nlines) {
   const int lane = threadIdx.x & 31;
-  const int64_t nyz = int64_t(ny) * nz, nlines = nyz * nG;
-  const int64_t ng = nyz * nx;
   const int64_t wstride = int64_t(gridDim.x) * (blockDim.x >> 5);
   for (int64_t line = int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5); line < nlines; line += wstride) {
-    const int64_t r = line / nyz;
-    const int rem = int(line - r * nyz);
-    const int k = rem / ny, j = rem - k * ny;
-    const double yz = ty[r * ny + j] * tz[r * nz + k];
-    const double* __restrict__ xr = tx + r * nx;
-    double* __restrict__ out = phi + r * ng + (int64_t(k) * ny + j) * nx;
-    for (int i = lane; i < nx; i += 32) out[i] = xr[i] * yz;
+    int lo = 0, hi = nd - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (D[mid].l0 <= line) lo = mid;
+      else hi = mid - 1;
+    }
+    const PhiDesc d = D[lo];
+    const int64_t nyz = int64_t(d.ny) * d.nz, ll = line - d.l0;
+    const int64_t r = ll / nyz;
+    const int rem = int(ll - r * nyz);
+    const int k = rem / d.ny, j = rem - k * d.ny;
+    const double yz = d.ty[r * d.ny + j] * d.tz[r * d.nz + k];
+    const double* __restrict__ xr = d.tx + r * d.nx;
+    double* __restrict__ out = d.phi + r * (nyz * d.nx) + (int64_t(k) * d.ny + j) * d.nx;
+    for (int i = lane; i < d.nx; i += 32) out[i] = xr[i] * yz;
   }
 }
 
@@ -82,65 +119,102 @@ void image_range(double A, double L, double alpha, double tol, int* lo, int* hi)
 
 }  // namespace
 
-isdf_status basis_build(Plan* p) {
-  cudaStream_t s = p->stream;
+// Basis of every level of every plan in one k_tab1d and one k_phi launch on
+// `s` (the plans' buffers must be allocated and visible to `s`).  Per-function
+// data of all (plan, level, axis) go to the device in one staging copy.
+isdf_status basis_eval(Plan* const* plans, int nplans, cudaStream_t s) {
+  Plan* p0 = plans[0];
+  std::vector<TabDesc> td;
+  std::vector<PhiDesc> pd;
+  std::vector<double> hA, hal, hsc;
+  std::vector<int> hlp, hlo, hhi;
+  int64_t e = 0, lines = 0;
+  double tab_bytes = 0.0, phi_bytes = 0.0;
+  for (int b = 0; b < nplans; ++b) {
+    Plan* p = plans[b];
+    for (int l = 0; l < p->nlev; ++l) {
+      Level& lv = p->lev[l];
+      const int nG = lv.nG;
+      if (nG == 0) continue;
+      std::vector<int> rows(lv.L);  // rows of Phi: L then N
+      rows.insert(rows.end(), lv.N.begin(), lv.N.end());
+      for (int a = 0; a < 3; ++a) {
+        TabDesc d{e, nG, lv.n[a], p->edge[a], int64_t(hA.size()), lv.tab[a]};
+        for (int r = 0; r < nG; ++r) {
+          const int mu = rows[r];
+          int lo = 0, hi = 0;
+          hA.push_back(p->xyz[3 * p->f_atom[mu] + a]);
+          hal.push_back(p->f_alpha[mu]);
+          hlp.push_back(p->f_l[a][mu]);
+          hsc.push_back(a == 0 ? p->f_norm[mu] : 1.0);
+          image_range(hA.back(), p->edge[a], hal.back(), p->image_tol, &lo, &hi);
+          hlo.push_back(lo);
+          hhi.push_back(hi);
+        }
+        td.push_back(d);
+        e += int64_t(nG) * lv.n[a];
+      }
+      pd.push_back(PhiDesc{lines, nG, lv.n[0], lv.n[1], lv.n[2], lv.tab[0], lv.tab[1], lv.tab[2], lv.phi});
+      lines += int64_t(nG) * lv.n[1] * lv.n[2];
+      phi_bytes += 8.0 * double(nG) * double(lv.ng);
+    }
+  }
+  if (td.empty()) return ISDF_OK;
+  tab_bytes = 8.0 * double(e);
+  const size_t nf = hA.size();
+  // staging: descriptors, then A, alpha, scale (double), then lpow, tlo, thi (int)
+  const size_t b_td = td.size() * sizeof(TabDesc), b_pd = pd.size() * sizeof(PhiDesc);
+  const size_t off_pd = (b_td + 15) & ~size_t(15), off_f = (off_pd + b_pd + 15) & ~size_t(15);
+  const size_t bytes = off_f + nf * (3 * sizeof(double) + 3 * sizeof(int));
+  std::vector<unsigned char> h(bytes);
+  std::memcpy(h.data(), td.data(), b_td);
+  std::memcpy(h.data() + off_pd, pd.data(), b_pd);
+  double* hd = reinterpret_cast<double*>(h.data() + off_f);
+  int* hi3 = reinterpret_cast<int*>(hd + 3 * nf);
+  for (size_t r = 0; r < nf; ++r) {
+    hd[r] = hA[r], hd[nf + r] = hal[r], hd[2 * nf + r] = hsc[r];
+    hi3[r] = hlp[r], hi3[nf + r] = hlo[r], hi3[2 * nf + r] = hhi[r];
+  }
+  unsigned char* dd = nullptr;
+  isdf_status st = dalloc_t(p0, &dd, bytes, "basis staging");
+  if (st) return st;
+  st = cuda_check(p0, cudaMemcpyAsync(dd, h.data(), bytes, cudaMemcpyHostToDevice, s), "copy");
+  const double* dA = reinterpret_cast<const double*>(dd + off_f);
+  const int* di = reinterpret_cast<const int*>(dA + 3 * nf);
+  if (!st) {
+    Prof pr(nplans == 1 ? p0 : nullptr, "basis_tab1d", tab_bytes, "byte", 1);
+    k_tab1d<<<unsigned((e + 255) / 256), 256, 0, s>>>(reinterpret_cast<const TabDesc*>(dd), int(td.size()), e, dA,
+                                                      dA + nf, di, di + nf, di + 2 * nf, dA + 2 * nf);
+    st = cuda_check(p0, cudaGetLastError(), "k_tab1d");
+  }
+  if (!st) {
+    Prof pr(nplans == 1 ? p0 : nullptr, "basis_phi", phi_bytes, "byte", 1);
+    k_phi<<<152 * 16, 256, 0, s>>>(reinterpret_cast<const PhiDesc*>(dd + off_pd), int(pd.size()), lines);
+    st = cuda_check(p0, cudaGetLastError(), "k_phi");
+  }
+  // the staging buffer must outlive the kernels
+  isdf_status st2 = cuda_check(p0, cudaStreamSynchronize(s), "basis");
+  dfree(dd);
+  return st ? st : st2;
+}
+
+// Allocate the 1-D factor tables and the basis matrix of every level.
+isdf_status basis_alloc(Plan* p) {
   for (int l = 0; l < p->nlev; ++l) {
     Level& lv = p->lev[l];
-    std::vector<int> rows(lv.L);  // rows of Phi: L then N
-    rows.insert(rows.end(), lv.N.begin(), lv.N.end());
-    const int nG = lv.nG;
-    if (nG == 0) continue;
-    for (int a = 0; a < 3; ++a) {
-      std::vector<double> A(nG), al(nG), sc(nG);
-      std::vector<int> lp(nG), lo(nG), hi(nG);
-      for (int r = 0; r < nG; ++r) {
-        const int mu = rows[r];
-        A[r] = p->xyz[3 * p->f_atom[mu] + a];
-        al[r] = p->f_alpha[mu];
-        lp[r] = p->f_l[a][mu];
-        sc[r] = (a == 0) ? p->f_norm[mu] : 1.0;
-        image_range(A[r], p->edge[a], al[r], p->image_tol, &lo[r], &hi[r]);
-      }
-      // one staging buffer: A, alpha, scale (double) then lpow, tlo, thi (int)
-      double* dd = nullptr;
-      isdf_status st = dalloc_t(p, &dd, size_t(3) * nG + size_t(3) * nG, "basis staging");
-      if (st) return st;
-      int* di = reinterpret_cast<int*>(dd + 3 * nG);
-      std::vector<double> hd(3 * nG);
-      std::vector<int> hi3(3 * nG);
-      for (int r = 0; r < nG; ++r) {
-        hd[r] = A[r];
-        hd[nG + r] = al[r];
-        hd[2 * nG + r] = sc[r];
-        hi3[r] = lp[r];
-        hi3[nG + r] = lo[r];
-        hi3[2 * nG + r] = hi[r];
-      }
-      st = cuda_check(p, cudaMemcpyAsync(dd, hd.data(), sizeof(double) * 3 * nG, cudaMemcpyHostToDevice, s), "copy");
-      if (st) return st;
-      st = cuda_check(p, cudaMemcpyAsync(di, hi3.data(), sizeof(int) * 3 * nG, cudaMemcpyHostToDevice, s), "copy");
-      if (st) return st;
-      st = dalloc_t(p, &lv.tab[a], size_t(nG) * lv.n[a], "basis 1-D tables");
-      if (st) return st;
-      const int64_t tot = int64_t(nG) * lv.n[a];
-      Prof pr(p, "basis_tab1d", 8.0 * double(tot), "byte", 1);
-      k_tab1d<<<unsigned((tot + 255) / 256), 256, 0, s>>>(nG, lv.n[a], p->edge[a], dd, dd + nG, di, di + nG,
-                                                          di + 2 * nG, dd + 2 * nG, lv.tab[a]);
-      st = cuda_check(p, cudaGetLastError(), "k_tab1d");
-      if (st) return st;
-      // the staging buffer must outlive the kernel: synchronise before freeing
-      st = cuda_check(p, cudaStreamSynchronize(s), "basis tables");
-      dfree(dd);
-      if (st) return st;
-    }
-    isdf_status st = dalloc_t(p, &lv.phi, size_t(nG) * lv.ng, "basis values Phi");
-    if (st) return st;
-    Prof pr(p, "basis_phi", 8.0 * double(nG) * double(lv.ng), "byte", 1);
-    k_phi<<<152 * 16, 256, 0, s>>>(nG, lv.n[0], lv.n[1], lv.n[2], lv.tab[0], lv.tab[1], lv.tab[2], lv.phi);
-    st = cuda_check(p, cudaGetLastError(), "k_phi");
-    if (st) return st;
+    if (lv.nG == 0) continue;
+    isdf_status st;
+    for (int a = 0; a < 3; ++a)
+      if ((st = dalloc_t(p, &lv.tab[a], size_t(lv.nG) * lv.n[a], "basis 1-D tables"))) return st;
+    if ((st = dalloc_t(p, &lv.phi, size_t(lv.nG) * lv.ng, "basis values Phi"))) return st;
   }
   return ISDF_OK;
+}
+
+isdf_status basis_build(Plan* p) {
+  isdf_status st = basis_alloc(p);
+  if (!st) st = basis_eval(&p, 1, p->stream);
+  return st;
 }
 
 // X^L and X^N (N x nip, level-ordered pivot columns) from Phi at the pivots.

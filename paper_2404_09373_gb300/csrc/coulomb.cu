@@ -174,6 +174,7 @@ isdf_status coulomb_block_tc(Plan* p, const double2* left, const Level& la, cons
   if (same) tiles = (tiles + a.nrt) / 2;
   int64_t splits = (4 * 152 + tiles - 1) / tiles;
   splits = std::max<int64_t>(1, std::min<int64_t>(splits, std::min<int64_t>(64, a.nkt / 64 + 1)));
+  splits = oz_tuned_splits(p, a, b, Cblk, p->nip, 0, same ? 1 : 0, int(splits), s);
   if (splits > 1 && (st = dalloc_t(p, &work, size_t(splits) * la.k * lb.k, "split-k partials"))) {
     oz_free(a), oz_free(b);
     return st;

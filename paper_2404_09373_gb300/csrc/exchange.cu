@@ -152,10 +152,12 @@ isdf_status tc_product(Plan* p, const double* a, int64_t M, int64_t sar, int64_t
   int64_t tiles = A.nrt * B.nrt;
   int64_t splits = std::max<int64_t>(1, std::min<int64_t>((2 * 152 + tiles - 1) / tiles, A.nkt / 32 + 1));
   splits = std::min<int64_t>(splits, 16);
+  splits = oz_tuned_splits(p, A, B, C, ldc, 0, sym, int(splits), s);
   if (splits > 1 && (st = dalloc_t(p, &work, size_t(splits) * M * N, "split-k partials")))
     return oz_free(A), oz_free(B), st;
   oz_gemm(A, B, C, ldc, 0, 1.0, 0, sym, int(splits), work, p->d_ozerr, s);
-  st = oz_check(p);
+  // under graph capture the error word is read after the graph has run
+  st = p->capturing ? cuda_check(p, cudaGetLastError(), "tensor-core launch") : oz_check(p);
   oz_free(A);
   oz_free(B);
   dfree(work);
@@ -228,19 +230,28 @@ isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* d
   double *y2 = nullptr, *yg = nullptr, *rgg = nullptr, *rgl = nullptr, *rll = nullptr, *W = nullptr, *x2 = nullptr,
          *T = nullptr, *kc = nullptr, *kcp = nullptr, *cp = nullptr, *xlp = nullptr, *xnp = nullptr, *u = nullptr,
          *tmp = nullptr, *part = nullptr, *dex = nullptr;
-  int* dperm = nullptr;
   auto cleanup = [&]() {
     for (double* q : {y2, yg, rgg, rgl, rll, W, x2, T, kc, kcp, cp, xlp, xnp, u, tmp, part, dex}) dfree(q);
-    dfree(dperm);
   };
   isdf_status st;
+  if (!p->d_perm) {
+    // the level order lives with the plan (uploaded once, outside any capture)
+    if (p->capturing) return fail(p, ISDF_ERR_STATE, "exchange under capture before a first exchange");
+    if ((st = dalloc_t(p, &p->d_perm, size_t(N), "level order"))) return st;
+    if ((st = cuda_check(p, cudaMemcpyAsync(p->d_perm, lo.perm.data(), sizeof(int) * size_t(N), cudaMemcpyHostToDevice,
+                                            s),
+                         "level order")) ||
+        (st = cuda_check(p, cudaStreamSynchronize(s), "level order")))
+      return st;
+  }
+  const int* dperm = p->d_perm;
   if ((st = dalloc_t(p, &y2, size_t(n2) * n, "Y_L, Y_N")) || (st = dalloc_t(p, &yg, size_t(nip) * n, "Y_G")) ||
       (st = dalloc_t(p, &rgg, size_t(nip) * nip, "R_GG")) || (st = dalloc_t(p, &rgl, size_t(nip) * nip, "R_GL")) ||
       (st = dalloc_t(p, &rll, size_t(nip) * nip, "R_LL")) || (st = dalloc_t(p, &W, size_t(n2) * n2, "W")) ||
       (st = dalloc_t(p, &cp, size_t(N) * n, "C by level")) || (st = dalloc_t(p, &xlp, size_t(N) * nip, "X^L by level")) ||
       (st = dalloc_t(p, &xnp, size_t(N) * nip, "X^N by level")) || (st = dalloc_t(p, &kc, size_t(N) * n, "K C")) ||
       (st = dalloc_t(p, &tmp, size_t(N) * std::max<int64_t>(n, nip), "block partials")) ||
-      (st = dalloc_t(p, &dperm, size_t(N), "level order")) || (st = dalloc_t(p, &part, 1024, "reduction")) ||
+      (st = dalloc_t(p, &part, 1024, "reduction")) ||
       (st = dalloc_t(p, &dex, 1, "E_x"))) {
     cleanup();
     return st;
@@ -266,7 +277,6 @@ isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* d
   const double fl = fl_y + fl_r + (dK ? 2.0 * n2 * n2 * N + 2.0 * N * N * n2 + 2.0 * N * N * n : 2.0 * n2 * n2 * n + fl_kc);
   {
     Prof pr(p, "exchange", fl, "flop", kLaunchesInside);
-    cudaMemcpyAsync(dperm, lo.perm.data(), sizeof(int) * size_t(N), cudaMemcpyHostToDevice, s);
     k_gather_rows<<<unsigned((N * n + 255) / 256), 256, 0, s>>>(N, n, dperm, dC, cp);
     k_gather_rows<<<unsigned((N * nip + 255) / 256), 256, 0, s>>>(N, nip, dperm, p->XL, xlp);
     k_gather_rows<<<unsigned((N * nip + 255) / 256), 256, 0, s>>>(N, nip, dperm, p->XN, xnp);
@@ -340,6 +350,11 @@ isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* d
     k_dot_partial<<<nb, 256, 0, s>>>(N * n, dC, kc, part);
     k_sum_final<<<1, 256, 0, s>>>(nb, part, -1.0, dex);
     count_launches(2);
+  }
+  if (p->capturing) {
+    st = cuda_check(p, cudaMemcpyAsync(p->d_ex_slot, dex, sizeof(double), cudaMemcpyDeviceToDevice, s), "E_x copy");
+    cleanup();
+    return st;
   }
   st = cuda_check(p, cudaMemcpyAsync(Ex, dex, sizeof(double), cudaMemcpyDeviceToHost, s), "E_x copy");
   if (!st) st = cuda_check(p, cudaStreamSynchronize(s), "exchange");

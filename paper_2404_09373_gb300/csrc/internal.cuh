@@ -102,6 +102,12 @@ struct Plan {
   bool resid_ready = false;     // fit_resid / lev[].resid computed for the current fit
   std::string err;
   std::string fault;            // host fault injection (ISDF_FAULT)
+  // exchange build: function level order on the device (made by the first
+  // exchange), and the capture mode of isdf_exchange_graph (no host
+  // synchronisation, no pageable copies, E_x written to *d_ex_slot)
+  int* d_perm = nullptr;
+  bool capturing = false;
+  double* d_ex_slot = nullptr;
   // profiling
   std::vector<ProfEvent> pend;
   std::map<std::string, KStat> stats;
@@ -135,6 +141,8 @@ bool is_device_ptr(const void* ptr);
 
 // ---- kernels / stages ----
 isdf_status basis_build(Plan* p);                                    // basis.cu
+isdf_status basis_alloc(Plan* p);                                    // basis.cu
+isdf_status basis_eval(Plan* const* plans, int nplans, cudaStream_t s);  // basis.cu: one launch per kernel
 isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>* cand, int* nfound);  // select.cu
 isdf_status fit_run(Plan* p);                                        // fit.cu
 isdf_status fit_residual_run(Plan* p);  // fit.cu: residual statistics on request (precision 1)
@@ -219,6 +227,11 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
              int splits, double* work, int* err, cudaStream_t s);
 int64_t oz_tile_elems(int64_t rows, int64_t K, int rt, int S);
 // the same product with its scratch in a fixed static device array (no allocation)
+// split-K factor of a product shape: cached, else timed on these operands
+// (outside graph capture; ISDF_NO_AUTOTUNE keeps the heuristic)
+int oz_tuned_splits(Plan* p, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, int sym,
+                    int heuristic, cudaStream_t s);
+std::string oz_tune_json();
 size_t gemm_noalloc_capacity();
 isdf_status gemm_noalloc(const double* A, const double* B, double* C, int64_t M, int64_t N, int64_t K, int64_t lda,
                          int64_t ldb, int64_t ldc, double alpha, int slices, cudaStream_t s, std::string& why);

@@ -33,8 +33,11 @@
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
+#include <vector>
 
 #include "internal.cuh"
 
@@ -1042,6 +1045,90 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
     k_oz_reduce<<<unsigned((tot + 255) / 256), 256, 0, s>>>(work, P.splits, A.rows, B.rows, C, P.cm, P.cn, sym);
     count_launches(1);
   }
+}
+
+// ---------------------------------------------------------------- split-K autotuner
+//
+// The one free launch parameter of a product shape is its split-K factor
+// (how many CTAs share one output tile's k range).  On the first product of
+// a shape (rows of A, rows of B, k tiles, digits, symmetric or not) outside
+// any graph capture, every admissible candidate runs on the real operands
+// (one warm-up, then the best of two timed runs, CUDA events on the product's
+// stream) and the fastest is cached for the process; the heuristic's choice
+// is among the candidates, and the chosen one runs last so C holds its
+// result.  Candidates whose split-K partials would exceed 2 GiB are skipped.
+
+namespace {
+struct TuneKey {
+  int64_t M, N, nkt;
+  int S, sym, trans;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(M, N, nkt, S, sym, trans) < std::tie(o.M, o.N, o.nkt, o.S, o.sym, o.trans);
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, float>> g_tune;  // shape -> (splits, ms)
+}  // namespace
+
+int oz_tuned_splits(Plan* p, const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, int sym,
+                    int heuristic, cudaStream_t s) {
+  const TuneKey key{A.rows, B.rows, A.nkt, A.S, sym, trans};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second.first;
+  }
+  if ((p && p->capturing) || std::getenv("ISDF_NO_AUTOTUNE")) return heuristic;
+  std::vector<int> cand;
+  for (int c : {1, 2, 4, 8, 16, 32, 64})
+    if (c <= std::max<int64_t>(1, A.nkt)) cand.push_back(c);
+  if (std::find(cand.begin(), cand.end(), heuristic) == cand.end()) cand.push_back(heuristic);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int* err = p ? p->d_ozerr : nullptr;
+  int best = heuristic;
+  float best_ms = 1e30f;
+  for (int c : cand) {
+    double* work = nullptr;
+    const size_t wbytes = c > 1 ? sizeof(double) * size_t(c) * A.rows * B.rows : 0;
+    if (wbytes > (size_t(2) << 30)) continue;
+    if (wbytes && cudaMallocAsync(reinterpret_cast<void**>(&work), wbytes, s) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    float ms = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0, s);
+      oz_gemm(A, B, C, ldc, trans, 1.0, 0, sym, c, work, err, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0.0f;
+      if (rep > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms = std::min(ms, t);
+    }
+    if (work) cudaFreeAsync(work, s);
+    if (ms < best_ms) best_ms = ms, best = c;
+  }
+  cudaStreamSynchronize(s);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaGetLastError();
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  g_tune[key] = {best, best_ms};
+  return best;
+}
+
+std::string oz_tune_json() {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  std::string o = "[";
+  for (const auto& kv : g_tune) {
+    if (o.size() > 1) o += ",";
+    o += "{\"M\":" + std::to_string(kv.first.M) + ",\"N\":" + std::to_string(kv.first.N) +
+         ",\"k_tiles\":" + std::to_string(kv.first.nkt) + ",\"digits\":" + std::to_string(kv.first.S) +
+         ",\"sym\":" + std::to_string(kv.first.sym) + ",\"splits\":" + std::to_string(kv.second.first) +
+         ",\"ms\":" + std::to_string(kv.second.second) + "}";
+  }
+  return o + "]";
 }
 
 // ---------------------------------------------------------------- fixed scratch

@@ -52,6 +52,13 @@ EXPORTED = [
     "isdf_rfft3",
     "isdf_grids_for_threshold",
     "isdf_exchange_occ",
+    "isdf_save",
+    "isdf_load",
+    "isdf_plan_batch",
+    "isdf_exchange_graph",
+    "isdf_exchange_graph_run",
+    "isdf_exchange_graph_destroy",
+    "isdf_autotune_table",
 ]
 
 
@@ -152,6 +159,20 @@ def load_library(build_if_missing: bool = True):
     lib.isdf_gemm_f64_noalloc.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_int64, c_int64, c_int64,
                                           c_int64, c_double, c_int, c_void_p]
     lib.isdf_gemm_f64_noalloc.restype = c_int
+    lib.isdf_plan_batch.argtypes = [POINTER(isdf_system), c_int, POINTER(isdf_options), c_void_p, c_void_p]
+    lib.isdf_plan_batch.restype = c_int
+    lib.isdf_exchange_graph.argtypes = [c_void_p, c_int, c_void_p, c_int, c_void_p, POINTER(c_void_p)]
+    lib.isdf_exchange_graph.restype = c_int
+    lib.isdf_exchange_graph_run.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+    lib.isdf_exchange_graph_run.restype = c_int
+    lib.isdf_exchange_graph_destroy.argtypes = [c_void_p]
+    lib.isdf_exchange_graph_destroy.restype = None
+    lib.isdf_autotune_table.argtypes = []
+    lib.isdf_autotune_table.restype = ctypes.c_char_p
+    lib.isdf_save.argtypes = [c_void_p, ctypes.c_char_p]
+    lib.isdf_save.restype = c_int
+    lib.isdf_load.argtypes = [c_void_p, ctypes.c_char_p]
+    lib.isdf_load.restype = c_int
     lib.isdf_exchange_occ.argtypes = [c_void_p, c_void_p, c_int, c_void_p, POINTER(c_double)]
     lib.isdf_exchange_occ.restype = c_int
     lib.isdf_grids_for_threshold.argtypes = [POINTER(isdf_system), c_double, POINTER(c_int)]
@@ -271,6 +292,82 @@ def isdf_plan(system: dict, options=None, stream=None) -> Plan:
     return Plan(h.value, lib, system)
 
 
+def isdf_plan_batch(systems, options=None, streams=None):
+    """Plans for many cells; the basis of all cells and levels is evaluated by
+    one launch of each basis kernel.  Returns a list of Plan."""
+    lib = load_library()
+    if options is None:
+        options = default_options()
+    elif isinstance(options, dict):
+        options = default_options(**options)
+    n = len(systems)
+    arr = (isdf_system * n)()
+    keep = []
+    for i, sysd in enumerate(systems):
+        st_, k = _system_struct(sysd)
+        arr[i] = st_
+        keep.append(k)
+    sp = None
+    if streams is not None:
+        sp = (c_void_p * n)(*[c_void_p(int(x)) for x in streams])
+    out = (c_void_p * n)()
+    st = lib.isdf_plan_batch(arr, n, ctypes.byref(options), sp, out)
+    if st != ISDF_OK:
+        raise IsdfError(st, lib.isdf_last_error(None).decode())
+    return [Plan(out[i], lib, systems[i]) for i in range(n)]
+
+
+class ExchangeGraph:
+    """One CUDA graph holding the exchange builds of several fitted plans."""
+
+    def __init__(self, plans, n_occ, occ=False, stream=None):
+        self._lib = load_library()
+        self.plans = list(plans)
+        self.n = [int(x) for x in n_occ]
+        self.occ = bool(occ)
+        hp = (c_void_p * len(self.plans))(*[c_void_p(p.handle) for p in self.plans])
+        nn = (c_int * len(self.plans))(*self.n)
+        h = c_void_p()
+        st = self._lib.isdf_exchange_graph(hp, len(self.plans), nn, int(self.occ),
+                                           c_void_p(_default_stream() if stream is None else stream), ctypes.byref(h))
+        if st != ISDF_OK:
+            raise IsdfError(st, self._lib.isdf_last_error(None).decode())
+        self.handle = h.value
+
+    def run(self, Cs, outs=None):
+        """Replay with orbitals Cs[i]; returns (outputs, E_x list).  Outputs are
+        NumPy arrays unless ``outs`` (arrays or tensors) are given."""
+        m = len(self.plans)
+        Cs = [np.ascontiguousarray(C, dtype=np.float64) if isinstance(C, np.ndarray) else C for C in Cs]
+        if outs is None:
+            outs = [np.zeros((p.system_nfun, n) if self.occ else (p.system_nfun, p.system_nfun))
+                    for p, n in zip(self._nfun_views(), self.n)]
+        cp = (c_void_p * m)(*[c_void_p(_addr(C, np.float64)) for C in Cs])
+        op = (c_void_p * m)(*[c_void_p(_addr(o, np.float64)) for o in outs])
+        ex = (c_double * m)()
+        st = self._lib.isdf_exchange_graph_run(self.handle, cp, op, ex)
+        if st != ISDF_OK:
+            raise IsdfError(st, self._lib.isdf_last_error(None).decode())
+        return outs, list(ex)
+
+    def _nfun_views(self):
+        from types import SimpleNamespace
+
+        return [SimpleNamespace(system_nfun=int(sum(1 if l == 0 else 3 for l in p.system["shell_l"])))
+                for p in self.plans]
+
+    def close(self):
+        if self.handle:
+            self._lib.isdf_exchange_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def isdf_grids_for_threshold(system: dict, eps_K: float):
     """Grid points per axis of every level from the accuracy threshold eps_K
     (host computation in the library).  Returns an int array (nlevel, 3)."""
@@ -333,6 +430,23 @@ def isdf_exchange_occ(plan: Plan, C, KC_out=None):
     plan._check(plan._lib.isdf_exchange_occ(plan.handle, _addr(C, np.float64), n, _addr(KC, np.float64),
                                             ctypes.byref(ex)))
     return KC, ex.value
+
+
+def isdf_autotune_table():
+    """Split-K choices the library measured so far (list of dicts)."""
+    import json
+
+    return json.loads(load_library().isdf_autotune_table().decode())
+
+
+def isdf_save(plan: Plan, path):
+    """Write the pivots, X^L, X^N and V of a plan (after isdf_coulomb)."""
+    plan._check(plan._lib.isdf_save(plan.handle, os.fsencode(path)))
+
+
+def isdf_load(plan: Plan, path):
+    """Read a checkpoint into a plan of the same system; exchange builds follow."""
+    plan._check(plan._lib.isdf_load(plan.handle, os.fsencode(path)))
 
 
 def isdf_get(plan: Plan, what: int, dst=None):

@@ -327,3 +327,52 @@ def test_threshold_driven_grids_and_isdf_tolerance():
         g = gpu_run(sysd, C, cap, tol=1e-4, opts={"precision": prec, "prefilter": 1, "select_block": 64})
         assert 0 < o["pivots"].size < cap
         assert_parity(g, o, natom=8, k_tol=1e-8 if prec == 0 else 1e-6, tc=prec == 1)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_checkpoint_resume_gives_the_same_exchange(small, tmp_path, prec):
+    """isdf_save after the Coulomb matrix, isdf_load into a fresh plan of the
+    same system: the exchange builds (K and the occ-RI output) are bitwise
+    those of the original plan, and E_x matches the oracle.  Malformed files
+    and a plan of another system are refused with ISDF_ERR_ARG."""
+    sysd, C, o = small
+    path = str(tmp_path / "factors.isdf")
+    plan = B.isdf_plan(sysd, {"precision": prec})
+    try:
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_save(plan, path)
+        assert e.value.status == B.ISDF_ERR_STATE
+        piv, _ = B.isdf_select_points(plan, 300)
+        B.isdf_fit(plan, piv)
+        B.isdf_coulomb(plan)
+        K1, E1 = B.isdf_exchange(plan, C)
+        KC1, _ = B.isdf_exchange_occ(plan, C)
+        B.isdf_save(plan, path)
+    finally:
+        plan.close()
+    plan = B.isdf_plan(sysd, {"precision": prec})
+    try:
+        B.isdf_load(plan, path)
+        K2, E2 = B.isdf_exchange(plan, C)
+        KC2, _ = B.isdf_exchange_occ(plan, C)
+        np.testing.assert_array_equal(K2, K1)
+        np.testing.assert_array_equal(KC2, KC1)
+        assert E2 == E1
+        assert abs(E2 - o["Ex"]) / 8 <= (1e-8 if prec == 0 else 1e-6)
+    finally:
+        plan.close()
+    raw = open(path, "rb").read()
+    bad = tmp_path / "bad.isdf"
+    other, _ = S.small_multigrid(per_cell=(12, 6, 4), seed=5)
+    for content, sysx in ((raw[:200], sysd), (b"NOTACKPT" + raw[8:], sysd), (raw + b"x", sysd), (raw, other)):
+        bad.write_bytes(content)
+        plan = B.isdf_plan(sysx)
+        try:
+            with pytest.raises(B.IsdfError) as e:
+                B.isdf_load(plan, str(bad))
+            assert e.value.status == B.ISDF_ERR_ARG
+            with pytest.raises(B.IsdfError) as e:
+                B.isdf_exchange(plan, C)
+            assert e.value.status == B.ISDF_ERR_STATE  # the refused load changed nothing
+        finally:
+            plan.close()
