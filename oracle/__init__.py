@@ -21,6 +21,8 @@ from .isdf import (  # noqa: F401
     coulomb,
     exchange,
     run,
+    run_sinc,
+    coarse_points,
     PIVOT_SHIFT,
 )
 from .nofit import nofit_exchange, brute_exchange  # noqa: F401

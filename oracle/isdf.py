@@ -501,6 +501,51 @@ def exchange(XL, XN, V, C):
 
 
 # ---------------------------------------------------------------------------
+# The coarsest level as the paper's sparse universal grid (Section III and
+# III.A: every point of the universal grid U is an ISDF point, its fitting
+# function the grid's sinc function, so the pair densities of that grid are
+# represented exactly; (R_U|R_U') is only ever applied)
+# ---------------------------------------------------------------------------
+
+
+def coarse_points(system):
+    """Pivot codes of every point of the coarsest level, in grid order."""
+    lev = len(system["grids"]) - 1
+    ng = int(np.prod(system["grids"][lev]))
+    return (np.int64(lev) << PIVOT_SHIFT) | np.arange(ng, dtype=np.int64)
+
+
+def run_sinc(system, C, nip, tol=0.0, tie_rel=1e-9, tie_abs=1e-13, reg_rel=1e-14, pivots=None):
+    """Multigrid ISDF with the coarsest level as the universal sinc grid.
+
+    The greedy selection (Eq. 2) and the least-squares fit (Eq. 3) run on the
+    finer levels only (``nip`` counts their pivots).  On the coarsest level
+    every grid point is an interpolation point and its interpolation vector is
+    the unit vector of that point (Xi = I): a grid function is its own
+    interpolant, so no fit is needed.  V (Eq. 1) and K (Eq. 8) are then the
+    same definitions over all interpolation points -- fitted and coarse.
+    """
+    funcs = expand_functions(system)
+    levels = _level_data(system, funcs)
+    fine = levels[:-1]
+    sel = None
+    if pivots is None:
+        sel = select_points(fine, nip, tol, tie_rel, tie_abs)
+        pivots = sel["pivots"]
+    pivots = np.asarray(pivots, dtype=np.int64)
+    Xi = fit(fine, pivots, reg_rel)
+    ngc = levels[-1]["PhiL"].shape[1]
+    Xi.append(np.eye(ngc))
+    V = coulomb(system, Xi)
+    allp = np.concatenate([pivots, coarse_points(system)])
+    XL, XN = pivot_factors(system, funcs, allp)
+    K, Ex = exchange(XL, XN, V, C)
+    return {"pivots": pivots, "dvals": None if sel is None else sel["dvals"], "all_pivots": allp,
+            "order": level_ordered(allp, len(levels)), "levels": levels, "funcs": funcs, "Xi": Xi, "V": V,
+            "XL": XL, "XN": XN, "K": K, "Ex": Ex}
+
+
+# ---------------------------------------------------------------------------
 # Whole path
 # ---------------------------------------------------------------------------
 

@@ -559,3 +559,70 @@ def test_level_grids_for_threshold_follow_the_sharpest_function_and_nest():
     # a loose threshold that gives two levels the same size: the finer one is raised
     g = O.grids_for_threshold(sysd, 0.5)
     assert np.all(g[:-1] > g[1:])
+
+
+# --------------------------------------------------------------------------- coarse level as the sinc grid (Section III)
+
+
+@pytest.mark.parametrize("levels,sites,a,rel", [(2, ONE_ATOM, 4.0, 1e-10), (3, ONE_ATOM, 4.0, 1e-10),
+                                                (3, TWO_ATOMS, 4.5, 5e-8)])
+def test_sinc_coarse_level_is_exact_at_full_rank(levels, sites, a, rel):
+    """With every finer level fitted to its full pair rank and every coarse
+    point an interpolation point (Xi = I), the four-term exchange reproduces
+    the exact no-fit exchange: the coarse pair densities are grid functions
+    of the coarse grid, represented exactly by its sinc functions.  (With two
+    atoms the full-rank fit is ill-conditioned and the agreement stops near
+    1e-8 relative; a wrong coarse treatment is off by orders of magnitude.)"""
+    sysd = tiny(levels=levels, sites=sites, a=a)
+    C = orbitals(sysd)
+    Kn, En = oracle.nofit_exchange(sysd, C)
+    npts = int(sum(np.prod(g) for g in sysd["grids"][:-1]))
+    r = oracle.run_sinc(sysd, C, npts, tol=1e-14, reg_rel=0.0)
+    assert np.max(np.abs(r["K"] - Kn)) <= rel * np.max(np.abs(Kn))
+    assert abs(r["Ex"] - En) <= rel * abs(En)
+
+
+def test_planted_mistake_in_the_sinc_coarse_level_is_caught(monkeypatch):
+    """Xi = 2 I instead of I on the coarse level breaks the exactness pin."""
+    sysd = tiny(levels=2)
+    C = orbitals(sysd)
+    Kn, _ = oracle.nofit_exchange(sysd, C)
+    orig = np.eye
+    monkeypatch.setattr(O.np, "eye", lambda n, *a, **k: 2.0 * orig(n, *a, **k))
+    r = oracle.run_sinc(sysd, C, int(np.prod(sysd["grids"][0])), tol=1e-14, reg_rel=0.0)
+    monkeypatch.setattr(O.np, "eye", orig)
+    assert np.max(np.abs(r["K"] - Kn)) > 1e-3 * np.max(np.abs(Kn))
+
+
+def test_sinc_identity_is_the_least_squares_fit_with_all_coarse_points():
+    """Xi = I on the coarse level is what the fit of Eq. 3 gives when every
+    coarse point is a pivot and M_c is nonsingular (a 2^3 coarse grid with
+    more pair functions than points)."""
+    sysd = tiny(levels=2, n=(8, 2), sites=TWO_ATOMS, a=4.5)
+    funcs = O.expand_functions(sysd)
+    levels = O._level_data(sysd, funcs)
+    allc = oracle.coarse_points(sysd)
+    Xi = O.fit(levels, allc, reg_rel=0.0)
+    assert np.max(np.abs(Xi[1] - np.eye(8))) <= 1e-8
+
+
+def test_sinc_coarse_coulomb_block_is_a_circulant():
+    """(R_U|R_U') depends only on the difference of the two grid points
+    (periodic), so it can be applied by FFT without being stored; it is PSD
+    and has the constant vector (G = 0) in its null space."""
+    sysd = tiny(levels=2, n=(8, 4), sites=TWO_ATOMS, a=4.5)
+    C = orbitals(sysd)
+    r = oracle.run_sinc(sysd, C, 20)
+    k = r["pivots"].size
+    Vu = r["V"][k:, k:]
+    n = 4
+    idx = np.arange(n ** 3)
+    ijk = np.stack([idx % n, (idx // n) % n, idx // (n * n)], axis=1)
+    for g in range(0, n ** 3, 7):
+        for h in range(0, n ** 3, 5):
+            d = (ijk[h] - ijk[g]) % n
+            h0 = d[0] + n * (d[1] + n * d[2])
+            assert abs(Vu[g, h] - Vu[0, h0]) <= 1e-12 * np.abs(Vu).max()
+    ev = np.linalg.eigvalsh(Vu)
+    assert ev.min() >= -1e-10 * ev.max()
+    assert np.max(np.abs(Vu @ np.ones(n ** 3))) <= 1e-10 * np.abs(Vu).max()
