@@ -50,9 +50,10 @@ def parse():
     ap.add_argument("--select-block", type=int, default=96,
                     help="speculative block size of the selection (0: one FP64 step at a time)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-FP64 comparison step")
-    ap.add_argument("--batch", action="store_true",
-                    help="also run the 24-cell batch (6 each of 1x1x1, 1x1x2, 1x2x2, 2x2x2, sigma 0.1) on "
-                         "concurrent streams and one stream")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 24-cell batch (6 each of 1x1x1, 1x1x2, 1x2x2, 2x2x2, sigma 0.1): one basis "
+                         "launch for all cells, ISDF on 4 and on 1 concurrent streams, the exchange builds of all "
+                         "cells as one captured CUDA graph")
     ap.add_argument("--learned", type=int, default=0,
                     help="train the point proposer on this many seeded 1x1x1/2x2x1 cells, then time the "
                          "learned selection (4 N_ip candidates, fallback check) on the workload")
@@ -527,6 +528,7 @@ def main():
                  "dEx_per_atom_vs_fast_Ha": abs(r0["Ex"] - res[-1]["Ex"]) / sysd["xyz"].shape[0]}
 
     # ---- occ-RI output (K C without K) on the same workload, beside the exchange
+    step(occ=True)  # first call of the occ-RI shapes (the autotuner measures them)
     r_occ = step(occ=True)
     occ_ri = {"exchange_s": r_occ["exchange"], "exchange_occ_s": r_occ["exchange_occ"],
               "s_iter_occ": (r_occ["plan"] + r_occ["select"] + r_occ["fit"] + r_occ["coulomb"]) / SCF_CHARGE +
@@ -540,12 +542,28 @@ def main():
         sys_t = dict(sysd)
         sys_t["grids"] = B.isdf_grids_for_threshold(sysd, EPS_K).astype(np.int64)
         cap = int(1.25 * nip)
+        step(sysx=sys_t, nipx=cap, tol=EPS_ISDF)  # warm-up: new shapes for the autotuner
         rt = step(sysx=sys_t, nipx=cap, tol=EPS_ISDF)
         thr = {"eps_K": EPS_K, "eps_isdf": EPS_ISDF, "grids": sys_t["grids"].tolist(), "nip_cap": cap,
                "nip_level": rt["nip_level"], "nip": int(sum(rt["nip_level"])),
                "s_iter": (rt["plan"] + rt["select"] + rt["fit"] + rt["coulomb"]) / SCF_CHARGE + rt["exchange"],
                "stages_s": {k: rt[k] for k in ("plan", "select", "fit", "coulomb", "exchange")},
                "Ex_per_atom": rt["Ex"] / sysd["xyz"].shape[0]}
+
+    # ---- the coarsest level as the universal sinc grid (all 24^3 points, Xi = I;
+    # the finer levels keep the default run's number of fitted points)
+    sinc = None
+    if args.workload == "2x2x2":
+        nlv = res[-1]["nip_level"]
+        nip_f = int(sum(nlv[:-1]))
+        o_s = dict(opts, coarse_sinc=1)
+        step(o=o_s, sysx=sysd, nipx=nip_f)  # warm-up (new product shapes)
+        rs = step(o=o_s, sysx=sysd, nipx=nip_f)
+        sinc = {"fitted_points": nip_f, "coarse_points": int(np.prod(sysd["grids"][-1])),
+                "s_iter": (rs["plan"] + rs["select"] + rs["fit"] + rs["coulomb"]) / SCF_CHARGE + rs["exchange"],
+                "stages_s": {k: rs[k] for k in ("plan", "select", "fit", "coulomb", "exchange")},
+                "Ex_per_atom": rs["Ex"] / sysd["xyz"].shape[0],
+                "dEx_per_atom_vs_fitted_coarse_Ha": abs(rs["Ex"] - res[-1]["Ex"]) / sysd["xyz"].shape[0]}
 
     # ---- learned point proposal (trained here; reported beside the main number)
     learned = None
@@ -587,17 +605,21 @@ def main():
 
     # ---- batched workload: 24 uneven cells, concurrent streams vs one stream
     batch = None
-    if args.batch:
+    if not args.no_batch and args.workload == "2x2x2":
         from paper_2404_09373_gb300 import batch as Bt
 
         cells = S.batch_cells()
-        res_c, wall_c = Bt.run_batch(cells, opts, n_streams=4)
-        res_s, wall_s = Bt.run_batch(cells, opts, n_streams=1)
-        same = all(np.array_equal(a["K"], b["K"]) for a, b in zip(res_c, res_s))
-        batch = {"cells": len(cells), "wall_s_concurrent": wall_c, "wall_s_one_stream": wall_s,
-                 "speedup": wall_s / wall_c, "identical_results": bool(same),
-                 "s_iter_per_cell_concurrent": (sum(r["t_isdf_s"] for r in res_s) / SCF_CHARGE +
-                                                sum(r["t_exchange_s"] for r in res_s)) / len(cells) * wall_c / wall_s}
+        res_c, tc = Bt.run_batch(cells, opts, n_streams=4, iterations=3)
+        res_1, t1 = Bt.run_batch(cells, opts, n_streams=1, iterations=1)
+        same = all(np.array_equal(a["pivots"], b["pivots"]) for a, b in zip(res_c, res_1))
+        dK = max(float(np.max(np.abs(a["K"] - b["K"]))) for a, b in zip(res_c, res_1))
+        t_k = statistics.mean(tc["exchange_replay_s"][1:])
+        batch = {"cells": len(cells), "sizes": "6 each of 1x1x1, 1x1x2, 1x2x2, 2x2x2 (sigma 0.1, N_ip = 6N)",
+                 "plan_batch_s": tc["plan_s"], "isdf_s_4_streams": tc["isdf_s"], "isdf_s_1_stream": t1["isdf_s"],
+                 "graph_capture_s": tc["capture_s"], "exchange_graph_replay_s": t_k,
+                 "s_iter_per_cell": ((tc["plan_s"] + tc["isdf_s"]) / SCF_CHARGE + t_k) / len(cells),
+                 "pivots_equal_4_vs_1_stream": bool(same), "max_abs_dK_4_vs_1_stream_Ha": dK,
+                 "autotuned_shapes": len(B.isdf_autotune_table())}
 
     # ---- per-kernel timing (separate profiled step, not part of the timed region)
     kern, roof = {}, None
@@ -641,7 +663,8 @@ def main():
         "config": gpu_config(args, workload, world),
         "stages_s": {k: statistics.mean(r[k] for r in res) for k in ("plan", "select", "fit", "coulomb", "exchange")},
         "Ex_per_atom": res[-1]["Ex"] / sysd["xyz"].shape[0],
-        "plain_fp64_gpu": plain, "occ_ri": occ_ri, "threshold_plan": thr, "learned": learned, "batch": batch,
+        "plain_fp64_gpu": plain, "occ_ri": occ_ri, "threshold_plan": thr, "coarse_sinc": sinc, "learned": learned,
+        "batch": batch,
         "speedup_vs_plain_fp64_gpu": (plain["s_iter"] / s_iter) if plain else None,
         "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
         "clocks": clk, "wall_s_timed": wall, "kernels": kern,

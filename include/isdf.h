@@ -128,7 +128,19 @@ typedef struct {
  *               greedy steps finish them until a pivot falls outside S.  The
  *               pivots are the same greedy ones (every decision is the argmax
  *               over all candidates' residuals with the same tie rule); only
- *               the rounding of the factor columns differs.  Default 0. */
+ *               the rounding of the factor columns differs.  Default 0.
+ *   coarse_sinc 1: the coarsest level is the paper's sparse universal grid
+ *               (Section III; Section III.A after Eq. 8): every one of its
+ *               points is an interpolation point with the grid's sinc
+ *               function as fitting function (Xi = I there), so the selection
+ *               and the fit run on the finer levels only and nip counts their
+ *               points; isdf_coulomb forms V over the fitted points plus
+ *               V_FU = (xi_P | sinc_g) (the fitted functions' potentials on
+ *               the coarse grid), and the coarse-coarse block (R_U|R_U') is
+ *               never formed: isdf_exchange applies it in Fourier space
+ *               (occ-RI over the coarse grid).  Needs nlevel >= 2; candidates
+ *               on the coarsest level are refused.  Not with isdf_save or
+ *               isdf_exchange_graph.  Default 0. */
 typedef struct {
   int precision;
   double tie_rel;
@@ -139,6 +151,7 @@ typedef struct {
   int prefilter;
   int profile;
   int select_block;
+  int coarse_sinc;
 } isdf_options;
 
 void isdf_options_default(isdf_options* opt);
@@ -293,6 +306,8 @@ enum {
   ISDF_GET_PHI_LEVEL0 = 10, /* double[|G_l| x N_g,l] basis values of level
                               0 (rows: functions of the level in index order,
                               then coarser ones); add the level index      */
+  ISDF_GET_V_COARSE = 7 + 16,     /* double[nip x N_g,coarsest]: V_FU of
+                                    options.coarse_sinc (after isdf_coulomb) */
   ISDF_GET_SELECT_STATS = 6 + 16 /* int64[2]: speculative blocks and
                               single steps of the last selection (0, 0 when
                               options.select_block = 0)                    */

@@ -17,7 +17,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libisdf.so")
-SOURCES = ["api.cu", "basis.cu", "select.cu", "dgemm.cu", "fit.cu", "coulomb.cu", "exchange.cu", "ozgemm.cu", "learn.cu", "fft.cu"]
+SOURCES = ["api.cu", "basis.cu", "select.cu", "dgemm.cu", "fit.cu", "coulomb.cu", "exchange.cu", "ozgemm.cu", "learn.cu", "fft.cu",
+           "sinc.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

@@ -185,6 +185,8 @@ void free_plan(Plan* p) {
   dfree(p->d_ozerr);
   dfree(p->d_perm);
   p->d_perm = nullptr;
+  dfree(p->VFU);
+  p->VFU = nullptr;
   p->d_ozerr = nullptr;
   p->d_diag = nullptr;
   p->d_selstate = nullptr;
@@ -273,6 +275,7 @@ isdf_status validate_options(const isdf_options* o, std::string& why) {
   if (o->col_batch < 0 || o->timeout_ms < 0) return bad("col_batch and timeout_ms must be >= 0");
   if (o->prefilter != 0 && o->prefilter != 1) return bad("prefilter must be 0 or 1");
   if (o->profile != 0 && o->profile != 1) return bad("profile must be 0 or 1");
+  if (o->coarse_sinc != 0 && o->coarse_sinc != 1) return bad("coarse_sinc must be 0 or 1");
   if (o->select_block < 0 || o->select_block > 256) return bad("select_block must be in [0, 256]");
   return ISDF_OK;
 }
@@ -291,6 +294,7 @@ void isdf_options_default(isdf_options* o) {
   o->tie_abs = 1e-13;
   o->reg_rel = 0.0;
   o->col_batch = 0;
+  o->coarse_sinc = 0;
   o->timeout_ms = 0;
   o->prefilter = 0;
   o->profile = 0;
@@ -318,6 +322,10 @@ isdf_status plan_create(const isdf_system* sys, const isdf_options* opt, void* s
   if (opt) o = *opt;
   if (validate_options(&o, why)) {
     g_plan_error = why;
+    return ISDF_ERR_ARG;
+  }
+  if (o.coarse_sinc && sys->nlevel < 2) {
+    g_plan_error = "options.coarse_sinc needs at least two grid levels";
     return ISDF_ERR_ARG;
   }
   isdf_plan_s* h = new (std::nothrow) isdf_plan_s();
@@ -440,7 +448,8 @@ isdf_status isdf_select_points(isdf_plan_t h, int nip, double tol, const int64_t
   Plan* p = &h->p;
   if (nip < 1 || !piv_out || !nip_out || !(tol >= 0.0) || (cand && ncand < 1) || (!cand && ncand != 0))
     return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_select_points");
-  if (nip > p->ntot) return fail(p, ISDF_ERR_ARG, "nip exceeds the number of grid points");
+  if (nip > (p->opt.coarse_sinc ? p->off[p->nlev - 1] : p->ntot))
+    return fail(p, ISDF_ERR_ARG, "nip exceeds the number of grid points that take part in the selection");
   std::vector<int64_t> cv;
   if (cand) {
     isdf_status st = to_host(p, cand, size_t(ncand), cv);
@@ -448,6 +457,8 @@ isdf_status isdf_select_points(isdf_plan_t h, int nip, double tol, const int64_t
     for (int64_t c : cv) {
       const int64_t l = c >> kPivShift, g = c & kPivMask;
       if (c < 0 || l >= p->nlev || g >= p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "candidate code out of range");
+      if (p->opt.coarse_sinc && l == p->nlev - 1)
+        return fail(p, ISDF_ERR_ARG, "with options.coarse_sinc the coarsest level has no candidates");
     }
   }
   int found = 0;
@@ -473,6 +484,8 @@ isdf_status isdf_fit(isdf_plan_t h, const int64_t* piv, int nip) {
   for (int64_t c : pv) {
     const int64_t l = c >> kPivShift, g = c & kPivMask;
     if (c < 0 || l >= p->nlev || g >= p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "pivot code out of range");
+    if (p->opt.coarse_sinc && l == p->nlev - 1)
+      return fail(p, ISDF_ERR_ARG, "with options.coarse_sinc every coarsest-level point is implicit: pass none");
     if (!seen.insert(c).second) return fail(p, ISDF_ERR_ARG, "duplicate pivot");
     per[l].push_back(g);
   }
@@ -623,7 +636,10 @@ isdf_status isdf_exchange_graph(isdf_plan_t* plans, int nplans, const int* n_occ
   }
   *out = nullptr;
   for (int i = 0; i < nplans; ++i)
-    if (!plans[i] || plans[i]->p.state < 3 || n_occ[i] < 1) {
+    if (plans[i] && plans[i]->p.opt.coarse_sinc) {
+      g_plan_error = "isdf_exchange_graph: plan " + std::to_string(i) + " uses options.coarse_sinc";
+      return ISDF_ERR_ARG;
+    } else if (!plans[i] || plans[i]->p.state < 3 || n_occ[i] < 1) {
       g_plan_error = "isdf_exchange_graph: plan " + std::to_string(i) + " needs isdf_coulomb first and n >= 1";
       return plans[i] ? ISDF_ERR_STATE : ISDF_ERR_ARG;
     }
@@ -663,25 +679,31 @@ isdf_status isdf_exchange_graph(isdf_plan_t* plans, int nplans, const int* n_occ
   cudaEvent_t fork = nullptr;
   cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
   g->ev.push_back(fork);
-  // one exchange per plan outside the capture: uploads each plan's level
-  // order and leaves every device-side state the captured run relies on
+  // one exchange per plan outside the capture, on the plan's own stream:
+  // uploads each plan's level order (a plan-owned buffer, freed with the
+  // plan on its stream) and fills the autotuner's table for these shapes
   for (size_t i = 0; i < g->plans.size(); ++i) {
     Plan* p = g->plans[i];
     double ex = 0.0;
-    const cudaStream_t keep = p->stream;
-    p->stream = g->branch[i];
     const isdf_status st = exchange_run(p, g->dC[i], g->n[i], occ ? nullptr : g->dOut[i], occ ? g->dOut[i] : nullptr, &ex);
-    p->stream = keep;
     if (st) return undo(st, "isdf_exchange_graph: plan " + std::to_string(i) + ": " + p->err);
   }
-  // capture: the stream forks into one branch per plan (every plan's exchange
-  // build is an independent chain of the graph) and joins again
+  // capture on a stream of the graph's own (the caller's stream may be the
+  // legacy default stream, which cannot be captured): it forks into one
+  // branch per plan (every plan's exchange build is an independent chain of
+  // the graph) and joins again
+  cudaStream_t cap = nullptr;
+  if ((e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking)) != cudaSuccess) {
+    cudaGetLastError();
+    return undo(ISDF_ERR_CUDA, std::string("isdf_exchange_graph: stream: ") + cudaGetErrorString(e));
+  }
+  g->branch.push_back(cap);  // destroyed with the graph
   cudaGraph_t graph = nullptr;
   const long long l0 = g_launches.load();
   isdf_status st = ISDF_OK;
   std::string why;
-  e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
-  if (e == cudaSuccess) e = cudaEventRecord(fork, g->stream);
+  e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaEventRecord(fork, cap);
   for (size_t i = 0; i < g->plans.size() && e == cudaSuccess && !st; ++i) {
     Plan* p = g->plans[i];
     e = cudaStreamWaitEvent(g->branch[i], fork, 0);
@@ -700,9 +722,9 @@ isdf_status isdf_exchange_graph(isdf_plan_t* plans, int nplans, const int* n_occ
     p->stream = keep;
     p->opt.profile = prof;
     if (!st) e = cudaEventRecord(g->ev[i], g->branch[i]);
-    if (!st && e == cudaSuccess) e = cudaStreamWaitEvent(g->stream, g->ev[i], 0);
+    if (!st && e == cudaSuccess) e = cudaStreamWaitEvent(cap, g->ev[i], 0);
   }
-  const cudaError_t e2 = cudaStreamEndCapture(g->stream, &graph);
+  const cudaError_t e2 = cudaStreamEndCapture(cap, &graph);
   if (e == cudaSuccess) e = e2;
   g->launches = g_launches.load() - l0;
   if (!st && e == cudaSuccess) e = cudaGraphInstantiate(&g->exec, graph, 0);
@@ -782,6 +804,7 @@ isdf_status isdf_save(isdf_plan_t h, const char* path) {
   Plan* p = &h->p;
   if (p->state < 3) return fail(p, ISDF_ERR_STATE, "isdf_save needs isdf_coulomb first");
   if (!path) return fail(p, ISDF_ERR_ARG, "isdf_save: path is NULL");
+  if (p->opt.coarse_sinc) return fail(p, ISDF_ERR_ARG, "isdf_save: options.coarse_sinc plans are not saved");
   const size_t nx = size_t(p->nfun) * p->nip, nv = size_t(p->nip) * p->nip;
   std::vector<double> xl(nx), xn(nx), v(nv);
   isdf_status st;
@@ -902,6 +925,8 @@ int64_t isdf_get_size(isdf_plan_t h, int what) {
       return p->state >= 2 ? 2 * p->nlev : 0;
     case ISDF_GET_SELECT_STATS:
       return p->state >= 1 ? 2 : 0;
+    case ISDF_GET_V_COARSE:
+      return (p->state >= 3 && p->VFU) ? int64_t(p->nip) * p->lev[p->nlev - 1].ng : 0;
     default:
       break;
   }
@@ -943,6 +968,8 @@ isdf_status isdf_get(isdf_plan_t h, int what, void* dst) {
       return put_host(p->piv_lo.data(), sizeof(int64_t) * p->piv_lo.size());
     case ISDF_GET_XL:
       return from_device(p, static_cast<double*>(dst), p->XL, size_t(n), true);
+    case ISDF_GET_V_COARSE:
+      return from_device(p, static_cast<double*>(dst), p->VFU, size_t(n), true);
     case ISDF_GET_XN:
       return from_device(p, static_cast<double*>(dst), p->XN, size_t(n), true);
     case ISDF_GET_V:

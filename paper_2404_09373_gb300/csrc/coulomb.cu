@@ -274,6 +274,37 @@ isdf_status apply_w(Plan* p) {
 
 }  // namespace
 
+void fold_spectra(int k, const double2* spf, int fx, int fy, int fz, double2* H, int cx, int cy, int cz,
+                  cudaStream_t s) {
+  const int64_t tot = int64_t(k) * (cx / 2 + 1) * cy * cz;
+  if (tot > 0) k_fold<<<unsigned((tot + 255) / 256), 256, 0, s>>>(k, spf, fx, fy, fz, H, cx, cy, cz);
+}
+
+isdf_status transform_real(Plan* p, const double* f, int nx, int ny, int nz, int64_t batch, double2* spec) {
+  cudaStream_t s = p->stream;
+  if (p->opt.precision == 1 && rfft3_df_supported(nx, ny, nz)) return rfft3_df(p, f, nx, ny, nz, batch, spec, s);
+  const int64_t ng = int64_t(nx) * ny * nz, nq = int64_t(nx / 2 + 1) * ny * nz;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  for (int64_t b0 = 0; b0 < batch;) {
+    const int nb = int(std::min<int64_t>(batch - b0, 4096));
+    const FftKey key{dev, nz, ny, nx, nb};
+    cufftHandle h = 0;
+    cufftResult r = fft_acquire(key, &h);
+    if (r != CUFFT_SUCCESS) return fail(p, ISDF_ERR_CUFFT, "cufftPlanMany failed (" + std::to_string(int(r)) + ")");
+    r = cufftSetStream(h, s);
+    if (r == CUFFT_SUCCESS)
+      r = cufftExecD2Z(h, const_cast<double*>(f) + b0 * ng, reinterpret_cast<cufftDoubleComplex*>(spec + b0 * nq));
+    const cudaError_t e = cudaStreamSynchronize(s);
+    fft_release(key, h);
+    if (r != CUFFT_SUCCESS) return fail(p, ISDF_ERR_CUFFT, "cufftExecD2Z failed (" + std::to_string(int(r)) + ")");
+    isdf_status st = cuda_check(p, e, "FFT");
+    if (st) return st;
+    b0 += nb;
+  }
+  return ISDF_OK;
+}
+
 isdf_status coulomb_run(Plan* p) {
   cudaStream_t s = p->stream;
   isdf_status st;
@@ -391,7 +422,9 @@ isdf_status coulomb_run(Plan* p) {
   // A factored fit (Xi = ZC W, W = R^-T R^-1) transformed ZC: V = W V_Z W
   bool factored = false;
   for (int l = 0; l < p->nlev; ++l) factored = factored || p->lev[l].zct != nullptr;
-  return factored ? apply_w(p) : ISDF_OK;
+  if (factored && (st = apply_w(p))) return st;
+  // the coarsest level as the universal sinc grid: V_FU (V_UU is never formed)
+  return p->opt.coarse_sinc ? sinc_coulomb(p) : ISDF_OK;
 }
 
 }  // namespace isdf

@@ -166,6 +166,11 @@ isdf_status tc_product(Plan* p, const double* a, int64_t M, int64_t sar, int64_t
 
 }  // namespace
 
+isdf_status tc_product5(Plan* p, const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t N,
+                        int64_t sbr, int64_t sbk, int64_t K, double* C, int64_t ldc) {
+  return tc_product(p, a, M, sar, sak, b, N, sbr, sbk, K, C, ldc, 0);
+}
+
 namespace {
 
 // C (M x N, ldc) = A B^T over sub-blocks, FP64 SIMT (precision 0) or
@@ -223,6 +228,14 @@ LevelOrder level_order(const Plan* p) {
 
 // dK: N x N exchange matrix (nullable); dKC: N x n occ-RI output K C (nullable).
 isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* dKC, double* Ex) {
+  if (p->opt.coarse_sinc && !dK) {
+    // the coarse-grid terms are built into K: the occ-RI output is K C
+    double* tk = nullptr;
+    isdf_status st = dalloc_t(p, &tk, size_t(p->nfun) * p->nfun, "K");
+    if (!st) st = exchange_run(p, dC, n, tk, dKC, Ex);
+    dfree(tk);
+    return st;
+  }
   cudaStream_t s = p->stream;
   const int64_t nip = p->nip, N = p->nfun, n2 = 2 * nip;
   const LevelOrder lo = level_order(p);
@@ -315,16 +328,28 @@ isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* d
       if (p->opt.precision == 1) {
         // T = W X2^T (rows of W against rows of X2), K = X2 T (rows of X2 against columns of T)
         if ((st = tc_product(p, W, n2, n2, 1, x2, N, n2, 1, n2, T, N, 0)) ||
-            (st = tc_product(p, x2, N, n2, 1, T, N, 1, N, n2, dK, N, 0)) ||
-            (st = tc_product(p, dK, N, N, 1, dC, n, 1, n, N, kc, n, 0))) {  // (K C)[mu][i]
+            (st = tc_product(p, x2, N, n2, 1, T, N, 1, N, n2, dK, N, 0))) {
           cleanup();
           return st;
         }
       } else {
         dgemm(gemm(0, 1, n2, N, n2, W, n2, x2, n2, T, N), s);  // T = W X2^T
         dgemm(gemm(0, 0, N, N, n2, x2, n2, T, N, dK, N), s);   // K = X2 T
-        dgemm(gemm(0, 0, N, n, N, dK, N, dC, n, kc, n), s);    // K C
       }
+      // the universal sinc grid's terms: K_FU + K_FU^T + K_UU
+      if (p->opt.coarse_sinc && (st = sinc_exchange(p, dC, yl, yg, n, dK))) {
+        cleanup();
+        return st;
+      }
+      if (p->opt.precision == 1) {
+        if ((st = tc_product(p, dK, N, N, 1, dC, n, 1, n, N, kc, n, 0))) {  // (K C)[mu][i]
+          cleanup();
+          return st;
+        }
+      } else {
+        dgemm(gemm(0, 0, N, n, N, dK, N, dC, n, kc, n), s);  // K C
+      }
+      if (dKC) cudaMemcpyAsync(dKC, kc, sizeof(double) * size_t(N) * n, cudaMemcpyDeviceToDevice, s);
     } else {
       // U = W [Y_L; Y_N]: rows of W against the columns i of Y2
       if ((st = block_product(p, W, n2, n2, 1, y2, n, 1, n, n2, u, n, false, tmp))) {

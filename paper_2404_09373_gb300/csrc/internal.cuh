@@ -106,6 +106,7 @@ struct Plan {
   // exchange), and the capture mode of isdf_exchange_graph (no host
   // synchronisation, no pageable copies, E_x written to *d_ex_slot)
   int* d_perm = nullptr;
+  double* VFU = nullptr;  // options.coarse_sinc: (xi_P | sinc_g) [nip][N_g of the coarsest level]
   bool capturing = false;
   double* d_ex_slot = nullptr;
   // profiling
@@ -148,6 +149,16 @@ isdf_status fit_run(Plan* p);                                        // fit.cu
 isdf_status fit_residual_run(Plan* p);  // fit.cu: residual statistics on request (precision 1)
 isdf_status fit_xi_run(Plan* p, int level);  // fit.cu: Xi^T of a level on request (precision 1)
 isdf_status coulomb_run(Plan* p);                                    // coulomb.cu
+// the coarsest level as the universal sinc grid (sinc.cu)
+isdf_status sinc_coulomb(Plan* p);
+isdf_status sinc_exchange(Plan* p, const double* dC, const double* yl, const double* yg, int n, double* dK);
+// coulomb.cu helpers shared with sinc.cu
+void fold_spectra(int k, const double2* spf, int fx, int fy, int fz, double2* H, int cx, int cy, int cz,
+                  cudaStream_t s);
+isdf_status transform_real(Plan* p, const double* f, int nx, int ny, int nz, int64_t batch, double2* spec);
+// 5-digit tensor-core product C = A B^T over strided operands (exchange.cu)
+isdf_status tc_product5(Plan* p, const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t N,
+                        int64_t sbr, int64_t sbk, int64_t K, double* C, int64_t ldc);
 // dK (N x N) and dKC (N x n, K C) are nullable; exchange.cu
 isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* dKC, double* Ex);
 isdf_status gather_pivot_factors(Plan* p);                           // basis.cu

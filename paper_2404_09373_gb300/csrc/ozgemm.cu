@@ -1053,8 +1053,8 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
 // (how many CTAs share one output tile's k range).  On the first product of
 // a shape (rows of A, rows of B, k tiles, digits, symmetric or not) outside
 // any graph capture, every admissible candidate runs on the real operands
-// (one warm-up, then the best of two timed runs, CUDA events on the product's
-// stream) and the fastest is cached for the process; the heuristic's choice
+// (one warm-up run, then one timed run per candidate, CUDA events on the
+// product's stream) and the fastest is cached for the process; the heuristic's choice
 // is among the candidates, and the chosen one runs last so C holds its
 // result.  Candidates whose split-K partials would exceed 2 GiB are skipped.
 
@@ -1098,7 +1098,7 @@ int oz_tuned_splits(Plan* p, const OzOperand& A, const OzOperand& B, double* C, 
       continue;
     }
     float ms = 1e30f;
-    for (int rep = 0; rep < 3; ++rep) {
+    for (int rep = (c == cand.front() ? 0 : 1); rep < 2; ++rep) {  // one warm-up run before the first candidate
       cudaEventRecord(e0, s);
       oz_gemm(A, B, C, ldc, trans, 1.0, 0, sym, c, work, err, s);
       cudaEventRecord(e1, s);

@@ -1478,6 +1478,9 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     dfree(d0);
     return r;
   };
+  // with the coarsest level as the universal sinc grid it takes no part in
+  // the selection: no candidates there, and d_0 is the finer levels' largest
+  const int nsel = p->opt.coarse_sinc ? p->nlev - 1 : p->nlev;
   int kl[ISDF_MAX_LEVELS];
   auto loop = [&](int* const* ci, const int64_t* n) {
     return p->opt.select_block > 0 ? select_loop_blocked(p, nip, tol, d0, ci, n, nfound, kl)
@@ -1501,14 +1504,14 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     return done(loop(cidx, nc));
   }
   if (!p->opt.prefilter) {
-    for (int l = 0; l < p->nlev; ++l) nc[l] = p->lev[l].ng;
+    for (int l = 0; l < p->nlev; ++l) nc[l] = l < nsel ? p->lev[l].ng : 0;
     return done(loop(cidx, nc));
   }
   // exact prefilter: tau relative to the largest initial residual d_0
   unsigned long long* dmax_slot = nullptr;
   if ((st = dalloc_t(p, &dmax_slot, 1, "max slot"))) return done(st);
   cudaMemsetAsync(dmax_slot, 0, sizeof(unsigned long long), s);
-  k_vec_max<<<152 * 4, 256, 0, s>>>(d0, p->ntot, dmax_slot);
+  k_vec_max<<<152 * 4, 256, 0, s>>>(d0, p->off[nsel], dmax_slot);
   count_launches(1);
   unsigned long long bits = 0;
   cudaMemcpyAsync(&bits, dmax_slot, sizeof(bits), cudaMemcpyDeviceToHost, s);
@@ -1523,6 +1526,10 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     free_cidx();
     for (int l = 0; l < p->nlev; ++l) {
       Level& lv = p->lev[l];
+      if (l >= nsel) {
+        nc[l] = 0;
+        continue;
+      }
       if (tau <= 0.0) {
         nc[l] = lv.ng;
         continue;
@@ -1558,7 +1565,7 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
       if (st) return done(st);
     }
     bool all_kept = true;
-    for (int l = 0; l < p->nlev; ++l) all_kept = all_kept && nc[l] == p->lev[l].ng;
+    for (int l = 0; l < nsel; ++l) all_kept = all_kept && nc[l] == p->lev[l].ng;
     if (all_kept) {  // nothing dropped: this is the full greedy run
       free_cidx();
       return done(loop(cidx, nc));

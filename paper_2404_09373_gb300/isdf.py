@@ -22,7 +22,7 @@ ISDF_OK, ISDF_ERR_ARG, ISDF_ERR_OOM, ISDF_ERR_NOT_PD, ISDF_ERR_CUDA, ISDF_ERR_CU
 STATUS_NAMES = ["OK", "ERR_ARG", "ERR_OOM", "ERR_NOT_PD", "ERR_CUDA", "ERR_CUFFT", "ERR_TIMEOUT", "ERR_STATE"]
 GET_NBASIS, GET_NIP_LEVEL, GET_PIVOTS, GET_XL, GET_XN, GET_V, GET_XI_LEVEL0 = 0, 1, 2, 3, 4, 5, 6
 GET_PHI_LEVEL0 = 10
-GET_NPOINTS, GET_FIT_RESIDUAL, GET_SELECT_STATS = 20, 21, 22
+GET_NPOINTS, GET_FIT_RESIDUAL, GET_SELECT_STATS, GET_V_COARSE = 20, 21, 22, 23
 # element type written by isdf_get for each selector (float64 otherwise)
 _GET_DTYPE = {GET_NBASIS: np.int32, GET_NIP_LEVEL: np.int32, GET_PIVOTS: np.int64, GET_NPOINTS: np.int64,
               GET_SELECT_STATS: np.int64}
@@ -89,6 +89,7 @@ class isdf_options(ctypes.Structure):
         ("prefilter", c_int),
         ("profile", c_int),
         ("select_block", c_int),
+        ("coarse_sinc", c_int),
     ]
 
 

@@ -376,3 +376,67 @@ def test_checkpoint_resume_gives_the_same_exchange(small, tmp_path, prec):
             assert e.value.status == B.ISDF_ERR_STATE  # the refused load changed nothing
         finally:
             plan.close()
+
+
+# --------------------------------------------------------------------------- coarse level as the universal sinc grid
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", ["three_levels", "two_levels"])
+def test_coarse_level_as_sinc_grid_matches_oracle(prec, case):
+    """options.coarse_sinc: every point of the coarsest grid is an
+    interpolation point with Xi = I (Section III; Section III.A after Eq. 8).
+    Pivots of the finer levels, the fitted block of V, V_FU = (xi_P|sinc_g),
+    K and E_x against the oracle's run_sinc; the coarse-coarse block of V is
+    never formed on the GPU (applied in Fourier space in the exchange)."""
+    if case == "three_levels":
+        sysd, C = S.small_multigrid(per_cell=(16, 8, 4), seed=5)
+        nip, natom = 200, 8
+    else:
+        rng = np.random.default_rng(2)
+        sysd = S.make_system((1, 1, 1), 0.05, rng, ((18, 18, 18), (10, 10, 10)), (0.5,))
+        C = S.make_orbitals(sysd, 8, rng)
+        nip, natom = 150, 8
+    o = oracle.run_sinc(sysd, C, nip)
+    k = o["pivots"].size
+    plan = B.isdf_plan(sysd, {"precision": prec, "coarse_sinc": 1, "prefilter": 1})
+    try:
+        piv, dv = B.isdf_select_points(plan, nip)
+        np.testing.assert_array_equal(piv, o["pivots"])
+        np.testing.assert_allclose(dv, o["dvals"], rtol=1e-9, atol=1e-14 * o["dvals"][0])
+        B.isdf_fit(plan, piv)
+        V = np.zeros((k, k))
+        B.isdf_coulomb(plan, V)
+        Vfu = B.isdf_get(plan, B.GET_V_COARSE).reshape(k, -1)
+        K, Ex = B.isdf_exchange(plan, C)
+        KC, Ex2 = B.isdf_exchange_occ(plan, C)
+    finally:
+        plan.close()
+    scale = np.abs(o["V"]).max()
+    vtol = 1e-9 if prec == 0 else 1e-6
+    assert np.max(np.abs(V - o["V"][:k, :k])) <= vtol * scale
+    assert np.max(np.abs(Vfu - o["V"][:k, k:])) <= vtol * scale
+    ktol = 1e-8 if prec == 0 else 1e-6
+    assert np.max(np.abs(K - o["K"])) <= ktol
+    assert abs(Ex - o["Ex"]) / natom <= ktol
+    assert np.max(np.abs(KC - o["K"] @ C)) <= ktol * np.max(np.sum(np.abs(C), axis=0))
+    assert abs(Ex2 - Ex) <= 1e-12 * abs(Ex)
+
+
+def test_coarse_sinc_refuses_coarse_pivots_and_candidates(small):
+    sysd, C, o = small
+    plan = B.isdf_plan(sysd, {"coarse_sinc": 1})
+    try:
+        coarse = (np.int64(2) << 40) | np.arange(3, dtype=np.int64)
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_select_points(plan, 10, cand=coarse)
+        assert e.value.status == B.ISDF_ERR_ARG
+        with pytest.raises(B.IsdfError) as e:
+            B.isdf_fit(plan, coarse)
+        assert e.value.status == B.ISDF_ERR_ARG
+    finally:
+        plan.close()
+    one = S.make_system((1, 1, 1), 0.0, None, ((8, 8, 8),), ())
+    with pytest.raises(B.IsdfError) as e:
+        B.isdf_plan(one, {"coarse_sinc": 1})
+    assert e.value.status == B.ISDF_ERR_ARG
