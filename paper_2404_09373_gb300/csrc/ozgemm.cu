@@ -80,8 +80,9 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-// Bounded wait: gives up after wait_ns of device time, after kWaitLimit polls,
-// or as soon as any CTA of the launch has recorded an error in *err.  The
+// Bounded wait: gives up after wait_ns of device time (0: after the first
+// unsuccessful try), after kWaitLimit polls, or as soon as any CTA of the
+// launch has recorded an error in *err.  The
 // pipeline waits take the launch's limit (kWaitNs unless a host-side fault
 // injection shortens it); the drain waits for copies and MMAs in flight
 // always take kWaitNs.
@@ -97,6 +98,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, const i
         : "r"(addr), "r"(phase)
         : "memory");
     if (done) return true;
+    if (wait_ns == 0) return false;  // a zero limit gives up after the first unsuccessful try
     if ((i & 255) == 0) {
       const unsigned long long now = globaltimer_ns();
       if (i == 0) t0 = now;
