@@ -54,9 +54,9 @@ def parse():
                     help="skip the 24-cell batch (6 each of 1x1x1, 1x1x2, 1x2x2, 2x2x2, sigma 0.1): one basis "
                          "launch for all cells, ISDF on 4 and on 1 concurrent streams, the exchange builds of all "
                          "cells as one captured CUDA graph")
-    ap.add_argument("--learned", type=int, default=0,
-                    help="train the point proposer on this many seeded 1x1x1/2x2x1 cells, then time the "
-                         "learned selection (4 N_ip candidates, fallback check) on the workload")
+    ap.add_argument("--learned", type=int, default=40,
+                    help="train the point proposer on this many seeded 1x1x1/2x2x1 cells (0: skip), then time the "
+                         "learned path on the workload: 1.2 N_ip points among 4x as many candidates, residual check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip the separately profiled step")
@@ -565,7 +565,9 @@ def main():
                 "Ex_per_atom": rs["Ex"] / sysd["xyz"].shape[0],
                 "dEx_per_atom_vs_fitted_coarse_Ha": abs(rs["Ex"] - res[-1]["Ex"]) / sysd["xyz"].shape[0]}
 
-    # ---- learned point proposal (trained here; reported beside the main number)
+    # ---- learned point proposal (trained here on a reduced set of cells; reported
+    # beside the main number): 1.2 N_ip points among 4x as many candidates; the
+    # residual trace (pair-fit error^2) of both paths measures their accuracy
     learned = None
     if args.learned > 0:
         from paper_2404_09373_gb300 import learn as Lr
@@ -580,19 +582,28 @@ def main():
         K_full = K_dev.clone()
         with torch.cuda.stream(stream):
             plan = B.isdf_plan(sysd, opts, stream=stream.cuda_stream)
-            te = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-            te[0].record(stream)
-            piv_l, info = Lr.select_learned(plan, params, nip, stats["level_density"], factor=4)
-            te[1].record(stream)
-            B.isdf_coulomb(plan)
-            te[2].record(stream)
-            _, ex_l = B.isdf_exchange(plan, C_dev, K_dev)
-            te[3].record(stream)
-        stream.synchronize()
-        plan.close()
+            p_f, _ = B.isdf_select_points(plan, nip)
+            B.isdf_fit(plan, p_f)
+            res_trace_full = float(B.isdf_get(plan, B.GET_FIT_RESIDUAL).reshape(-1, 2)[:, 1].sum())
+            plan.close()
+        for _ in range(2):  # the second pass is timed (the first meets new product shapes)
+            with torch.cuda.stream(stream):
+                plan = B.isdf_plan(sysd, opts, stream=stream.cuda_stream)
+                te = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+                te[0].record(stream)
+                piv_l, info = Lr.select_learned(plan, params, nip, stats["level_density"], factor=4)
+                te[1].record(stream)
+                B.isdf_coulomb(plan)
+                te[2].record(stream)
+                _, ex_l = B.isdf_exchange(plan, C_dev, K_dev)
+                te[3].record(stream)
+            stream.synchronize()
+            plan.close()
         tl = [te[i].elapsed_time(te[i + 1]) / 1e3 for i in range(3)]
         full_sel = statistics.mean(r["select"] for r in res)
         learned = {"train_cells": args.learned, "train_samples": int(X.shape[0]), "train_s": t_train,
+                   "n_selected": info["n_selected"], "residual_trace": info["residual_trace"],
+                   "residual_trace_full": res_trace_full,
                    "final_loss": losses[-1], "ncand": info["ncand"], "fallback": info["fallback"],
                    "residual_ratio": info["residual_ratio"], "t_select_s": info["t_select_s"],
                    "quota": info["quota"], "pivots_per_level": info["pivots_per_level"],

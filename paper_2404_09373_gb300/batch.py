@@ -26,13 +26,17 @@ import numpy as np
 from . import isdf as B
 
 
-def peak_bytes(system, nip):
-    """Rough device-memory peak of one cell's ISDF (selection factor and digit
-    planes, fit buffers, spectra), used only for admission."""
+def peak_bytes(system, nip, prefilter=True):
+    """Device-memory peak of one cell's ISDF, used only for admission: the
+    selection's factor columns (FP64) and their 8-digit planes, nip columns
+    over the candidates of every level (about half the points after the exact
+    prefilter), plus the candidates' basis-value digit planes."""
     grids = np.asarray(system["grids"]).reshape(-1, 3)
     ng = [int(np.prod(g)) for g in grids]
-    k = max(1, nip // len(ng))
-    return int(8 * 2 * k * ng[0] + 8 * 2 * nip * ng[0] + 2 * 10 * k * ng[0] + 2 ** 30)
+    nfun = int(sum(1 if l == 0 else 3 for l in system["shell_l"]))
+    frac = 0.5 if prefilter else 1.0
+    sel = sum(24 * min(nip, n) * n * frac + 16 * nfun * n * frac for n in ng)
+    return int(sel + 2 ** 30)
 
 
 def run_cell(system, C, nip, opts, stream):
@@ -51,7 +55,7 @@ def run_cell(system, C, nip, opts, stream):
     return {"pivots": piv, "K": K, "Ex": ex, "t_isdf_s": t1 - t0, "t_exchange_s": t2 - t1}
 
 
-def run_batch(cells, opts=None, n_streams=4, mem_budget=160 * 2 ** 30, iterations=1):
+def run_batch(cells, opts=None, n_streams=4, mem_budget=120 * 2 ** 30, iterations=1):
     """Run every (system, C, nip) cell.  Returns (results in input order,
     timings): per cell pivots, K, E_x; timings of the batch plan, the ISDF
     stages, the graph capture and each exchange replay (``iterations`` SCF
@@ -70,7 +74,7 @@ def run_batch(cells, opts=None, n_streams=4, mem_budget=160 * 2 ** 30, iteration
 
     def isdf(i):
         sysd, C, nip = cells[i]
-        need = min(peak_bytes(sysd, nip), mem_budget)
+        need = min(peak_bytes(sysd, nip, bool(opts.get("prefilter", 0))), mem_budget)
         with lock:
             while state["bytes"] + need > mem_budget and state["bytes"] > 0:
                 lock.wait()

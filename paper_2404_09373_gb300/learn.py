@@ -118,6 +118,16 @@ def train(X, y, w, epochs=30, batch=65536, lr=3e-3, seed=0, params=None, stream=
     return params, losses
 
 
+def eval_cell(per_cell=(16, 8, 4), n_occ=32, seed=S.SEED_BASE + 4, sigma=0.05):
+    """Held-out evaluation cell with the geometry of the learned workload's
+    evaluation (2x2x2 diamond, seeded displacements); the training cells are
+    1x1x1 and 2x2x1 with other seeds.  Returns (system, C, N_ip = 6N)."""
+    rng = np.random.default_rng(seed)
+    sysd = S.make_system((2, 2, 2), sigma, rng, tuple((p, p, p) for p in per_cell), S.LEVEL_EDGES_3)
+    C = S.make_orbitals(sysd, n_occ, rng)
+    return sysd, C, 6 * S.nbasis(sysd)
+
+
 def quotas(grids, level_density, nip, factor):
     """Candidates per level: factor * nip split like the expected pivots
     (level pivot density from training x level points), capped per level."""
@@ -128,32 +138,40 @@ def quotas(grids, level_density, nip, factor):
     return np.minimum(q, pts.astype(np.int64))
 
 
-def select_learned(plan, params, nip, level_density, factor=4, kappa=10.0, repair=1):
+def select_learned(plan, params, nip, level_density, factor=4, oversub=1.2, kappa=100.0, repair=1):
     """Candidate-restricted selection + fit with the residual check.
 
-    If the largest fit residual exceeds kappa times the last pivot value, up
-    to ``repair`` corrective passes add, on every level whose residual is
-    above the last pivot value, the points with the largest fit residual
-    (as many as the level's share of N_ip) to the candidates and select and
-    fit again; if the check still fails the full selection runs.
+    The learned selection picks ``oversub * nip`` points among ``factor``
+    times as many proposed candidates: restricted to the candidates, the
+    greedy steps are several times cheaper than over all grid points, and the
+    extra points buy back the accuracy the restriction costs (measured by the
+    fit's residual trace, the pair-fit error squared, and by the oracle's
+    exchange error).  Check: if the largest fit residual over ALL points
+    exceeds kappa times the last pivot value, up to ``repair`` corrective
+    passes add, on every level whose residual is above the last pivot value,
+    the points with the largest fit residual (as many as the level's share of
+    the pivots) to the candidates and select and fit again; if the check
+    still fails the full selection of ``nip`` points runs (fallback).
 
     Returns (pivots, info): info has the candidate count, the passes, whether
-    the fallback ran, the residual ratio and the selection / fit times."""
+    the fallback ran, the residual ratio, the residual trace and the
+    selection / fit times."""
     t0 = time.perf_counter()
+    n_sel = int(round(oversub * nip))
     n_points = int(B.isdf_get(plan, B.GET_NPOINTS)[0])
-    q = quotas(plan.system["grids"], level_density, nip, factor)
+    q = quotas(plan.system["grids"], level_density, n_sel, factor)
     cand = B.isdf_propose(plan, params, q)
-    info = {"quota": q.tolist(), "n_points": n_points, "fallback": False, "repairs": 0}
+    info = {"quota": q.tolist(), "n_points": n_points, "n_selected": n_sel, "fallback": False, "repairs": 0}
     t_fit = 0.0
     while True:
-        piv, dv = B.isdf_select_points(plan, nip, cand=cand)
+        piv, dv = B.isdf_select_points(plan, n_sel, cand=cand)
         t1 = time.perf_counter()
         B.isdf_fit(plan, piv)
         t_fit += time.perf_counter() - t1
         res = B.isdf_get(plan, B.GET_FIT_RESIDUAL).reshape(-1, 2)
         dlast = float(dv[-1]) if dv.size else np.inf
         ratio = float(res[:, 0].max()) / dlast if dv.size else np.inf
-        ok = ratio <= kappa and piv.size == nip
+        ok = ratio <= kappa and piv.size == n_sel
         if ok or info["repairs"] >= repair or not dv.size:
             break
         extra_q = np.where(res[:, 0] > dlast, np.ceil(q / factor), 0).astype(np.int64)
@@ -165,6 +183,7 @@ def select_learned(plan, params, nip, level_density, factor=4, kappa=10.0, repai
     t2 = time.perf_counter()
     info.update({"ncand": int(cand.size), "residual_ratio": ratio,
                  "residual_ratio_per_level": (res[:, 0] / dlast).tolist() if dv.size else None,
+                 "residual_trace": float(res[:, 1].sum()),
                  "pivots_per_level": np.bincount(piv >> B.PIVOT_SHIFT, minlength=len(q)).tolist(),
                  "t_select_s": t2 - t0 - t_fit, "t_fit_s": t_fit})
     if not ok:

@@ -1,16 +1,17 @@
 """Learned point proposer: kernels against the FP64 oracle network, features
 against NumPy, exact top-K, and what the trained network gains.
 
-The gain test trains on seeded displaced cells (labels = the full greedy
-selection's picks), then selects on a held-out cell from 4 N_ip candidates.
-Measure: the oracle's exchange error |K - K_nofit| (exact no-fit exchange), for
-the learned selection against the full one; an untrained network must trip
-the fallback check instead.
+The gain test trains on seeded displaced 1x1x1 / 2x2x1 cells (labels = the
+full greedy selection's picks) and evaluates on held-out 2x2x2 cells: the
+oracle's exact no-fit exchange judges the accuracy (learned path against the
+full selection), CUDA events the time per SCF iteration at full resolution;
+an untrained network must leave a larger residual ratio than the trained one.
 """
+import os
+
 import numpy as np
 import pytest
 
-import oracle
 from oracle import isdf as O
 from oracle import mlp as OM
 from paper_2404_09373_gb300 import isdf as B
@@ -135,45 +136,105 @@ def test_propose_returns_exact_top_k_in_order():
     np.testing.assert_array_equal(got, np.concatenate(ref))
 
 
-def test_learned_proposer_gain_measured_by_oracle_exchange_error():
-    per_cell = (24, 12, 6)
-    cells = Lr.training_cells(12, per_cell=per_cell)
-    stats = {}
-    X, y, w = Lr.collect(cells, neg_per_pos=20, stats=stats)
-    params, losses = Lr.train(X, y, w, epochs=40, batch=32768, lr=3e-3)
-    assert losses[-1] < 0.7 * losses[0]
-    # held-out evaluation cell of the same family
-    rng = np.random.default_rng(S.SEED_BASE + 4)
-    sysd = S.make_system((1, 1, 1), 0.05, rng, tuple((p, p, p) for p in per_cell), S.LEVEL_EDGES_3)
-    C = S.make_orbitals(sysd, 16, rng)
-    nip = 6 * S.nbasis(sysd)
-    Kn, _ = oracle.nofit_exchange(sysd, C)
+GOLD_EVAL = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "learned_eval_2x2x2.npz")
 
-    def finish(plan):
-        B.isdf_coulomb(plan)
-        return B.isdf_exchange(plan, C)[0]
 
-    plan = B.isdf_plan(sysd, {"precision": 1, "prefilter": 1})
+def _s_iter(t):
+    return (t["plan"] + t["select"] + t["fit"] + t["coulomb"]) / 7.0 + t["exchange"]
+
+
+def _timed_path(sysd, C, nip, opts, select):
+    """One pass of the path with CUDA events around each stage (s)."""
+    import torch
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    ev[0].record()
+    plan = B.isdf_plan(sysd, opts)
+    ev[1].record()
     try:
-        piv_full, _ = B.isdf_select_points(plan, nip)
-        B.isdf_fit(plan, piv_full)
-        K_full = finish(plan)
-        piv_l, info = Lr.select_learned(plan, params, nip, stats["level_density"], factor=4)
-        K_l = finish(plan)
-        untrained = Lr.init_params(123)
-        _, info_u = Lr.select_learned(plan, untrained, nip, stats["level_density"], factor=4)
+        select(plan)
+        ev[3].record()
+        B.isdf_coulomb(plan)
+        ev[4].record()
+        K, _ = B.isdf_exchange(plan, C)
+        ev[5].record()
+        torch.cuda.synchronize()
     finally:
         plan.close()
-    err_full = np.max(np.abs(K_full - Kn))
-    err_l = np.max(np.abs(K_l - Kn))
-    print(f"\nlearned proposer: ncand {info['ncand']} of {info['n_points']} points, residual ratio "
-          f"{info['residual_ratio']:.3g}, repairs {info['repairs']}, fallback {info['fallback']}; "
-          f"|K - K_nofit|: full {err_full:.3e}, "
-          f"learned {err_l:.3e}; untrained ratio {info_u['residual_ratio']:.3g} fallback {info_u['fallback']}")
+    t = [ev[0].elapsed_time(ev[1]), 0.0, ev[1].elapsed_time(ev[3]), 0.0, ev[3].elapsed_time(ev[4]),
+         ev[4].elapsed_time(ev[5])]
+    return {"plan": t[0] / 1e3, "select": t[2] / 1e3, "fit": 0.0, "coulomb": t[4] / 1e3, "exchange": t[5] / 1e3}, K
+
+
+def test_learned_proposer_gains_over_the_full_selection():
+    """What the trained network gains over the method without it (the full
+    pivoted selection of N_ip points).  The learned path selects 1.2 N_ip
+    points among 4x as many proposed candidates.
+
+    Accuracy, judged by the oracle: on the held-out 2x2x2 cell of the
+    evaluation geometry (seeded displacements sigma = 0.05, grids of 16 / 8 /
+    4 points per cell edge so that the oracle's exact no-fit exchange is
+    affordable; 32 orbitals), the learned path's exchange error
+    max|K - K_nofit| is no larger than the full selection's.
+    Speed: on the 2x2x2 workload at full resolution (96^3 / 48^3 / 24^3,
+    N_ip = 4992, 128 orbitals) the learned path's s/iter (ISDF / 7 +
+    exchange, CUDA events; the proposal, selection and fit of the learned
+    path inside) is lower than the full path's.
+    Training cells (1x1x1 and 2x2x1, other seeds) never include the
+    evaluation cells."""
+    gold = np.load(GOLD_EVAL)
+    opts = {"precision": 1, "prefilter": 1, "select_block": 96}
+    # ---- accuracy on the held-out cell (reduced resolution)
+    per_cell = (16, 8, 4)
+    stats = {}
+    X, y, w = Lr.collect(Lr.training_cells(24, per_cell=per_cell), neg_per_pos=20, stats=stats)
+    params, losses = Lr.train(X, y, w, epochs=40, batch=32768, lr=3e-3)
+    assert losses[-1] < 0.7 * losses[0]
+    sysd, C, nip = Lr.eval_cell(per_cell=per_cell)
+    Kn = gold["K"]
+    plan = B.isdf_plan(sysd, opts)
+    try:
+        piv, _ = B.isdf_select_points(plan, nip)
+        B.isdf_fit(plan, piv)
+        res_full = float(B.isdf_get(plan, B.GET_FIT_RESIDUAL).reshape(-1, 2)[:, 1].sum())
+        B.isdf_coulomb(plan)
+        K_full, _ = B.isdf_exchange(plan, C)
+        _, info = Lr.select_learned(plan, params, nip, stats["level_density"])
+        B.isdf_coulomb(plan)
+        K_l, _ = B.isdf_exchange(plan, C)
+        untrained = Lr.init_params(123)
+        _, info_u = Lr.select_learned(plan, untrained, nip, stats["level_density"], repair=0)
+    finally:
+        plan.close()
+    err_full = float(np.max(np.abs(K_full - Kn)))
+    err_l = float(np.max(np.abs(K_l - Kn)))
+    print(f"\nheld-out 2x2x2 ({per_cell} per cell): |K - K_nofit| full {err_full:.3e} (N_ip {nip}), learned "
+          f"{err_l:.3e} ({info['n_selected']} of {info['ncand']} candidates, ratio {info['residual_ratio']:.3g}, "
+          f"repairs {info['repairs']}, fallback {info['fallback']}); residual trace full {res_full:.4g}, learned "
+          f"{info['residual_trace']:.4g}; untrained ratio {info_u['residual_ratio']:.3g}")
     assert not info["fallback"]
-    assert info["ncand"] * 5 < info["n_points"]
-    assert err_l <= 2.0 * err_full + 1e-5
-    assert info_u["fallback"] or info_u["residual_ratio"] > info["residual_ratio"]
+    assert err_l <= err_full
+    assert info_u["residual_ratio"] > info["residual_ratio"]
+    # ---- speed at full resolution
+    stats48 = {}
+    X, y, w = Lr.collect(Lr.training_cells(40), neg_per_pos=20, stats=stats48)
+    params48, _ = Lr.train(X, y, w, epochs=30, batch=65536, lr=3e-3)
+    sysd, C, nip = S.config(2)
+
+    def full(plan):
+        p_, _ = B.isdf_select_points(plan, nip)
+        B.isdf_fit(plan, p_)
+
+    def learned(plan):
+        _, inf = Lr.select_learned(plan, params48, nip, stats48["level_density"])
+        assert not inf["fallback"]
+
+    for _ in range(2):  # the second pass of each is timed (the first meets new product shapes)
+        t_full, K_f = _timed_path(sysd, C, nip, opts, full)
+        t_l, K_l2 = _timed_path(sysd, C, nip, opts, learned)
+    print(f"2x2x2 full resolution: s/iter full {_s_iter(t_full):.4f}, learned {_s_iter(t_l):.4f}; "
+          f"max|K_learned - K_full| {np.max(np.abs(K_l2 - K_f)):.3e}")
+    assert _s_iter(t_l) < _s_iter(t_full)
 
 
 def test_propose_residual_returns_the_worst_represented_points():
