@@ -116,7 +116,12 @@ typedef struct {
  *               dropped; the call verifies that the last pivot value stays
  *               above tau plus the tie margin (then the result equals the
  *               full greedy one, residuals never grow) and otherwise repeats
- *               the selection with a lower tau
+ *               the selection with a lower tau (1e-5, 1e-6, 1e-9 d_0, then
+ *               none; the step-by-step form starts at 1e-6).  With
+ *               select_block > 0, candidates whose residual falls below tau
+ *               are dropped between blocks (same pivots, fewer candidates),
+ *               and an attempt stops as soon as a pivot value breaks the
+ *               certificate
  *   profile     1: time every kernel family with CUDA events on the plan's
  *               stream and count its algorithmic work (isdf_profile_json)
  *   select_block  0: the selection takes one step at a time (FP64 column of
@@ -308,9 +313,10 @@ enum {
                               then coarser ones); add the level index      */
   ISDF_GET_V_COARSE = 7 + 16,     /* double[nip x N_g,coarsest]: V_FU of
                                     options.coarse_sinc (after isdf_coulomb) */
-  ISDF_GET_SELECT_STATS = 6 + 16 /* int64[2]: speculative blocks and
-                              single steps of the last selection (0, 0 when
-                              options.select_block = 0)                    */
+  ISDF_GET_SELECT_STATS = 6 + 16 /* int64[3]: speculative blocks, single
+                              steps and candidate compactions of the last
+                              selection (0, 0, 0 when options.select_block
+                              = 0)                                         */
 };
 int64_t isdf_get_size(isdf_plan_t plan, int what);
 isdf_status isdf_get(isdf_plan_t plan, int what, void* dst);

@@ -924,7 +924,7 @@ int64_t isdf_get_size(isdf_plan_t h, int what) {
     case ISDF_GET_FIT_RESIDUAL:
       return p->state >= 2 ? 2 * p->nlev : 0;
     case ISDF_GET_SELECT_STATS:
-      return p->state >= 1 ? 2 : 0;
+      return p->state >= 1 ? 3 : 0;
     case ISDF_GET_V_COARSE:
       return (p->state >= 3 && p->VFU) ? int64_t(p->nip) * p->lev[p->nlev - 1].ng : 0;
     default:
@@ -984,7 +984,7 @@ isdf_status isdf_get(isdf_plan_t h, int what, void* dst) {
       return put_host(p->fit_resid, sizeof(double) * 2 * p->nlev);
     }
     case ISDF_GET_SELECT_STATS: {
-      const int64_t v[2] = {p->sel_blocks, p->sel_plain_steps};
+      const int64_t v[3] = {p->sel_blocks, p->sel_plain_steps, p->sel_compactions};
       return put_host(v, sizeof(v));
     }
     default:

@@ -89,6 +89,7 @@ struct Plan {
   double* d_dval = nullptr;
   int sel_cap = 0;
   int64_t sel_blocks = 0, sel_plain_steps = 0;  // speculative-block statistics of the last selection
+  int64_t sel_compactions = 0;                   // candidate compactions of the last selection
   // fit results, level-ordered pivots
   int nip = 0;
   int poff[ISDF_MAX_LEVELS + 1] = {0};

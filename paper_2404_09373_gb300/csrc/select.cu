@@ -1122,6 +1122,21 @@ __global__ void k_scatter_pos(const int* __restrict__ cidx, int64_t nc, int* __r
   if (t < nc) gpos[cidx[t]] = int(t);
 }
 
+// out[j] = in ? in[keep[j]] : keep[j]  (candidate grid indices after compaction)
+__global__ void k_map_idx(const int* __restrict__ in, const int* __restrict__ keep, int64_t n, int* __restrict__ out) {
+  const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (t < n) out[t] = in ? in[keep[t]] : keep[t];
+}
+
+// fac_new[c][j] = fac_old[c][keep[j]] for the first ncol columns
+__global__ void k_gather_cols(const double* __restrict__ fo, int64_t no, const int* __restrict__ keep, int64_t nn,
+                              int64_t ncol, double* __restrict__ fn) {
+  const int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (e >= nn * ncol) return;
+  const int64_t c = e / nn, j = e % nn;
+  fn[e] = fo[c * no + keep[j]];
+}
+
 constexpr int kSlices = 8;  // FP64-grade sliced products for the selection
 
 // Speculative-block form of select_loop (same result: every pivot is the
@@ -1129,12 +1144,27 @@ constexpr int kSlices = 8;  // FP64-grade sliced products for the selection
 // tensor-core products per level for the columns of S, then up to s greedy
 // steps replayed from a CUDA graph; a step whose pivot lies outside S ends the
 // block (if it was the block's first step, one ordinary step is taken).
+// tau > 0: the candidates are the points with initial residual >= tau (the
+// exact prefilter).  Residuals only shrink, so a candidate whose residual
+// falls below tau can never be picked while every pivot value stays above
+// tau plus the tie margin (the certificate select_run checks): between
+// blocks such candidates are dropped and every candidate-side array is
+// rebuilt for the rest, which changes no pivot and no column entry (rows
+// are computed independently, ties go to the smallest grid index either
+// way).  As soon as a pivot value breaks the certificate the attempt stops
+// (*aborted) so that select_run can retry with a lower tau.
 isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0full, int* const* cidx,
-                                const int64_t* nc, int* nfound, int* kl_out) {
+                                const int64_t* nc_in, int* nfound, int* kl_out, double tau, bool* aborted) {
   cudaStream_t s = p->stream;
   isdf_status st = ISDF_OK;
   const int smax = p->opt.select_block;
   const int nlev = p->nlev;
+  *aborted = false;
+  int64_t nc[ISDF_MAX_LEVELS] = {0, 0, 0, 0};
+  for (int l = 0; l < nlev; ++l) nc[l] = nc_in[l];
+  int* cur_cidx[ISDF_MAX_LEVELS] = {nullptr, nullptr, nullptr, nullptr};  // after compaction: owned here
+  for (int l = 0; l < nlev; ++l) cur_cidx[l] = cidx[l];
+  std::vector<int*> own_cidx;
   SelParams P{};
   P.nlev = nlev;
   P.coff[0] = 0;
@@ -1161,6 +1191,8 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
   cudaGraphExec_t exec = nullptr;
   void* sync_mem = nullptr;
   auto cleanup = [&]() {
+    for (int* q : own_cidx) dfree(q);
+    own_cidx.clear();
     for (int l = 0; l < nlev; ++l) {
       oz_free(lb[l].aL), oz_free(lb[l].aN), oz_free(lb[l].aF);
       oz_free(lb[l].bL), oz_free(lb[l].bN), oz_free(lb[l].bF);
@@ -1245,7 +1277,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
   P.tie_rel = p->opt.tie_rel;
   P.tie_abs = p->opt.tie_abs;
   P.timeout_ns = (unsigned long long)p->opt.timeout_ms * 1000000ull;
-  const int64_t nbk = (P.ntot + kCompactBlock - 1) / kCompactBlock;
+  int64_t nbk = (P.ntot + kCompactBlock - 1) / kCompactBlock;
   if ((st = dalloc_t(p, &counts, size_t(std::max<int64_t>(nbk, 1)), "block counts")) ||
       (st = dalloc_t(p, &nlist, 1, "list size")) ||
       (st = dalloc_t(p, &list, size_t(std::max<int64_t>(P.ntot, 1)), "local maxima")) ||
@@ -1311,6 +1343,119 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
     cudaGetLastError();
   }
 
+  // ---- exact compaction of the candidates below tau (see above)
+  int64_t since_compact = 0;
+  auto compact = [&]() -> isdf_status {
+    isdf_status cst;
+    // survivors per level (ordered compaction of {t : d[t] >= tau})
+    int64_t keep_n[ISDF_MAX_LEVELS] = {0, 0, 0, 0}, tot_old = 0, tot_new = 0;
+    std::vector<std::vector<int>> offs(nlev);
+    for (int l = 0; l < nlev; ++l) {
+      tot_old += nc[l];
+      if (!nc[l]) continue;
+      const int64_t nb = (nc[l] + kCompactBlock - 1) / kCompactBlock;
+      k_flag_count<<<unsigned(nb), kCompactBlock, 0, s>>>(P.d + P.coff[l], nc[l], tau, counts);
+      offs[l].resize(nb);
+      cudaMemcpyAsync(offs[l].data(), counts, sizeof(int) * nb, cudaMemcpyDeviceToHost, s);
+      if ((cst = cuda_check(p, cudaStreamSynchronize(s), "compaction counts"))) return cst;
+      int64_t acc = 0;
+      for (int64_t b = 0; b < nb; ++b) {
+        const int c = offs[l][b];
+        offs[l][b] = int(acc);
+        acc += c;
+      }
+      keep_n[l] = acc;
+      tot_new += acc;
+      count_launches(1);
+    }
+    // rebuild only when at least a fifth of the candidates would go
+    if (tot_new == 0 || 5 * tot_new > 4 * tot_old) return ISDF_OK;
+    double* dnew = nullptr;
+    if ((cst = dalloc_t(p, &dnew, size_t(tot_new), "residual diagonal"))) return cst;
+    int64_t coff_new[ISDF_MAX_LEVELS + 1] = {0};
+    for (int l = 0; l < nlev; ++l) coff_new[l + 1] = coff_new[l] + keep_n[l];
+    for (int l = 0; l < nlev; ++l) {
+      if (!nc[l]) continue;
+      Level& lv = p->lev[l];
+      LevBuf& b = lb[l];
+      const int64_t nn = keep_n[l], no = nc[l];
+      const int64_t nb = (no + kCompactBlock - 1) / kCompactBlock;
+      int *keep = nullptr, *ci = nullptr;
+      double *fnew = nullptr, *d0c = nullptr;
+      if (nn && ((cst = dalloc_t(p, &keep, size_t(nn), "compaction")) || (cst = dalloc_t(p, &ci, size_t(nn), "candidates")) ||
+                 (cst = dalloc_t(p, &fnew, size_t(std::max<int64_t>(lv.fac_cap * nn, 1)), "selection factor columns")) ||
+                 (cst = dalloc_t(p, &d0c, size_t(nn), "initial residuals")))) {
+        dfree(keep), dfree(ci), dfree(fnew), dfree(d0c), dfree(dnew);
+        return cst;
+      }
+      if (nn) {
+        cudaMemcpyAsync(counts, offs[l].data(), sizeof(int) * nb, cudaMemcpyHostToDevice, s);
+        k_compact<<<unsigned(nb), kCompactBlock, 0, s>>>(P.d + P.coff[l], no, tau, counts, keep);
+        k_map_idx<<<unsigned((nn + 255) / 256), 256, 0, s>>>(cur_cidx[l], keep, nn, ci);
+        k_gather_diag<<<unsigned((nn + 255) / 256), 256, 0, s>>>(P.d + P.coff[l], keep, nn, dnew + coff_new[l]);
+        if (h.kl[l] > 0)
+          k_gather_cols<<<unsigned((nn * h.kl[l] + 255) / 256), 256, 0, s>>>(lv.fac, no, keep, nn, h.kl[l], fnew);
+        k_gather_diag<<<unsigned((nn + 255) / 256), 256, 0, s>>>(d0full + p->off[l], ci, nn, d0c);
+        count_launches(5);
+      }
+      // grid -> candidate map
+      if (!b.gpos && (cst = dalloc_t(p, &b.gpos, size_t(lv.ng), "grid-to-candidate map"))) {
+        dfree(keep), dfree(ci), dfree(fnew), dfree(d0c), dfree(dnew);
+        return cst;
+      }
+      cudaMemsetAsync(b.gpos, 0xFF, sizeof(int) * size_t(lv.ng), s);
+      if (nn) {
+        k_scatter_pos<<<unsigned((nn + 255) / 256), 256, 0, s>>>(ci, nn, b.gpos);
+        count_launches(1);
+      }
+      // candidate-side digit planes for the survivors: basis values, then the
+      // factor columns so far (fixed scales from sqrt(d0), as at set-up)
+      auto setrows = [&](OzOperand& op, int64_t rows) {
+        op.rows = rows;
+        op.nrt = (rows + op.rt - 1) / op.rt;
+      };
+      setrows(b.aL, nn);
+      if (lv.nN > 0) setrows(b.aN, nn);
+      setrows(b.aF, nn);
+      if (nn) {
+        Prof pr(p, "select_slice", 8.0 * double(nn) * (lv.nG + h.kl[l]), "byte", 0);
+        if (lv.nL > 0) oz_slice_ex(lv.phi, 1, lv.ng, ci, b.aL, 0, b.aL.nkt * (kOzBK / 8), false, s);
+        if (lv.nN > 0)
+          oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, ci, b.aN, 0, b.aN.nkt * (kOzBK / 8), false, s);
+        const int64_t kst_keep = b.aF.kst;
+        cudaMemsetAsync(b.aF.tiles, 0, size_t(b.aF.nrt) * size_t(kst_keep) * kSlices * 128 * kOzBK * 2, s);
+        k_fac_exps<<<unsigned((b.aF.nrt * 128 + 255) / 256), 256, 0, s>>>(d0c, nn, b.aF.nrt * 128, b.aF.exps);
+        count_launches(1);
+        if (h.kl[l] > 0) oz_slice_ex(fnew, 1, nn, nullptr, b.aF, 0, (h.kl[l] + 7) / 8, true, s);
+      }
+      dfree(lv.fac);
+      lv.fac = fnew;
+      P.fac[l] = fnew;
+      cur_cidx[l] = ci;
+      if (ci) own_cidx.push_back(ci);
+      P.cidx[l] = ci;
+      Q.cidx[l] = ci;
+      Q.gpos[l] = b.gpos;
+      nc[l] = nn;
+      P.nc[l] = nn;
+      if ((cst = cuda_check(p, cudaStreamSynchronize(s), "compaction"))) {
+        dfree(keep), dfree(d0c), dfree(dnew);
+        return cst;
+      }
+      dfree(keep);
+      dfree(d0c);
+    }
+    dfree(p->d_diag);
+    p->d_diag = dnew;
+    P.d = dnew;
+    Q.d = dnew;
+    for (int l = 0; l <= nlev; ++l) P.coff[l] = Q.coff[l] = coff_new[l];
+    P.ntot = Q.ntot = coff_new[nlev];
+    BP.P = P;
+    since_compact = 0;
+    ++p->sel_compactions;
+    return ISDF_OK;
+  };
   int64_t nblocks = 0, nplain = 0;
   std::vector<int> hcount(ISDF_MAX_LEVELS + 1);
   while (true) {
@@ -1409,6 +1554,10 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
       p->pend.back().work = bytes;
     }
     if (h.err || h.final_ || h.k >= nip) break;
+    if (tau > 0.0 && h.dp * (1.0 - 2.0 * p->opt.tie_rel) - 2.0 * p->opt.tie_abs * h.d0 < tau) {
+      *aborted = true;  // a pivot value broke the certificate: retry with a lower tau
+      break;
+    }
     if (h.bsteps == 0) {
       // the greedy pivot was not in S: one ordinary step
       Prof pr(p, "select_loop", 0.0, "flop", 4);
@@ -1423,6 +1572,10 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
       if ((st = cuda_check(p, cudaStreamSynchronize(s), "plain step"))) return bail(st);
       if (h.err || h.final_ || h.k >= nip) break;
     }
+    if (tau > 0.0 && h.dp * (1.0 - 2.0 * p->opt.tie_rel) - 2.0 * p->opt.tie_abs * h.d0 < tau) {
+      *aborted = true;
+      break;
+    }
     // ---- 4. digits of the new factor columns (whole k tiles from the first changed one)
     {
       Prof pr(p, "select_slice", 0.0, "byte", nlev);
@@ -1433,6 +1586,12 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
         oz_slice_ex(p->lev[l].fac, 1, nc[l], nullptr, b.aF, b.sliced / 8, (h.kl[l] + 7) / 8, true, s);
         b.sliced = h.kl[l];
       }
+    }
+    // ---- 5. drop the candidates whose residual fell below tau (checked every
+    // other block; the graph of the non-cooperative form holds the old arrays)
+    if (tau > 0.0 && !exec && ++since_compact >= 2) {
+      if ((st = compact())) return bail(st);
+      nbk = (P.ntot + kCompactBlock - 1) / kCompactBlock;
     }
   }
   if ((st = oz_check(p))) return bail(st);
@@ -1482,8 +1641,11 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
   // the selection: no candidates there, and d_0 is the finer levels' largest
   const int nsel = p->opt.coarse_sinc ? p->nlev - 1 : p->nlev;
   int kl[ISDF_MAX_LEVELS];
-  auto loop = [&](int* const* ci, const int64_t* n) {
-    return p->opt.select_block > 0 ? select_loop_blocked(p, nip, tol, d0, ci, n, nfound, kl)
+  bool aborted = false;
+  p->sel_compactions = 0;
+  auto loop = [&](int* const* ci, const int64_t* n, double tau = 0.0) {
+    aborted = false;
+    return p->opt.select_block > 0 ? select_loop_blocked(p, nip, tol, d0, ci, n, nfound, kl, tau, &aborted)
                                    : select_loop(p, nip, tol, d0, ci, n, nfound, kl);
   };
   if (cand) {
@@ -1520,9 +1682,13 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
   if (st) return done(st);
   double dmax0;
   std::memcpy(&dmax0, &bits, sizeof(dmax0));
-  const double taus[3] = {1e-6, 1e-9, 0.0};
-  for (int attempt = 0; attempt < 3; ++attempt) {
-    const double tau = taus[attempt] * dmax0;
+  // attempts: the blocked form starts at 1e-5 d_0 (its candidates shrink as
+  // the residuals fall below tau, and an attempt whose pivot values break the
+  // certificate stops at once); the step-by-step form at 1e-6 d_0
+  const bool blocked = p->opt.select_block > 0;
+  const double taus[4] = {blocked ? 1e-5 : 1e-6, 1e-6, 1e-9, 0.0};
+  for (int attempt = blocked ? 0 : 1; attempt < 4; ++attempt) {
+    const double tau = (attempt == 0 ? taus[0] : taus[attempt]) * dmax0;
     free_cidx();
     for (int l = 0; l < p->nlev; ++l) {
       Level& lv = p->lev[l];
@@ -1570,8 +1736,9 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
       free_cidx();
       return done(loop(cidx, nc));
     }
-    st = loop(cidx, nc);
+    st = loop(cidx, nc, tau);
     if (st || tau <= 0.0) return done(st);
+    if (aborted) continue;
     // certificate: every step's tie threshold stayed above tau
     std::vector<double> dv(*nfound);
     cudaMemcpyAsync(dv.data(), p->d_dval, sizeof(double) * dv.size(), cudaMemcpyDeviceToHost, s);
