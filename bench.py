@@ -372,10 +372,8 @@ def gpu_config(args, workload, world):
 # DRAM traffic of a kernel family per unit of its algorithmic work, from one
 # ncu capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum
 # over the algorithmic bytes of the captured launches); absent where no capture
-# of the current kernel exists.  select_gemm: three full-size launches of the
-# 2x2x2 selection (persistent tile loop), ratio 2.21-2.29 (16-byte digit
-# planes streamed once).
-TRAFFIC_PER_WORK = {"select_gemm": 2.25}
+# of the current kernel exists.
+TRAFFIC_PER_WORK = {}
 
 
 # BF16 digit-pair products per FP64-equivalent flop: 5 digits (s + t <= 4) in

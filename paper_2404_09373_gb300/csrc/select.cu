@@ -971,6 +971,7 @@ __global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, St
   if (tid < ISDF_MAX_LEVELS) kl_sh[tid] = kb[tid] = st->kl[tid];
   __syncthreads();
   long long last = -1;  // global index of the previous step's pivot (its residual is zeroed next phase B)
+  double last_dp = st->dp;  // value of the last pivot taken (written back with the counters)
   int bsteps = 0, reason = 0;  // reason: 0 running, 1 block end, 2 final, 3 timeout, 4 barrier failure
   // Residual comparisons use the order-preserving integer keys of the values,
   // and the per-step scalars are formed by one thread per CTA: the FP64 unit
@@ -1044,6 +1045,7 @@ __global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, St
     }
     __syncthreads();
     if (k == 0) d0 = dmax;
+    last_dp = dp;
     if (gtid == 0) {
       const long long g = P.cidx[l] ? P.cidx[l][tp] : tp;
       P.piv[k] = ((long long)l << kPivShift) | g;
@@ -1101,6 +1103,7 @@ __global__ void __launch_bounds__(512) k_blk_steps(BlkParams B, SelState* st, St
   if (last >= 0 && gtid == 0) P.d[last] = 0.0;
   if (gtid == 0) {
     st->k = k;
+    st->dp = last_dp;
     for (int l = 0; l < ISDF_MAX_LEVELS; ++l) st->kl[l] = kl_sh[l];
     st->bsteps = bsteps;
     st->done = 1;

@@ -18,6 +18,7 @@ def _fake_peaks(monkeypatch):
 
 def test_hbm_family_dominant(monkeypatch):
     _fake_peaks(monkeypatch)
+    monkeypatch.setattr(bench, "TRAFFIC_PER_WORK", {"select_gemm": 2.0})
     kern = {
         "select_gemm": {"launches": 10, "ms": 40.0, "work": 1.0e11, "unit": "byte"},
         "coulomb_V": {"launches": 0, "ms": 20.0, "work": 1.0e15, "unit": "flop"},
