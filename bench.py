@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--nz", type=int, default=96)
     ap.add_argument("--batch-vectors", type=int, default=37)
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--minimal", action="store_true",
+                    help="only the warm-up and timed steps (for profiler launch lists): no plain-FP64, occ-RI, "
+                         "threshold, sinc, learned or batch runs, no e2e, CPU baseline or profiled step")
     ap.add_argument("--launch-summary", default=None, metavar="CSV",
                     help="summarise an ncu launch list (gpu__time_duration.sum, --csv) by kernel and exit")
     return ap.parse_args()
@@ -419,6 +422,9 @@ def roofline(kern, precision):
 
 def main():
     args = parse()
+    if args.minimal:
+        args.no_plain = args.no_e2e = args.no_cpu_baseline = args.no_profile = args.no_batch = True
+        args.learned = 0
     if args.launch_summary:
         return print_launch_summary(args.launch_summary)
     if args.probe == "gemm":
@@ -526,9 +532,11 @@ def main():
                  "dEx_per_atom_vs_fast_Ha": abs(r0["Ex"] - res[-1]["Ex"]) / sysd["xyz"].shape[0]}
 
     # ---- occ-RI output (K C without K) on the same workload, beside the exchange
-    step(occ=True)  # first call of the occ-RI shapes (the autotuner measures them)
-    r_occ = step(occ=True)
-    occ_ri = {"exchange_s": r_occ["exchange"], "exchange_occ_s": r_occ["exchange_occ"],
+    occ_ri = None
+    if not args.minimal:
+        step(occ=True)  # first call of the occ-RI shapes (the autotuner measures them)
+        r_occ = step(occ=True)
+    occ_ri = None if args.minimal else {"exchange_s": r_occ["exchange"], "exchange_occ_s": r_occ["exchange_occ"],
               "s_iter_occ": (r_occ["plan"] + r_occ["select"] + r_occ["fit"] + r_occ["coulomb"]) / SCF_CHARGE +
               r_occ["exchange_occ"],
               "max_abs_dKC_vs_KC_Ha": float((KC_dev - K_dev @ C_dev).abs().max()),
@@ -536,7 +544,7 @@ def main():
 
     # ---- threshold-driven plan: grids from eps_K (Section III, Eq. 6), N_ip from eps_ISDF
     thr = None
-    if args.workload == "2x2x2":
+    if args.workload == "2x2x2" and not args.minimal:
         sys_t = dict(sysd)
         sys_t["grids"] = B.isdf_grids_for_threshold(sysd, EPS_K).astype(np.int64)
         cap = int(1.25 * nip)
@@ -551,7 +559,7 @@ def main():
     # ---- the coarsest level as the universal sinc grid (all 24^3 points, Xi = I;
     # the finer levels keep the default run's number of fitted points)
     sinc = None
-    if args.workload == "2x2x2":
+    if args.workload == "2x2x2" and not args.minimal:
         nlv = res[-1]["nip_level"]
         nip_f = int(sum(nlv[:-1]))
         o_s = dict(opts, coarse_sinc=1)
@@ -618,6 +626,7 @@ def main():
         from paper_2404_09373_gb300 import batch as Bt
 
         cells = S.batch_cells()
+        torch.cuda.empty_cache()  # the batch plans allocate through the library's own pool
         res_c, tc = Bt.run_batch(cells, opts, n_streams=4, iterations=3)
         res_1, t1 = Bt.run_batch(cells, opts, n_streams=1, iterations=1)
         same = all(np.array_equal(a["pivots"], b["pivots"]) for a, b in zip(res_c, res_1))

@@ -28,15 +28,21 @@ from . import isdf as B
 
 def peak_bytes(system, nip, prefilter=True):
     """Device-memory peak of one cell's ISDF, used only for admission: the
-    selection's factor columns (FP64) and their 8-digit planes, nip columns
-    over the candidates of every level (about half the points after the exact
-    prefilter), plus the candidates' basis-value digit planes."""
+    larger of (a) the selection -- factor columns (FP64) and their 8-digit
+    planes, nip columns over the candidates of every level (about half the
+    points after the exact prefilter), the candidates' basis-value digit
+    planes -- and (b) the Coulomb stage on the finest level, with about half
+    the pivots there: ZC (FP64), its half spectra and the two 7-digit operands
+    of the spectra product."""
     grids = np.asarray(system["grids"]).reshape(-1, 3)
     ng = [int(np.prod(g)) for g in grids]
     nfun = int(sum(1 if l == 0 else 3 for l in system["shell_l"]))
     frac = 0.5 if prefilter else 1.0
     sel = sum(24 * min(nip, n) * n * frac + 16 * nfun * n * frac for n in ng)
-    return int(sel + 2 ** 30)
+    k = max(1, nip // 2)
+    nq = (int(grids[0][0]) // 2 + 1) * int(grids[0][1]) * int(grids[0][2])
+    coul = 8 * k * ng[0] + 16 * k * nq + 2 * 14 * k * 2 * nq
+    return int(max(sel, coul) + 2 ** 30)
 
 
 def run_cell(system, C, nip, opts, stream):

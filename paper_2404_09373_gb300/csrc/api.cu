@@ -109,6 +109,18 @@ isdf_status dalloc(Plan* p, void** ptr, size_t bytes, const char* what) {
     std::lock_guard<std::mutex> lock(g_alloc_mu);
     pool_setup();
     e = cudaMallocAsync(ptr, bytes, p->stream);
+    if (e == cudaErrorMemoryAllocation && !p->capturing) {
+      // the pool keeps freed memory (raised release threshold); when a large
+      // request finds it fragmented, give the unused part back once and retry
+      cudaGetLastError();
+      int dev = 0;
+      cudaMemPool_t pool;
+      if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+        cudaStreamSynchronize(p->stream);
+        cudaMemPoolTrimTo(pool, 0);
+        e = cudaMallocAsync(ptr, bytes, p->stream);
+      }
+    }
     if (e == cudaSuccess) g_async_owner[*ptr] = p->stream;
   } else {
     e = cudaMalloc(ptr, bytes);
