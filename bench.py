@@ -375,8 +375,11 @@ def gpu_config(args, workload, world):
 # DRAM traffic of a kernel family per unit of its algorithmic work, from one
 # ncu capture of the same kernel (dram__bytes_read.sum + dram__bytes_write.sum
 # over the algorithmic bytes of the captured launches); absent where no capture
-# of the current kernel exists.
-TRAFFIC_PER_WORK = {}
+# of the current kernel exists.  select_gemm: the 8-digit product with the
+# selection's launch shape on a probe of 262144 x 48 x 832 (3.51 GB read +
+# 0.11 GB written for 1.745 GB of FP64 operands: the 16-byte digit planes
+# read once).
+TRAFFIC_PER_WORK = {"select_gemm": 2.075}
 
 
 # BF16 digit-pair products per FP64-equivalent flop: 5 digits (s + t <= 4) in
@@ -506,10 +509,13 @@ def main():
     clocks = ClockSampler(local)
     clocks.start()
     l0 = B.isdf_kernel_launches()
+    # profiler range = the timed steps (ncu --profile-from-start off captures only these)
+    torch.cuda.cudart().cudaProfilerStart()
     tw0 = time.perf_counter()
     res = [step() for _ in range(args.steps)]
     barrier()
     wall = time.perf_counter() - tw0
+    torch.cuda.cudart().cudaProfilerStop()
     launches = B.isdf_kernel_launches() - l0
     clk = clocks.stop()
     per = [r["plan"] + r["select"] + r["fit"] + r["coulomb"] for r in res]
@@ -627,16 +633,16 @@ def main():
 
         cells = S.batch_cells()
         torch.cuda.empty_cache()  # the batch plans allocate through the library's own pool
-        res_c, tc = Bt.run_batch(cells, opts, n_streams=4, iterations=3)
+        res_c, tc = Bt.run_batch(cells, opts, n_streams=3, iterations=3)
         res_1, t1 = Bt.run_batch(cells, opts, n_streams=1, iterations=1)
         same = all(np.array_equal(a["pivots"], b["pivots"]) for a, b in zip(res_c, res_1))
         dK = max(float(np.max(np.abs(a["K"] - b["K"]))) for a, b in zip(res_c, res_1))
         t_k = statistics.mean(tc["exchange_replay_s"][1:])
         batch = {"cells": len(cells), "sizes": "6 each of 1x1x1, 1x1x2, 1x2x2, 2x2x2 (sigma 0.1, N_ip = 6N)",
-                 "plan_batch_s": tc["plan_s"], "isdf_s_4_streams": tc["isdf_s"], "isdf_s_1_stream": t1["isdf_s"],
+                 "plan_batch_s": tc["plan_s"], "isdf_s_3_streams": tc["isdf_s"], "isdf_s_1_stream": t1["isdf_s"],
                  "graph_capture_s": tc["capture_s"], "exchange_graph_replay_s": t_k,
                  "s_iter_per_cell": ((tc["plan_s"] + tc["isdf_s"]) / SCF_CHARGE + t_k) / len(cells),
-                 "pivots_equal_4_vs_1_stream": bool(same), "max_abs_dK_4_vs_1_stream_Ha": dK,
+                 "pivots_equal_3_vs_1_stream": bool(same), "max_abs_dK_3_vs_1_stream_Ha": dK,
                  "autotuned_shapes": len(B.isdf_autotune_table())}
 
     # ---- per-kernel timing (separate profiled step, not part of the timed region)

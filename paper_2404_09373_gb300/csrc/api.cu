@@ -116,7 +116,7 @@ isdf_status dalloc(Plan* p, void** ptr, size_t bytes, const char* what) {
       int dev = 0;
       cudaMemPool_t pool;
       if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
-        cudaStreamSynchronize(p->stream);
+        cudaDeviceSynchronize();  // frees pending on other streams complete first
         cudaMemPoolTrimTo(pool, 0);
         e = cudaMallocAsync(ptr, bytes, p->stream);
       }
@@ -426,6 +426,18 @@ isdf_status isdf_plan_batch(const isdf_system* systems, int ncells, const isdf_o
     return ISDF_ERR_ARG;
   }
   for (int i = 0; i < ncells; ++i) out[i] = nullptr;
+  // a batch is a new, large working set: give the memory the stream-ordered
+  // pool kept from earlier work back first, so the cells' buffers are not
+  // fragmented around it
+  {
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      cudaDeviceSynchronize();
+      cudaMemPoolTrimTo(pool, 0);
+    }
+    cudaGetLastError();
+  }
   std::vector<Plan*> plans;
   auto undo = [&](isdf_status st) {
     const std::string why = g_plan_error;
