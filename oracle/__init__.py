@@ -23,6 +23,9 @@ from .isdf import (  # noqa: F401
     run,
     run_sinc,
     coarse_points,
+    run_local,
+    local_grid,
+    local_radius,
     PIVOT_SHIFT,
 )
-from .nofit import nofit_exchange, brute_exchange  # noqa: F401
+from .nofit import nofit_exchange, brute_exchange, brute_exchange_local  # noqa: F401

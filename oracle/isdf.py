@@ -38,6 +38,17 @@ Readings of places where the paper is silent or garbled:
   R7 images: on an orthorhombic cell the image sum of a Cartesian Gaussian is
      taken over the box of lattice translations t (per axis) whose shifted
      centre A + t L lies within r_cut = sqrt(ln(1/image_tol)/alpha) of [0, L].
+  R10 local grids: alpha_min is the finest level's edge; atom A's grid is
+     the finest grid's points within r_max (Eq. 5) of A, taken from a box
+     around A's nearest grid index (local_grid); a box wider than the cell
+     is refused.
+  R11 local function sets: L_A = finest-level functions of A, N_A = finest-
+     level functions of atoms with a larger index plus all coarser functions
+     (a sharp-sharp product of two atoms is represented once, on the grid of
+     the lower-index atom; functions vanishing on the sphere are kept).
+  R12 local ISDF: per atom its own greedy (Eq. 2) with a cap and a threshold
+     relative to the atom's largest initial residual, its own fit (Eq. 3,
+     lambda per atom); the coarser levels are selected together as usual.
 """
 from __future__ import annotations
 
@@ -543,6 +554,145 @@ def run_sinc(system, C, nip, tol=0.0, tie_rel=1e-9, tie_abs=1e-13, reg_rel=1e-14
     return {"pivots": pivots, "dvals": None if sel is None else sel["dvals"], "all_pivots": allp,
             "order": level_ordered(allp, len(levels)), "levels": levels, "funcs": funcs, "Xi": Xi, "V": V,
             "XL": XL, "XN": XN, "K": K, "Ex": Ex}
+
+
+# ---------------------------------------------------------------------------
+# Atom-centred local dense grids (Section III, Eq. 5, the local ISDF of Eq. 7
+# on each atom's grid, Fig. Grids; readings R10-R12)
+# ---------------------------------------------------------------------------
+
+LOCAL_ATOM_SHIFT = 24  # local pivot code on level 0: (atom << 24) | box index
+
+
+def local_radius(alpha_min, eps_r):
+    """r_max = sqrt(-ln(eps_r) / alpha_min) (Eq. 5): beyond it a Gaussian of
+    exponent >= alpha_min has fallen below eps_r."""
+    return math.sqrt(-math.log(eps_r) / alpha_min)
+
+
+def local_grid(system, atom, r_max):
+    """The finest grid's points around one atom (reading R10).
+
+    Box: per axis the centre index c = floor(x / h + 1/2) and the half-width
+    r = floor(r_max / h) + 1, so every grid point within r_max of the atom is
+    inside; the box's points (i, j, k), i fastest, sit at the unwrapped
+    positions (c - r + i) h and map to the parent index (c - r + i) mod n.
+    Returns (box dims, parent index of every box point, sphere mask)."""
+    n = [int(v) for v in system["grids"][0]]
+    E = system["edges"]
+    x = system["xyz"][atom]
+    h = [E[a] / n[a] for a in range(3)]
+    c = [int(math.floor(x[a] / h[a] + 0.5)) for a in range(3)]
+    r = [int(math.floor(r_max / h[a])) + 1 for a in range(3)]
+    B = [2 * r[a] + 1 for a in range(3)]
+    if any(B[a] > n[a] for a in range(3)):
+        raise ValueError("local grid wider than the cell")
+    ax = [np.arange(B[a]) + c[a] - r[a] for a in range(3)]
+    K, J, I = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")  # box order: i fastest
+    d2 = (I * h[0] - x[0]) ** 2 + (J * h[1] - x[1]) ** 2 + (K * h[2] - x[2]) ** 2
+    parent = np.mod(I, n[0]) + n[0] * (np.mod(J, n[1]) + n[1] * np.mod(K, n[2]))
+    return B, parent.ravel().astype(np.int64), (d2 <= r_max * r_max).ravel()
+
+
+def local_sets(funcs, atom):
+    """(L_A, N_A) of one atom's grid (reading R11): L_A the finest-level
+    functions of the atom; N_A the finest-level functions of atoms with a
+    larger index and every function of the coarser levels."""
+    fl, fa = funcs["level"], funcs["atom"]
+    L = np.flatnonzero((fl == 0) & (fa == atom))
+    N = np.flatnonzero(((fl == 0) & (fa > atom)) | (fl > 0))
+    return L, N
+
+
+def local_blocks(system, funcs, eps_r):
+    """Per atom the block data of its local grid: the sphere's points (box
+    order), their parent indices, Phi_L and Phi_N there, w = dV of the finest
+    grid.  alpha_min is the finest level's edge (every function of level 0 has
+    alpha >= alpha_min)."""
+    r_max = local_radius(float(system["level_min_exp"][0]), eps_r)
+    nfun = funcs["level"].shape[0]
+    Phi0 = basis_on_level(system, funcs, np.arange(nfun), 0)
+    out = []
+    for A in range(system["xyz"].shape[0]):
+        B, parent, inside = local_grid(system, A, r_max)
+        L, N = local_sets(funcs, A)
+        pts = parent[inside]
+        out.append({"L": L, "N": N, "PhiL": Phi0[L][:, pts], "PhiN": Phi0[N][:, pts], "w": level_weight(system, 0),
+                    "box": B, "box_index": np.flatnonzero(inside).astype(np.int64), "parent": pts})
+    return out, r_max
+
+
+def run_local(system, C, nip, tol=0.0, local_tol=1e-8, local_cap=64, eps_r=1e-5, sinc=False, tie_rel=1e-9,
+              tie_abs=1e-13, reg_rel=1e-14):
+    """Multigrid ISDF with the finest level on atom-centred local grids.
+
+    Per atom (reading R12): the greedy pivoted Cholesky of Eq. 2 on its own
+    block w M_A over the sphere's points, at most ``local_cap`` pivots,
+    stopping once the largest residual is below ``local_tol`` times the atom's
+    largest initial residual; the least-squares fit of Eq. 3 on the block.
+    The coarser levels are selected together by the usual greedy (``nip``
+    pivots, ``tol``) and fitted as usual; with ``sinc`` the coarsest of them
+    is the universal sinc grid (Xi = I, see run_sinc).  The local xi_A are
+    zero off their sphere; placed on the finest full grid they enter the
+    Coulomb matrix of Eq. 1 like any finest-level vector, and K follows from
+    Eq. 8 with X^L_{mu P} = phi_mu(P) for mu in L_A and X^N for mu in N_A.
+    Pivot codes: (atom << 24) | box index on level 0, then (level << 40) | g.
+    """
+    funcs = expand_functions(system)
+    nlev = len(system["grids"])
+    blocks, r_max = local_blocks(system, funcs, eps_r)
+    levels = _level_data(system, funcs)
+    hi = nlev - 1 if sinc else nlev
+    # local selections and fits, atom by atom
+    loc_codes, loc_dv, Xi0_cols, XL_cols, XN_cols = [], [], [], [], []
+    nfun = funcs["level"].shape[0]
+    ng0 = int(np.prod(system["grids"][0]))
+    Phi0 = basis_on_level(system, funcs, np.arange(nfun), 0)
+    for A, blk in enumerate(blocks):
+        sel = select_points([blk], local_cap, local_tol, tie_rel, tie_abs)
+        P = sel["pivots"] & ((1 << PIVOT_SHIFT) - 1)  # indices into the sphere's points
+        loc_codes += [(A << LOCAL_ATOM_SHIFT) | int(blk["box_index"][i]) for i in P]
+        loc_dv += list(sel["dvals"])
+        Xi_A = fit([blk], P, reg_rel)[0]
+        emb = np.zeros((ng0, P.size))
+        emb[blk["parent"], :] = Xi_A
+        Xi0_cols.append(emb)
+        g = blk["parent"][P]
+        xl = np.zeros((nfun, P.size))
+        xn = np.zeros((nfun, P.size))
+        xl[blk["L"]] = Phi0[blk["L"]][:, g]
+        xn[blk["N"]] = Phi0[blk["N"]][:, g]
+        XL_cols.append(xl)
+        XN_cols.append(xn)
+    # the full-cell levels
+    main = levels[1:hi]
+    sel = select_points(main, nip, tol, tie_rel, tie_abs)
+    mp = sel["pivots"]
+    main_codes = ((mp >> PIVOT_SHIFT) + 1) << PIVOT_SHIFT | (mp & ((1 << PIVOT_SHIFT) - 1))
+    Xi = [np.concatenate(Xi0_cols, axis=1)] + fit(main, mp, reg_rel)
+    per = split_pivots(main_codes, nlev)
+    if sinc:
+        Xi.append(np.eye(int(np.prod(system["grids"][-1]))))
+        per[-1] = np.arange(int(np.prod(system["grids"][-1])), dtype=np.int64)
+    V = coulomb(system, Xi)
+    XL = [np.concatenate(XL_cols, axis=1)]
+    XN = [np.concatenate(XN_cols, axis=1)]
+    for lev in range(1, nlev):
+        P = per[lev]
+        L, N, _ = level_sets(funcs, lev)
+        xl = np.zeros((nfun, P.size))
+        xn = np.zeros((nfun, P.size))
+        if P.size:
+            xl[L] = basis_on_level(system, funcs, L, lev)[:, P]
+            xn[N] = basis_on_level(system, funcs, N, lev)[:, P]
+        XL.append(xl)
+        XN.append(xn)
+    XL = np.concatenate(XL, axis=1)
+    XN = np.concatenate(XN, axis=1)
+    K, Ex = exchange(XL, XN, V, C)
+    return {"local_pivots": np.array(loc_codes, dtype=np.int64), "local_dvals": np.array(loc_dv),
+            "pivots": main_codes, "dvals": sel["dvals"], "blocks": blocks, "r_max": r_max, "funcs": funcs,
+            "Xi": Xi, "V": V, "XL": XL, "XN": XN, "K": K, "Ex": Ex}
 
 
 # ---------------------------------------------------------------------------

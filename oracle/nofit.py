@@ -11,14 +11,21 @@ TEST INFRASTRUCTURE ONLY.  Two independent routes to the same matrix:
   * ``brute_exchange`` forms every pair density on its own level, builds the
     full 4-index tensor (mu lam|sig nu) by FFT and contracts it with D.
 
-Both use the Coulomb rule of the oracle (reading R5).  They pin the ISDF
+``brute_exchange_local`` is the same 4-index construction for the local
+grids of Section III: a product with a finest-level (sharp) factor lives on
+the finest grid, cut to the sphere of radius r_max (Eq. 5) around its owner
+atom -- the sharp factor's atom, the lower index of the two when both are
+sharp (reading R11) -- and every other product on its level as above.
+
+All use the Coulomb rule of the oracle (reading R5).  They pin the ISDF
 oracle from outside: with N_ip at the pair-space rank ISDF must reproduce them.
 """
 from __future__ import annotations
 
 import numpy as np
 
-from .isdf import basis_on_level, coulomb_pair, expand_functions, fourier_coeffs, level_sets
+from .isdf import (basis_on_level, coulomb_pair, expand_functions, fourier_coeffs, level_sets, local_grid,
+                   local_radius)
 
 
 def _coul(Fa, la, Fb, lb, system):
@@ -85,3 +92,42 @@ def brute_exchange(system, C):
     D = C @ C.T
     K = np.einsum("ls,mlsn->mn", D, eri)
     return K, -float(np.sum(D * K)), eri
+
+
+def brute_exchange_local(system, C, eps_r):
+    """K from the 4-index tensor of the local-grid pair partition (tiny cells).
+    Built pair by pair from its definition, with no ISDF and no L/N sets."""
+    funcs = expand_functions(system)
+    nfun = funcs["level"].shape[0]
+    nlev = len(system["grids"])
+    fl, fa = funcs["level"], funcs["atom"]
+    Phi = [basis_on_level(system, funcs, np.arange(nfun), lev) for lev in range(nlev)]
+    r_max = local_radius(float(system["level_min_exp"][0]), eps_r)
+    ng0 = Phi[0].shape[1]
+    sphere = []
+    for A in range(system["xyz"].shape[0]):
+        _, parent, inside = local_grid(system, A, r_max)
+        m = np.zeros(ng0, dtype=bool)
+        m[parent[inside]] = True
+        sphere.append(m)
+    pairs = [(m, l) for m in range(nfun) for l in range(nfun)]
+    rho = {lev: [] for lev in range(nlev)}
+    idx = {lev: [] for lev in range(nlev)}
+    for q, (m, l) in enumerate(pairs):
+        lev = min(fl[m], fl[l])
+        r = Phi[lev][m] * Phi[lev][l]
+        if lev == 0:
+            owners = [fa[x] for x in (m, l) if fl[x] == 0]
+            r = np.where(sphere[min(owners)], r, 0.0)
+        rho[lev].append(r)
+        idx[lev].append(q)
+    F = {lev: fourier_coeffs(np.stack(rho[lev], axis=0).T, system["grids"][lev]) for lev in range(nlev) if idx[lev]}
+    npair = len(pairs)
+    eri = np.zeros((npair, npair))
+    for la in F:
+        for lb in F:
+            eri[np.ix_(idx[la], idx[lb])] = _coul(F[la], la, F[lb], lb, system)
+    eri = eri.reshape(nfun, nfun, nfun, nfun)
+    D = C @ C.T
+    K = np.einsum("ls,mlsn->mn", D, eri)
+    return K, -float(np.sum(D * K))

@@ -626,3 +626,103 @@ def test_sinc_coarse_coulomb_block_is_a_circulant():
     ev = np.linalg.eigvalsh(Vu)
     assert ev.min() >= -1e-10 * ev.max()
     assert np.max(np.abs(Vu @ np.ones(n ** 3))) <= 1e-10 * np.abs(Vu).max()
+
+
+# --------------------------------------------------------------------------- atom-centred local grids (Section III)
+
+
+def test_local_radius_closed_form():
+    """Eq. 5 at the paper's own thresholds: eps_r = 1e-5, alpha_min = 2.8
+    bohr^-2 gives r_max = sqrt(ln(1e5) / 2.8) = 2.0277... bohr."""
+    assert abs(O.local_radius(2.8, 1e-5) - 2.027748) <= 1e-6
+    # a Gaussian of exponent alpha_min has fallen to eps_r exactly at r_max
+    r = O.local_radius(1.6, 1e-3)
+    assert abs(math.exp(-1.6 * r * r) - 1e-3) <= 1e-15
+
+
+@pytest.mark.parametrize("a,n,atom", [(4.5, 16, 0), (4.5, 16, 1), (6.74, 24, 1)])
+def test_local_grid_is_the_minimum_image_sphere(a, n, atom):
+    """The box construction returns exactly the finest-grid points whose
+    minimum-image distance to the atom is at most r_max (brute force over
+    every point of the cell), each once."""
+    sysd = tiny(levels=2, n=(n, n // 2), sites=TWO_ATOMS, a=a)
+    r_max = O.local_radius(1.6, 1e-2)
+    B, parent, inside = O.local_grid(sysd, atom, r_max)
+    got = np.sort(parent[inside])
+    assert np.unique(got).size == got.size
+    h = a / n
+    idx = np.arange(n ** 3)
+    pos = np.stack([idx % n, (idx // n) % n, idx // (n * n)], axis=1) * h
+    d = pos - sysd["xyz"][atom]
+    d -= a * np.round(d / a)
+    want = np.flatnonzero(np.sum(d * d, axis=1) <= r_max * r_max)
+    assert np.array_equal(got, want)
+
+
+CLOSE_ATOMS = np.array([[0.1, 0.2, 0.3], [0.3, 0.35, 0.45]])  # 1.3 bohr apart at a = 4.5
+
+
+def _local_case(levels=2):
+    sysd = tiny(levels=levels, n=(16, 8, 4), sites=CLOSE_ATOMS, a=4.5)
+    return sysd, orbitals(sysd)
+
+
+@pytest.mark.parametrize("levels", [2, 3])
+def test_local_isdf_exact_at_full_rank(levels):
+    """With every atom's local ISDF and the coarser levels at full pair rank,
+    the four-term exchange reproduces the 4-index tensor of the local pair
+    partition built pair by pair (brute_exchange_local).  The agreement is
+    limited by the conditioning of the full-rank fits (about 1e-9 of max|K|);
+    a wrong pair partition is off by 1e-3 or more (next test)."""
+    sysd, C = _local_case(levels)
+    Kb, Eb = oracle.brute_exchange_local(sysd, C, 1e-2)
+    r = oracle.run_local(sysd, C, 400, tol=1e-14, local_tol=1e-14, local_cap=400, eps_r=1e-2, reg_rel=0.0)
+    assert np.max(np.abs(r["K"] - Kb)) <= 2e-8 * np.max(np.abs(Kb))
+    assert abs(r["Ex"] - Eb) <= 2e-8 * abs(Eb)
+
+
+@pytest.mark.parametrize("slip", ["double", "missing"])
+def test_planted_mistake_in_the_local_sets_is_caught(monkeypatch, slip):
+    """N_A holding the sharp functions of every other atom (the pair counted
+    on both atoms' grids) or of none (the pair dropped) breaks the pin."""
+    sysd, C = _local_case(2)
+    Kb, _ = oracle.brute_exchange_local(sysd, C, 1e-2)
+
+    def wrong(funcs, atom):
+        fl, fa = funcs["level"], funcs["atom"]
+        L = np.flatnonzero((fl == 0) & (fa == atom))
+        other = (fl == 0) & (fa != atom) if slip == "double" else np.zeros_like(fl, dtype=bool)
+        return L, np.flatnonzero(other | (fl > 0))
+
+    monkeypatch.setattr(O, "local_sets", wrong)
+    r = oracle.run_local(sysd, C, 400, tol=1e-14, local_tol=1e-14, local_cap=400, eps_r=1e-2, reg_rel=1e-12)
+    assert np.max(np.abs(r["K"] - Kb)) > 1e-3 * np.max(np.abs(Kb))
+
+
+def test_local_partition_tends_to_the_full_cell_partition():
+    """As eps_r falls the spheres take in the sharp products' tails and the
+    local partition's exact exchange approaches the full-cell one."""
+    sysd, C = _local_case(2)
+    Kn, _ = oracle.nofit_exchange(sysd, C)
+    errs = [np.max(np.abs(oracle.brute_exchange_local(sysd, C, e)[0] - Kn)) for e in (1e-1, 1e-2, 5e-3)]
+    assert errs[1] < 0.2 * errs[0] and errs[2] < 0.6 * errs[1]
+    assert errs[2] < 2e-3 * np.max(np.abs(Kn))
+
+
+def test_local_selection_threshold_is_relative_per_atom():
+    """The local selection stops on each atom once its largest residual falls
+    below local_tol times that atom's own largest initial residual: the last
+    pivot value of every atom sits above the threshold and the atom's
+    remaining residual below it (or the cap was reached)."""
+    sysd, C = _local_case(2)
+    tol = 1e-6
+    r = oracle.run_local(sysd, C, 20, local_tol=tol, local_cap=400, eps_r=1e-2)
+    codes = r["local_pivots"]
+    atoms = codes >> O.LOCAL_ATOM_SHIFT
+    for A, blk in enumerate(r["blocks"]):
+        dv = r["local_dvals"][atoms == A]
+        d0 = np.max(O.initial_diagonal(blk))
+        assert dv.size and dv[0] == pytest.approx(d0)
+        assert np.all(dv >= tol * d0)
+        sel = O.select_points([blk], dv.size + 1, 0.0)
+        assert sel["dvals"][-1] < tol * d0
