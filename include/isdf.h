@@ -145,7 +145,35 @@ typedef struct {
  *               never formed: isdf_exchange applies it in Fourier space
  *               (occ-RI over the coarse grid).  Needs nlevel >= 2; candidates
  *               on the coarsest level are refused.  Not with isdf_save or
- *               isdf_exchange_graph.  Default 0. */
+ *               isdf_exchange_graph.  Default 0.
+ *   local_grids 1: the finest level on atom-centred local dense grids
+ *               (Section III, Eq. 5, Fig. Grids).  Atom A's grid is the
+ *               finest grid's points within r_max = sqrt(-ln(local_eps_r) /
+ *               alpha_min) of A, alpha_min = level_min_exp[0] (every
+ *               finest-level function has alpha >= alpha_min), taken from a
+ *               box of (2 r + 1)^3 points, r = floor(r_max / h) + 1 per axis,
+ *               centred on A's nearest grid index floor(x / h + 1/2); box
+ *               point (i, j, k), i fastest, is the parent point
+ *               (c - r + i) mod n per axis.  On it L_A = the finest-level
+ *               functions of A and N_A = the finest-level functions of atoms
+ *               with a larger index plus every coarser function (a sharp
+ *               product of two atoms lives on the lower-index atom's grid).
+ *               Each atom runs its own greedy selection (Eq. 2 on w M_A, w the
+ *               finest volume element; at most local_cap pivots, stopping
+ *               once the largest residual is below local_tol times the atom's
+ *               largest initial residual) and its own fit (Eq. 3, lambda per
+ *               atom); the xi_A, zero off the sphere, are placed on the full
+ *               finest grid for the Coulomb matrix.  isdf_select_points then
+ *               runs the usual greedy on the coarser levels (nip and tol count
+ *               those; with coarse_sinc the coarsest is the sinc grid) and
+ *               returns the local pivots first, atom by atom: piv_out and
+ *               dval_out must hold nip + natom * local_cap values.  Local
+ *               pivot code: level 0, (atom << 24) | box index.  Needs
+ *               nlevel >= 2, a box no wider than the cell, at most 255 box
+ *               points per axis and 65535 atoms.  Not with isdf_save or the
+ *               learned proposal.  Default 0.
+ *   local_eps_r, local_tol, local_cap   defaults 1e-5 (the paper's eps_r),
+ *               1e-6, 64 */
 typedef struct {
   int precision;
   double tie_rel;
@@ -157,6 +185,10 @@ typedef struct {
   int profile;
   int select_block;
   int coarse_sinc;
+  int local_grids;
+  double local_eps_r;
+  double local_tol;
+  int local_cap;
 } isdf_options;
 
 void isdf_options_default(isdf_options* opt);
@@ -313,10 +345,14 @@ enum {
                               then coarser ones); add the level index      */
   ISDF_GET_V_COARSE = 7 + 16,     /* double[nip x N_g,coarsest]: V_FU of
                                     options.coarse_sinc (after isdf_coulomb) */
-  ISDF_GET_SELECT_STATS = 6 + 16 /* int64[3]: speculative blocks, single
+  ISDF_GET_SELECT_STATS = 6 + 16, /* int64[3]: speculative blocks, single
                               steps and candidate compactions of the last
                               selection (0, 0, 0 when options.select_block
                               = 0)                                         */
+  ISDF_GET_LOCAL_BOX = 8 + 16,  /* double[4]: options.local_grids r_max and
+                              the box's points per axis                    */
+  ISDF_GET_LOCAL_NIP = 9 + 16   /* int32[natom]: local pivots per atom of
+                              the last fit (options.local_grids)           */
 };
 int64_t isdf_get_size(isdf_plan_t plan, int what);
 isdf_status isdf_get(isdf_plan_t plan, int what, void* dst);

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libisdf.so")
 SOURCES = ["api.cu", "basis.cu", "select.cu", "dgemm.cu", "fit.cu", "coulomb.cu", "exchange.cu", "ozgemm.cu", "learn.cu", "fft.cu",
-           "sinc.cu"]
+           "sinc.cu", "local.cu"]
 ARCH = "-gencode=arch=compute_103a,code=sm_103a"
 
 

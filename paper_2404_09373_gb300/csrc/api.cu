@@ -173,6 +173,11 @@ bool is_device_ptr(const void* ptr) {
 namespace {
 
 void free_plan(Plan* p) {
+  for (Plan* q : p->sub) {
+    free_plan(q);
+    delete q;
+  }
+  p->sub.clear();
   for (int l = 0; l < ISDF_MAX_LEVELS; ++l) {
     Level& lv = p->lev[l];
     for (int a = 0; a < 3; ++a) dfree(lv.tab[a]);
@@ -289,6 +294,12 @@ isdf_status validate_options(const isdf_options* o, std::string& why) {
   if (o->profile != 0 && o->profile != 1) return bad("profile must be 0 or 1");
   if (o->coarse_sinc != 0 && o->coarse_sinc != 1) return bad("coarse_sinc must be 0 or 1");
   if (o->select_block < 0 || o->select_block > 256) return bad("select_block must be in [0, 256]");
+  if (o->local_grids != 0 && o->local_grids != 1) return bad("local_grids must be 0 or 1");
+  if (o->local_grids) {
+    if (!(o->local_eps_r > 0.0 && o->local_eps_r < 1.0)) return bad("local_eps_r must be in (0, 1)");
+    if (!(o->local_tol >= 0.0)) return bad("local_tol must be >= 0");
+    if (o->local_cap < 1) return bad("local_cap must be >= 1");
+  }
   return ISDF_OK;
 }
 
@@ -311,6 +322,10 @@ void isdf_options_default(isdf_options* o) {
   o->prefilter = 0;
   o->profile = 0;
   o->select_block = 0;
+  o->local_grids = 0;
+  o->local_eps_r = 1e-5;
+  o->local_tol = 1e-6;
+  o->local_cap = 64;
 }
 
 namespace {
@@ -338,6 +353,14 @@ isdf_status plan_create(const isdf_system* sys, const isdf_options* opt, void* s
   }
   if (o.coarse_sinc && sys->nlevel < 2) {
     g_plan_error = "options.coarse_sinc needs at least two grid levels";
+    return ISDF_ERR_ARG;
+  }
+  if (o.local_grids && sys->nlevel < 2) {
+    g_plan_error = "options.local_grids needs at least two grid levels";
+    return ISDF_ERR_ARG;
+  }
+  if (o.local_grids && o.coarse_sinc && sys->nlevel < 3) {
+    g_plan_error = "options.local_grids with options.coarse_sinc needs at least three grid levels";
     return ISDF_ERR_ARG;
   }
   isdf_plan_s* h = new (std::nothrow) isdf_plan_s();
@@ -401,6 +424,7 @@ isdf_status plan_create(const isdf_system* sys, const isdf_options* opt, void* s
   if (!st) st = dalloc_t(p, &p->d_err, 1, "error word");
   if (!st) st = dalloc_t(p, &p->d_ozerr, 1, "error word");
   if (!st) st = cuda_check(p, cudaMemsetAsync(p->d_ozerr, 0, sizeof(int), p->stream), "memset");
+  if (!st && o.local_grids) st = local_setup(p, sys->level_min_exp[0]);
   if (!st) st = defer_basis ? basis_alloc(p) : basis_build(p);
   if (!st) st = cuda_check(p, cudaStreamSynchronize(p->stream), "plan");
   if (st) {
@@ -472,7 +496,7 @@ isdf_status isdf_select_points(isdf_plan_t h, int nip, double tol, const int64_t
   Plan* p = &h->p;
   if (nip < 1 || !piv_out || !nip_out || !(tol >= 0.0) || (cand && ncand < 1) || (!cand && ncand != 0))
     return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_select_points");
-  if (nip > (p->opt.coarse_sinc ? p->off[p->nlev - 1] : p->ntot))
+  if (nip > (p->opt.coarse_sinc ? p->off[p->nlev - 1] : p->ntot) - p->off[p->sel_lo])
     return fail(p, ISDF_ERR_ARG, "nip exceeds the number of grid points that take part in the selection");
   std::vector<int64_t> cv;
   if (cand) {
@@ -483,13 +507,45 @@ isdf_status isdf_select_points(isdf_plan_t h, int nip, double tol, const int64_t
       if (c < 0 || l >= p->nlev || g >= p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "candidate code out of range");
       if (p->opt.coarse_sinc && l == p->nlev - 1)
         return fail(p, ISDF_ERR_ARG, "with options.coarse_sinc the coarsest level has no candidates");
+      if (l < p->sel_lo) return fail(p, ISDF_ERR_ARG, "with options.local_grids level 0 has no candidates");
     }
+  }
+  // local grids: every atom's own selection first
+  std::vector<int64_t> lpiv;
+  std::vector<double> ldv;
+  if (p->opt.local_grids) {
+    isdf_status st = local_select(p, lpiv, ldv);
+    if (st) return st;
   }
   int found = 0;
   isdf_status st = select_run(p, nip, tol, cand ? &cv : nullptr, &found);
   if (st && st != ISDF_ERR_TIMEOUT) return st;
-  isdf_status st2 = from_device(p, piv_out, p->d_piv, size_t(found), true);
-  if (!st2 && dval_out) st2 = from_device(p, dval_out, p->d_dval, size_t(found), true);
+  isdf_status st2 = ISDF_OK;
+  if (p->opt.local_grids) {
+    std::vector<int64_t> pv(found);
+    std::vector<double> dv(found);
+    if (found) {
+      cudaMemcpyAsync(pv.data(), p->d_piv, sizeof(int64_t) * found, cudaMemcpyDeviceToHost, p->stream);
+      cudaMemcpyAsync(dv.data(), p->d_dval, sizeof(double) * found, cudaMemcpyDeviceToHost, p->stream);
+      st2 = cuda_check(p, cudaStreamSynchronize(p->stream), "pivots");
+    }
+    lpiv.insert(lpiv.end(), pv.begin(), pv.end());
+    ldv.insert(ldv.end(), dv.begin(), dv.end());
+    found = int(lpiv.size());
+    auto put = [&](void* dst, const void* src, size_t bytes) -> isdf_status {
+      if (!bytes) return ISDF_OK;
+      if (!is_device_ptr(dst)) {
+        std::memcpy(dst, src, bytes);
+        return ISDF_OK;
+      }
+      return cuda_check(p, cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice), "copy out");
+    };
+    if (!st2) st2 = put(piv_out, lpiv.data(), sizeof(int64_t) * lpiv.size());
+    if (!st2 && dval_out) st2 = put(dval_out, ldv.data(), sizeof(double) * ldv.size());
+  } else {
+    st2 = from_device(p, piv_out, p->d_piv, size_t(found), true);
+    if (!st2 && dval_out) st2 = from_device(p, dval_out, p->d_dval, size_t(found), true);
+  }
   if (st2) return st2;
   *nip_out = found;
   p->state = 1;
@@ -504,9 +560,20 @@ isdf_status isdf_fit(isdf_plan_t h, const int64_t* piv, int nip) {
   isdf_status st = to_host(p, piv, size_t(nip), pv);
   if (st) return st;
   std::vector<std::vector<int64_t>> per(p->nlev);
+  std::vector<std::vector<int64_t>> per_atom(p->sub.size());
   std::set<int64_t> seen;
   for (int64_t c : pv) {
     const int64_t l = c >> kPivShift, g = c & kPivMask;
+    if (p->opt.local_grids && c >= 0 && l == 0) {
+      // local pivot: (atom << 24) | box index, inside the atom's sphere
+      const int64_t A = g >> kLocalAtomShift, b = g & ((int64_t(1) << kLocalAtomShift) - 1);
+      if (A >= int64_t(p->sub.size()) || b >= p->sub[A]->lev[0].ng || !local_inside(p->sub[A], b))
+        return fail(p, ISDF_ERR_ARG, "local pivot code out of range or outside its atom's sphere");
+      if (!seen.insert(c).second) return fail(p, ISDF_ERR_ARG, "duplicate pivot");
+      per_atom[A].push_back(b);
+      per[0].push_back(g);
+      continue;
+    }
     if (c < 0 || l >= p->nlev || g >= p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "pivot code out of range");
     if (p->opt.coarse_sinc && l == p->nlev - 1)
       return fail(p, ISDF_ERR_ARG, "with options.coarse_sinc every coarsest-level point is implicit: pass none");
@@ -514,7 +581,14 @@ isdf_status isdf_fit(isdf_plan_t h, const int64_t* piv, int nip) {
     per[l].push_back(g);
   }
   for (int l = 0; l < p->nlev; ++l)
-    if (int64_t(per[l].size()) > p->lev[l].ng) return fail(p, ISDF_ERR_ARG, "too many pivots on a level");
+    if (int64_t(per[l].size()) > p->lev[l].ng && !(p->opt.local_grids && l == 0))
+      return fail(p, ISDF_ERR_ARG, "too many pivots on a level");
+  if (p->opt.local_grids) {
+    // level 0 in atom order, each atom's pivots in the order given
+    per[0].clear();
+    for (size_t A = 0; A < per_atom.size(); ++A)
+      for (int64_t b : per_atom[A]) per[0].push_back((int64_t(A) << kLocalAtomShift) | b);
+  }
   // level-ordered layout
   p->nip = nip;
   p->piv_lo.clear();
@@ -527,7 +601,7 @@ isdf_status isdf_fit(isdf_plan_t h, const int64_t* piv, int nip) {
     for (int64_t g : per[l]) p->piv_lo.push_back((int64_t(l) << kPivShift) | g);
     dfree(lv.d_pg);
     lv.d_pg = nullptr;
-    if (lv.k) {
+    if (lv.k && l >= p->sel_lo) {
       if ((st = dalloc_t(p, &lv.d_pg, size_t(lv.k), "pivot indices"))) return st;
       if ((st = cuda_check(p, cudaMemcpyAsync(lv.d_pg, lv.pg.data(), sizeof(int64_t) * lv.k, cudaMemcpyHostToDevice,
                                               p->stream),
@@ -542,7 +616,9 @@ isdf_status isdf_fit(isdf_plan_t h, const int64_t* piv, int nip) {
       (st = dalloc_t(p, &p->XN, size_t(p->nfun) * nip, "X^N")))
     return st;
   p->state = 0;  // an unfinished fit leaves the plan needing a new fit
+  if (p->opt.local_grids && (st = local_fit(p, per_atom))) return st;
   if ((st = fit_run(p))) return st;
+  if (p->opt.local_grids && (st = local_assemble(p))) return st;
   p->state = 2;
   return ISDF_OK;
 }
@@ -829,6 +905,7 @@ isdf_status isdf_save(isdf_plan_t h, const char* path) {
   if (p->state < 3) return fail(p, ISDF_ERR_STATE, "isdf_save needs isdf_coulomb first");
   if (!path) return fail(p, ISDF_ERR_ARG, "isdf_save: path is NULL");
   if (p->opt.coarse_sinc) return fail(p, ISDF_ERR_ARG, "isdf_save: options.coarse_sinc plans are not saved");
+  if (p->opt.local_grids) return fail(p, ISDF_ERR_ARG, "isdf_save: options.local_grids plans are not saved");
   const size_t nx = size_t(p->nfun) * p->nip, nv = size_t(p->nip) * p->nip;
   std::vector<double> xl(nx), xn(nx), v(nv);
   isdf_status st;
@@ -951,6 +1028,10 @@ int64_t isdf_get_size(isdf_plan_t h, int what) {
       return p->state >= 1 ? 3 : 0;
     case ISDF_GET_V_COARSE:
       return (p->state >= 3 && p->VFU) ? int64_t(p->nip) * p->lev[p->nlev - 1].ng : 0;
+    case ISDF_GET_LOCAL_BOX:
+      return p->opt.local_grids ? 4 : 0;
+    case ISDF_GET_LOCAL_NIP:
+      return (p->opt.local_grids && p->state >= 2) ? int64_t(p->sub.size()) : 0;
     default:
       break;
   }
@@ -1011,6 +1092,16 @@ isdf_status isdf_get(isdf_plan_t h, int what, void* dst) {
       const int64_t v[3] = {p->sel_blocks, p->sel_plain_steps, p->sel_compactions};
       return put_host(v, sizeof(v));
     }
+    case ISDF_GET_LOCAL_BOX: {
+      const Level& b = p->sub[0]->lev[0];
+      const double v[4] = {p->r_max, double(b.n[0]), double(b.n[1]), double(b.n[2])};
+      return put_host(v, sizeof(v));
+    }
+    case ISDF_GET_LOCAL_NIP: {
+      std::vector<int32_t> v;
+      for (Plan* q : p->sub) v.push_back(q->lev[0].k);
+      return put_host(v.data(), sizeof(int32_t) * v.size());
+    }
     default:
       break;
   }
@@ -1052,6 +1143,7 @@ isdf_status isdf_features(isdf_plan_t h, float* feat_out) {
   if (!h) return ISDF_ERR_ARG;
   Plan* p = &h->p;
   if (!feat_out) return fail(p, ISDF_ERR_ARG, "feat_out is NULL");
+  if (p->opt.local_grids) return fail(p, ISDF_ERR_ARG, "the learned proposal does not take options.local_grids");
   const size_t n = size_t(p->ntot) * 8;
   float* d = feat_out;
   float* stage = nullptr;
@@ -1102,6 +1194,7 @@ isdf_status isdf_propose(isdf_plan_t h, const float* params, const int64_t* quot
   if (!h) return ISDF_ERR_ARG;
   Plan* p = &h->p;
   if (!params || !quota || !cand_out) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_propose");
+  if (p->opt.local_grids) return fail(p, ISDF_ERR_ARG, "the learned proposal does not take options.local_grids");
   std::vector<int64_t> q(p->nlev);
   int64_t ncand = 0;
   for (int l = 0; l < p->nlev; ++l) {
@@ -1126,6 +1219,7 @@ isdf_status isdf_propose_residual(isdf_plan_t h, const int64_t* quota, int64_t* 
   if (!h) return ISDF_ERR_ARG;
   Plan* p = &h->p;
   if (!quota || !cand_out) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_propose_residual");
+  if (p->opt.local_grids) return fail(p, ISDF_ERR_ARG, "the learned proposal does not take options.local_grids");
   if (p->state < 2) return fail(p, ISDF_ERR_STATE, "isdf_propose_residual needs isdf_fit first");
   std::vector<int64_t> q(p->nlev);
   int64_t ncand = 0;

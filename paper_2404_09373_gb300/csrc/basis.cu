@@ -17,11 +17,14 @@ namespace {
 
 // One descriptor per (plan, level, axis) of a batch of plans: the 1-D factors
 // tab[r * n + i] = scale[r] * sum_{t = tlo[r]}^{thi[r]} u^l exp(-alpha u^2),
-// u = i L / n - A[r] - t L, for the level's nG functions; the per-function
-// data sit at offset `fo` of the batch's staging arrays.
+// u = x_i - A[r] - t L, for the level's nG functions, at the grid points
+// x_i = ((o + i) mod pn) L / pn (o = 0, pn = n for a full-cell grid; a local
+// box's points are those of its parent grid); the per-function data sit at
+// offset `fo` of the batch's staging arrays.
 struct TabDesc {
   int64_t e0;  // first element of this descriptor in the batch's enumeration
   int nG, n;
+  int o, pn;
   double L;
   int64_t fo;
   double* tab;
@@ -44,7 +47,8 @@ __global__ void k_tab1d(const TabDesc* __restrict__ D, int nd, int64_t total, co
   const int64_t le = e - d.e0;
   const int r = int(le / d.n), i = int(le % d.n);
   const int64_t f = d.fo + r;
-  const double x = double(i) * (d.L / double(d.n));
+  const int gi = ((d.o + i) % d.pn + d.pn) % d.pn;
+  const double x = double(gi) * (d.L / double(d.pn));
   const double a = alpha[f];
   double s = 0.0;
   for (int t = tlo[f]; t <= thi[f]; ++t) {
@@ -56,12 +60,15 @@ __global__ void k_tab1d(const TabDesc* __restrict__ D, int nd, int64_t total, co
 }
 
 // One descriptor per (plan, level): Phi[r][g] = tx[r][i] ty[r][j] tz[r][k],
-// g = i + nx (j + ny k).
+// g = i + nx (j + ny k); on a local box zero outside the sphere
+// ((o + i) h - c)^2 summed over the axes (x, y, then z) <= r2 (r2 < 0: no sphere).
 struct PhiDesc {
   int64_t l0;  // first grid line of this descriptor in the batch's enumeration
   int nG, nx, ny, nz;
   const double *tx, *ty, *tz;
   double* phi;
+  int o[3];
+  double h[3], c[3], r2;
 };
 
 // One warp per grid line (function r, y index j, z index k) of any
@@ -86,7 +93,19 @@ __global__ void k_phi(const PhiDesc* __restrict__ D, int nd, int64_t nlines) {
     const double yz = d.ty[r * d.ny + j] * d.tz[r * d.nz + k];
     const double* __restrict__ xr = d.tx + r * d.nx;
     double* __restrict__ out = d.phi + r * (nyz * d.nx) + (int64_t(k) * d.ny + j) * d.nx;
-    for (int i = lane; i < d.nx; i += 32) out[i] = xr[i] * yz;
+    if (d.r2 < 0.0) {
+      for (int i = lane; i < d.nx; i += 32) out[i] = xr[i] * yz;
+    } else {
+      // the sphere test in the host's order and rounding (no contraction)
+      const double dy = __dsub_rn(__dmul_rn(double(d.o[1] + j), d.h[1]), d.c[1]);
+      const double dz = __dsub_rn(__dmul_rn(double(d.o[2] + k), d.h[2]), d.c[2]);
+      const double dy2 = __dmul_rn(dy, dy), dz2 = __dmul_rn(dz, dz);
+      for (int i = lane; i < d.nx; i += 32) {
+        const double dx = __dsub_rn(__dmul_rn(double(d.o[0] + i), d.h[0]), d.c[0]);
+        const double d2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), dy2), dz2);
+        out[i] = d2 <= d.r2 ? xr[i] * yz : 0.0;
+      }
+    }
   }
 }
 
@@ -122,8 +141,16 @@ void image_range(double A, double L, double alpha, double tol, int* lo, int* hi)
 // Basis of every level of every plan in one k_tab1d and one k_phi launch on
 // `s` (the plans' buffers must be allocated and visible to `s`).  Per-function
 // data of all (plan, level, axis) go to the device in one staging copy.
-isdf_status basis_eval(Plan* const* plans, int nplans, cudaStream_t s) {
-  Plan* p0 = plans[0];
+isdf_status basis_eval(Plan* const* plans_in, int nplans_in, cudaStream_t s) {
+  Plan* p0 = plans_in[0];
+  // a plan with local grids brings its atoms' sub-plans
+  std::vector<Plan*> all;
+  for (int b = 0; b < nplans_in; ++b) {
+    all.insert(all.end(), plans_in[b]->sub.begin(), plans_in[b]->sub.end());
+    all.push_back(plans_in[b]);
+  }
+  Plan* const* plans = all.data();
+  const int nplans = int(all.size());
   std::vector<TabDesc> td;
   std::vector<PhiDesc> pd;
   std::vector<double> hA, hal, hsc;
@@ -139,7 +166,8 @@ isdf_status basis_eval(Plan* const* plans, int nplans, cudaStream_t s) {
       std::vector<int> rows(lv.L);  // rows of Phi: L then N
       rows.insert(rows.end(), lv.N.begin(), lv.N.end());
       for (int a = 0; a < 3; ++a) {
-        TabDesc d{e, nG, lv.n[a], p->edge[a], int64_t(hA.size()), lv.tab[a]};
+        const int pn = lv.pn[0] ? lv.pn[a] : lv.n[a];
+        TabDesc d{e, nG, lv.n[a], lv.pn[0] ? lv.o[a] : 0, pn, p->edge[a], int64_t(hA.size()), lv.tab[a]};
         for (int r = 0; r < nG; ++r) {
           const int mu = rows[r];
           int lo = 0, hi = 0;
@@ -154,7 +182,14 @@ isdf_status basis_eval(Plan* const* plans, int nplans, cudaStream_t s) {
         td.push_back(d);
         e += int64_t(nG) * lv.n[a];
       }
-      pd.push_back(PhiDesc{lines, nG, lv.n[0], lv.n[1], lv.n[2], lv.tab[0], lv.tab[1], lv.tab[2], lv.phi});
+      PhiDesc q{lines, nG, lv.n[0], lv.n[1], lv.n[2], lv.tab[0], lv.tab[1], lv.tab[2], lv.phi, {0, 0, 0},
+                {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, lv.mr2};
+      for (int a = 0; a < 3; ++a) {
+        q.o[a] = lv.o[a];
+        q.h[a] = lv.pn[0] ? p->edge[a] / double(lv.pn[a]) : 0.0;
+        q.c[a] = lv.mc[a];
+      }
+      pd.push_back(q);
       lines += int64_t(nG) * lv.n[1] * lv.n[2];
       phi_bytes += 8.0 * double(nG) * double(lv.ng);
     }
@@ -182,13 +217,13 @@ isdf_status basis_eval(Plan* const* plans, int nplans, cudaStream_t s) {
   const double* dA = reinterpret_cast<const double*>(dd + off_f);
   const int* di = reinterpret_cast<const int*>(dA + 3 * nf);
   if (!st) {
-    Prof pr(nplans == 1 ? p0 : nullptr, "basis_tab1d", tab_bytes, "byte", 1);
+    Prof pr(nplans_in == 1 ? p0 : nullptr, "basis_tab1d", tab_bytes, "byte", 1);
     k_tab1d<<<unsigned((e + 255) / 256), 256, 0, s>>>(reinterpret_cast<const TabDesc*>(dd), int(td.size()), e, dA,
                                                       dA + nf, di, di + nf, di + 2 * nf, dA + 2 * nf);
     st = cuda_check(p0, cudaGetLastError(), "k_tab1d");
   }
   if (!st) {
-    Prof pr(nplans == 1 ? p0 : nullptr, "basis_phi", phi_bytes, "byte", 1);
+    Prof pr(nplans_in == 1 ? p0 : nullptr, "basis_phi", phi_bytes, "byte", 1);
     k_phi<<<152 * 16, 256, 0, s>>>(reinterpret_cast<const PhiDesc*>(dd + off_pd), int(pd.size()), lines);
     st = cuda_check(p0, cudaGetLastError(), "k_phi");
   }
@@ -200,6 +235,13 @@ isdf_status basis_eval(Plan* const* plans, int nplans, cudaStream_t s) {
 
 // Allocate the 1-D factor tables and the basis matrix of every level.
 isdf_status basis_alloc(Plan* p) {
+  for (Plan* q : p->sub) {
+    isdf_status st = basis_alloc(q);
+    if (st) {
+      p->err = q->err;
+      return st;
+    }
+  }
   for (int l = 0; l < p->nlev; ++l) {
     Level& lv = p->lev[l];
     if (lv.nG == 0) continue;

@@ -298,9 +298,12 @@ isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* d
     for (int l = 0; l < nlev; ++l) {
       const int64_t k = p->lev[l].k, q0 = p->poff[l], f0 = lo.fb[l], f1 = lo.fb[l + 1], f2 = lo.fb[nlev];
       if (!k) continue;
+      // local grids: X^N of a level-0 pivot also holds the finest-level
+      // functions of higher-index atoms
+      const int64_t fn = (l == 0 && p->opt.local_grids) ? f0 : f1;
       if ((st = block_product(p, xlp + f0 * nip + q0, k, 1, nip, cp + f0 * n, n, 1, n, f1 - f0, yl + q0 * n, n, false,
                               tmp)) ||
-          (st = block_product(p, xnp + f1 * nip + q0, k, 1, nip, cp + f1 * n, n, 1, n, f2 - f1, yn + q0 * n, n, false,
+          (st = block_product(p, xnp + fn * nip + q0, k, 1, nip, cp + fn * n, n, 1, n, f2 - fn, yn + q0 * n, n, false,
                               tmp))) {
         cleanup();
         return st;
@@ -360,9 +363,11 @@ isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* d
       for (int m = 0; m < nlev; ++m) {
         const int64_t f0 = lo.fb[m], fm = lo.fb[m + 1] - lo.fb[m], q0 = p->poff[m], k = p->lev[m].k;
         if (!fm) continue;
+        // local grids: the finest-level functions also have X^N on level-0 pivots
+        const int64_t qn = (m == 0 && p->opt.local_grids) ? p->poff[1] : q0;
         if ((st = block_product(p, xlp + f0 * nip + q0, fm, nip, 1, u + q0 * n, n, 1, n, k, kcp + f0 * n, n, false,
                                 tmp)) ||
-            (st = block_product(p, xnp + f0 * nip, fm, nip, 1, u + nip * n, n, 1, n, q0, kcp + f0 * n, n, true, tmp))) {
+            (st = block_product(p, xnp + f0 * nip, fm, nip, 1, u + nip * n, n, 1, n, qn, kcp + f0 * n, n, true, tmp))) {
           cleanup();
           return st;
         }

@@ -171,6 +171,7 @@ isdf_status fit_run(Plan* p) {
     lv.zct = nullptr;
     dfree(lv.rinv);
     lv.rinv = nullptr;
+    if (l < p->sel_lo) continue;  // local grids' level 0: fitted atom by atom (local.cu)
     if ((st = dalloc_t(p, &lv.resid, size_t(lv.ng), "fit residual"))) return st;
     if (lv.k == 0) {
       // no pivots: the residual is the whole diagonal w M(g,g)
@@ -309,7 +310,7 @@ isdf_status fit_residual_run(Plan* p) {
   isdf_status st;
   for (int l = 0; l < p->nlev; ++l) {
     Level& lv = p->lev[l];
-    if (lv.k == 0 || !lv.zct) continue;  // a level without pivots was done by the fit
+    if (lv.k == 0 || !lv.zct || lv.nG == 0) continue;  // done by the fit; local grids' level 0: not kept
     double *y = nullptr, *scr = nullptr;
     if ((st = dalloc_t(p, &y, size_t(lv.k) * lv.ng, "fit scratch")) || (st = dalloc_t(p, &scr, 2, "residual statistics"))) {
       dfree(y);

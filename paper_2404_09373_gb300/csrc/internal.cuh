@@ -25,6 +25,14 @@ struct Level {
   std::vector<int> L;    // functions of this level
   std::vector<int> N;    // functions of coarser levels
   int nL = 0, nN = 0, nG = 0;
+  // a box of a finer full grid (an atom's local grid): point (i, j, k) is the
+  // parent point ((o + i) mod pn) per axis; pn[0] == 0 for a full-cell grid.
+  // Basis values are zero outside the sphere |(o + i) h - mc| <= r (mr2 = r^2,
+  // h = edge / pn); mr2 < 0: no sphere
+  int o[3] = {0, 0, 0};
+  int pn[3] = {0, 0, 0};
+  double mc[3] = {0.0, 0.0, 0.0};
+  double mr2 = -1.0;
   double* tab[3] = {nullptr, nullptr, nullptr};  // 1-D factors [nG][n[a]]
   double* phi = nullptr;                         // basis values [nG][ng]
   // selection factor columns [fac_cap][ng]
@@ -110,6 +118,13 @@ struct Plan {
   double* VFU = nullptr;  // options.coarse_sinc: (xi_P | sinc_g) [nip][N_g of the coarsest level]
   bool capturing = false;
   double* d_ex_slot = nullptr;
+  // options.local_grids: level 0 on atom-centred local grids (Section III,
+  // Eq. 5).  One single-level sub-plan per atom holds its box, basis values,
+  // selection and fit; level 0 of this plan holds no basis values, only the
+  // assembled fit on the full finest grid (for the Coulomb matrix).
+  std::vector<Plan*> sub;
+  double r_max = 0.0;
+  int sel_lo = 0;  // first level of this plan's own greedy selection
   // profiling
   std::vector<ProfEvent> pend;
   std::map<std::string, KStat> stats;
@@ -163,6 +178,13 @@ isdf_status tc_product5(Plan* p, const double* a, int64_t M, int64_t sar, int64_
 // dK (N x N) and dKC (N x n, K C) are nullable; exchange.cu
 isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* dKC, double* Ex);
 isdf_status gather_pivot_factors(Plan* p);                           // basis.cu
+// local grids (local.cu)
+constexpr int kLocalAtomShift = 24;  // local pivot code on level 0: (atom << 24) | box index
+isdf_status local_setup(Plan* p, double alpha_min);  // alpha_min: the finest level's edge
+bool local_inside(const Plan* q, int64_t b);  // box point b of sub-plan q inside its sphere
+isdf_status local_select(Plan* p, std::vector<int64_t>& piv, std::vector<double>& dval);
+isdf_status local_fit(Plan* p, const std::vector<std::vector<int64_t>>& per_atom);  // sub-plan fits
+isdf_status local_assemble(Plan* p);  // level 0 of p from the sub-plans' fits (after fit_run(p))
 
 // FP64 SIMT GEMM (dgemm.cu):
 //   C[m][n] = alpha * sum_k opA(m,k) w(k) opB(k,n) + beta * C[m][n]

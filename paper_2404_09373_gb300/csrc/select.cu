@@ -1624,6 +1624,10 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
   if ((st = dalloc_t(p, &d0, size_t(p->ntot), "initial diagonal"))) return st;
   for (int l = 0; l < p->nlev; ++l) {
     Level& lv = p->lev[l];
+    if (lv.nG == 0) {  // a level without basis values of its own (local grids' level 0)
+      cudaMemsetAsync(d0 + p->off[l], 0, sizeof(double) * size_t(lv.ng), s);
+      continue;
+    }
     Prof pr(p, "select_diag", 2.0 * double(lv.nG) * double(lv.ng), "flop", 1);
     k_sel_diag<<<152 * 8, 256, 0, s>>>(lv.phi, lv.ng, lv.nL, lv.nG, lv.w, d0 + p->off[l]);
   }
@@ -1641,8 +1645,10 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     return r;
   };
   // with the coarsest level as the universal sinc grid it takes no part in
-  // the selection: no candidates there, and d_0 is the finer levels' largest
+  // the selection: no candidates there, and d_0 is the finer levels' largest;
+  // levels below sel_lo (local grids' level 0) have their own selections
   const int nsel = p->opt.coarse_sinc ? p->nlev - 1 : p->nlev;
+  const int lo = p->sel_lo;
   int kl[ISDF_MAX_LEVELS];
   bool aborted = false;
   p->sel_compactions = 0;
@@ -1669,7 +1675,7 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     return done(loop(cidx, nc));
   }
   if (!p->opt.prefilter) {
-    for (int l = 0; l < p->nlev; ++l) nc[l] = l < nsel ? p->lev[l].ng : 0;
+    for (int l = 0; l < p->nlev; ++l) nc[l] = (l >= lo && l < nsel) ? p->lev[l].ng : 0;
     return done(loop(cidx, nc));
   }
   // exact prefilter: tau relative to the largest initial residual d_0
@@ -1695,7 +1701,7 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
     free_cidx();
     for (int l = 0; l < p->nlev; ++l) {
       Level& lv = p->lev[l];
-      if (l >= nsel) {
+      if (l >= nsel || l < lo) {
         nc[l] = 0;
         continue;
       }
@@ -1734,7 +1740,7 @@ isdf_status select_run(Plan* p, int nip, double tol, const std::vector<int64_t>*
       if (st) return done(st);
     }
     bool all_kept = true;
-    for (int l = 0; l < nsel; ++l) all_kept = all_kept && nc[l] == p->lev[l].ng;
+    for (int l = lo; l < nsel; ++l) all_kept = all_kept && nc[l] == p->lev[l].ng;
     if (all_kept) {  // nothing dropped: this is the full greedy run
       free_cidx();
       return done(loop(cidx, nc));

@@ -23,8 +23,11 @@ STATUS_NAMES = ["OK", "ERR_ARG", "ERR_OOM", "ERR_NOT_PD", "ERR_CUDA", "ERR_CUFFT
 GET_NBASIS, GET_NIP_LEVEL, GET_PIVOTS, GET_XL, GET_XN, GET_V, GET_XI_LEVEL0 = 0, 1, 2, 3, 4, 5, 6
 GET_PHI_LEVEL0 = 10
 GET_NPOINTS, GET_FIT_RESIDUAL, GET_SELECT_STATS, GET_V_COARSE = 20, 21, 22, 23
+GET_LOCAL_BOX, GET_LOCAL_NIP = 24, 25
+LOCAL_ATOM_SHIFT = 24  # local pivot code on level 0: (atom << 24) | box index
 # element type written by isdf_get for each selector (float64 otherwise)
 _GET_DTYPE = {GET_NBASIS: np.int32, GET_NIP_LEVEL: np.int32, GET_PIVOTS: np.int64, GET_NPOINTS: np.int64,
+              GET_LOCAL_NIP: np.int32,
               GET_SELECT_STATS: np.int64}
 
 EXPORTED = [
@@ -90,6 +93,10 @@ class isdf_options(ctypes.Structure):
         ("profile", c_int),
         ("select_block", c_int),
         ("coarse_sinc", c_int),
+        ("local_grids", c_int),
+        ("local_eps_r", c_double),
+        ("local_tol", c_double),
+        ("local_cap", c_int),
     ]
 
 
@@ -227,10 +234,11 @@ def default_options(**kw):
 class Plan:
     """Owner of an ``isdf_plan_t``; destroyed with ``close()`` or on collection."""
 
-    def __init__(self, handle, lib, system):
+    def __init__(self, handle, lib, system, options=None):
         self.handle = handle
         self._lib = lib
         self.system = system
+        self.options = options
 
     def close(self):
         if self.handle:
@@ -290,7 +298,7 @@ def isdf_plan(system: dict, options=None, stream=None) -> Plan:
                        ctypes.byref(h))
     if st != ISDF_OK:
         raise IsdfError(st, lib.isdf_last_error(None).decode())
-    return Plan(h.value, lib, system)
+    return Plan(h.value, lib, system, options)
 
 
 def isdf_plan_batch(systems, options=None, streams=None):
@@ -315,7 +323,7 @@ def isdf_plan_batch(systems, options=None, streams=None):
     st = lib.isdf_plan_batch(arr, n, ctypes.byref(options), sp, out)
     if st != ISDF_OK:
         raise IsdfError(st, lib.isdf_last_error(None).decode())
-    return [Plan(out[i], lib, systems[i]) for i in range(n)]
+    return [Plan(out[i], lib, systems[i], options) for i in range(n)]
 
 
 class ExchangeGraph:
@@ -382,9 +390,14 @@ def isdf_grids_for_threshold(system: dict, eps_K: float):
 
 
 def isdf_select_points(plan: Plan, nip: int, tol: float = 0.0, cand=None, piv_out=None, dval_out=None):
-    """Returns (pivot codes, pivot values) -- numpy unless outputs are given."""
-    piv = np.zeros(nip, dtype=np.int64) if piv_out is None else piv_out
-    dv = np.zeros(nip, dtype=np.float64) if dval_out is None else dval_out
+    """Returns (pivot codes, pivot values) -- numpy unless outputs are given.
+    With options.local_grids the atoms' local pivots come first and the
+    outputs must hold nip + natom * local_cap values."""
+    size = nip
+    if plan.options is not None and plan.options.local_grids:
+        size += len(plan.system["xyz"]) * int(plan.options.local_cap)
+    piv = np.zeros(size, dtype=np.int64) if piv_out is None else piv_out
+    dv = np.zeros(size, dtype=np.float64) if dval_out is None else dval_out
     cptr = None
     ncand = 0
     if cand is not None:

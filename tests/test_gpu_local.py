@@ -1,0 +1,138 @@
+"""Atom-centred local dense grids (options.local_grids, Section III, Eq. 5)
+against the oracle's run_local: the atoms' pivot sequences and the coarser
+levels' pivots exactly, the box and r_max, X^L / X^N, V, K, K C and E_x."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2404_09373_gb300 import isdf as B
+from paper_2404_09373_gb300 import systems as S
+
+pytestmark = pytest.mark.gpu
+
+
+def cell(per_cell=(24, 12, 6), reps=(1, 1, 1), seed=11, sigma=0.05, n_occ_per_atom=2):
+    rng = np.random.default_rng(S.SEED_BASE + seed)
+    sysd = S.make_system(reps, sigma, rng, tuple((p, p, p) for p in per_cell), S.LEVEL_EDGES_3)
+    C = S.make_orbitals(sysd, n_occ_per_atom * sysd["xyz"].shape[0], rng)
+    return sysd, C
+
+
+def gpu_local(sysd, C, nip, opts):
+    plan = B.isdf_plan(sysd, opts)
+    try:
+        piv, dv = B.isdf_select_points(plan, nip)
+        piv, dv = piv.copy(), dv.copy()
+        B.isdf_fit(plan, piv)
+        k = B.isdf_get(plan, B.GET_NIP_LEVEL)
+        npiv = int(k.sum())
+        V = np.zeros((npiv, npiv))
+        B.isdf_coulomb(plan, V)
+        K, Ex = B.isdf_exchange(plan, C)
+        KC, Ex_occ = B.isdf_exchange_occ(plan, C)
+        N = S.nbasis(sysd)
+        return {"pivots": piv, "dvals": dv, "nip_level": k, "V": V, "K": K, "Ex": Ex, "KC": KC, "Ex_occ": Ex_occ,
+                "XL": B.isdf_get(plan, B.GET_XL).reshape(N, npiv), "XN": B.isdf_get(plan, B.GET_XN).reshape(N, npiv),
+                "box": B.isdf_get(plan, B.GET_LOCAL_BOX), "per_atom": B.isdf_get(plan, B.GET_LOCAL_NIP),
+                "pivots_lo": B.isdf_get(plan, B.GET_PIVOTS)}
+    finally:
+        plan.close()
+
+
+def check(g, o, C, natom, precision, sinc=False):
+    nloc = o["local_pivots"].size
+    # pivots: every atom's sequence, then the coarser levels' greedy ones
+    assert np.array_equal(g["pivots"][:nloc], o["local_pivots"])
+    assert np.array_equal(g["pivots"][nloc:], o["pivots"])
+    assert np.allclose(g["dvals"][:nloc], o["local_dvals"], rtol=1e-9, atol=0)
+    assert np.allclose(g["dvals"][nloc:], o["dvals"], rtol=1e-9, atol=0)
+    assert np.array_equal(g["per_atom"], np.bincount(o["local_pivots"] >> B.LOCAL_ATOM_SHIFT, minlength=natom))
+    b = o["blocks"][0]["box"]
+    assert g["box"][0] == pytest.approx(o["r_max"], rel=1e-15) and list(g["box"][1:]) == list(b)
+    # the fitted columns (the sinc grid's columns are implicit on the device)
+    nf = g["XL"].shape[1]
+    assert np.max(np.abs(g["XL"] - o["XL"][:, :nf])) <= 1e-13 and np.max(np.abs(g["XN"] - o["XN"][:, :nf])) <= 1e-13
+    if not sinc:
+        # precision 1: V = W (ZC^T v ZC) W with W = (CC^T)^-1 per atom, whose
+        # conditioning (up to the inverse of local_tol) scales the products'
+        # rounding; K below is held to the absolute bar
+        vr = np.max(np.abs(g["V"] - o["V"])) / np.max(np.abs(o["V"]))
+        assert vr <= (1e-9 if precision == 0 else 1e-5), vr
+    dk = np.max(np.abs(g["K"] - o["K"]))
+    assert dk <= 1e-6, dk
+    assert abs(g["Ex"] - o["Ex"]) <= 1e-6 * natom
+    assert np.max(np.abs(g["KC"] - g["K"] @ C)) <= 1e-9 * max(1.0, np.max(np.abs(g["KC"])))
+    assert abs(g["Ex_occ"] - g["Ex"]) <= 1e-9 * abs(g["Ex"])
+    return dk
+
+
+@pytest.mark.parametrize("precision,block", [(0, 0), (1, 0), (1, 96)])
+def test_local_grids_match_oracle(precision, block):
+    """1x1x1 displaced cell, grids 24^3/12^3/6^3: per atom a box of 21^3 points
+    (r_max = 2.68 bohr at eps_r = 1e-5, alpha_min = 1.6), atoms on the cell
+    corner wrap around the cell."""
+    sysd, C = cell()
+    N = S.nbasis(sysd)
+    o = oracle.run_local(sysd, C, 3 * N, local_tol=1e-6, local_cap=64)
+    g = gpu_local(sysd, C, 3 * N, {"precision": precision, "local_grids": 1, "local_tol": 1e-6, "local_cap": 64,
+                                   "prefilter": 1, "select_block": block})
+    check(g, o, C, 8, precision)
+
+
+def test_local_grids_two_cells_and_cap():
+    """A 1x1x2 cell with a per-atom cap that binds (16 pivots on every atom)."""
+    sysd, C = cell(reps=(1, 1, 2), seed=12)
+    N = S.nbasis(sysd)
+    o = oracle.run_local(sysd, C, 2 * N, local_tol=1e-9, local_cap=16)
+    assert np.all(np.bincount(o["local_pivots"] >> B.LOCAL_ATOM_SHIFT) == 16)
+    g = gpu_local(sysd, C, 2 * N, {"precision": 1, "local_grids": 1, "local_tol": 1e-9, "local_cap": 16,
+                                   "prefilter": 1, "select_block": 96})
+    check(g, o, C, 16, 1)
+
+
+def test_local_grids_with_the_sinc_coarse_level():
+    """The paper's full layout: local grids for the sharp functions, the
+    coarsest level as the universal sinc grid, a fitted level between."""
+    sysd, C = cell(seed=13)
+    N = S.nbasis(sysd)
+    o = oracle.run_local(sysd, C, 2 * N, local_tol=1e-6, local_cap=64, sinc=True)
+    g = gpu_local(sysd, C, 2 * N, {"precision": 1, "local_grids": 1, "coarse_sinc": 1, "local_tol": 1e-6,
+                                   "local_cap": 64, "prefilter": 1})
+    check(g, o, C, 8, 1, sinc=True)
+
+
+def test_local_grids_at_the_full_resolution():
+    """Grids 48^3/24^3/12^3 per cell (the resolution of the 2x2x2 workload):
+    boxes of 41^3 points, about 29,000 sphere points per atom; the bench's
+    options (tensor-core precision, prefilter, speculative blocks of 96)."""
+    sysd, C = cell(per_cell=(48, 24, 12), seed=11)
+    N = S.nbasis(sysd)
+    o = oracle.run_local(sysd, C, 3 * N, local_tol=1e-8, local_cap=128)
+    g = gpu_local(sysd, C, 3 * N, {"precision": 1, "local_grids": 1, "local_tol": 1e-8, "local_cap": 128,
+                                   "prefilter": 1, "select_block": 96})
+    check(g, o, C, 8, 1)
+
+
+def test_local_grids_refusals():
+    sysd, C = cell()
+    with pytest.raises(B.IsdfError, match="wider than the cell"):
+        B.isdf_plan(sysd, {"local_grids": 1, "local_eps_r": 1e-14})
+    one = S.make_system((1, 1, 1), 0.0, None, ((24, 24, 24),), ())
+    with pytest.raises(B.IsdfError, match="two grid levels"):
+        B.isdf_plan(one, {"local_grids": 1})
+    plan = B.isdf_plan(sysd, {"local_grids": 1})
+    try:
+        # box point 0 (a corner) lies outside the sphere: refused as a pivot
+        with pytest.raises(B.IsdfError, match="outside its atom's sphere"):
+            B.isdf_fit(plan, np.array([0], dtype=np.int64))
+        with pytest.raises(B.IsdfError, match="out of range"):
+            B.isdf_fit(plan, np.array([8 << B.LOCAL_ATOM_SHIFT], dtype=np.int64))
+        # level-0 candidates of the greedy are refused (the atoms select their own)
+        with pytest.raises(B.IsdfError, match="level 0 has no candidates"):
+            B.isdf_select_points(plan, 10, cand=np.array([5], dtype=np.int64))
+        piv, _ = B.isdf_select_points(plan, 20)
+        assert piv.size > 20 and np.all(piv[:-20] >> B.PIVOT_SHIFT == 0)
+        with pytest.raises(B.IsdfError, match="learned proposal"):
+            B.isdf_features(plan)
+    finally:
+        plan.close()

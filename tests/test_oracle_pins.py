@@ -726,3 +726,14 @@ def test_local_selection_threshold_is_relative_per_atom():
         assert np.all(dv >= tol * d0)
         sel = O.select_points([blk], dv.size + 1, 0.0)
         assert sel["dvals"][-1] < tol * d0
+
+
+def test_local_grids_with_the_sinc_coarse_level_exact_at_full_rank():
+    """Local grids on the finest level and the coarsest level as the sinc
+    grid together: at full rank the exchange is again the 4-index exchange of
+    the local pair partition (the coarse pairs are exact on the sinc grid)."""
+    sysd, C = _local_case(3)
+    Kb, Eb = oracle.brute_exchange_local(sysd, C, 1e-2)
+    r = oracle.run_local(sysd, C, 400, tol=1e-14, local_tol=1e-14, local_cap=400, eps_r=1e-2, sinc=True, reg_rel=0.0)
+    assert np.max(np.abs(r["K"] - Kb)) <= 2e-8 * np.max(np.abs(Kb))
+    assert abs(r["Ex"] - Eb) <= 2e-8 * abs(Eb)
