@@ -74,6 +74,10 @@ def run_batch(cells, opts=None, n_streams=4, mem_budget=120 * 2 ** 30, iteration
     t0 = time.perf_counter()
     plans = B.isdf_plan_batch([c[0] for c in cells], opts, streams=[st.cuda_stream for st in streams])
     t_plan = time.perf_counter() - t0
+    # the budget never exceeds what the device has free once every cell's
+    # basis values are resident (other work of the process holds the rest)
+    torch.cuda.empty_cache()
+    mem_budget = min(mem_budget, int(0.8 * torch.cuda.mem_get_info(dev)[0]))
     lock = threading.Condition()
     state = {"bytes": 0}
     piv = [None] * len(cells)
