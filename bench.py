@@ -416,6 +416,11 @@ def roofline(kern, precision):
         hbm = pk.get("hbm_gbs", 6800.0)
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
+        if st.get("flop") and name in TC_KERNELS:
+            # the same launches' tensor work: FP64-equivalent flops x digit-pair products
+            tf = st["flop"] / (st["ms"] / 1e3) / 1e12
+            roof["tensor_issue_frac"] = tf * TC_KERNELS[name] / pk.get("bf16_tflops", 1900.0)
+            roof["fp64_equivalent_tflops"] = tf
     ratio = TRAFFIC_PER_WORK.get(name)
     roof.update({"traffic": ratio * per_launch if ratio else None, "traffic_unit": "byte per launch",
                  "kernel": name, "launches": st["launches"],
@@ -478,7 +483,9 @@ def main():
         except Exception as e:
             torch.cuda.synchronize()
             torch.cuda.empty_cache()
-            return {"error": f"{type(e).__name__}: {e}"[:400]}
+            free, total = torch.cuda.mem_get_info()
+            return {"error": f"{type(e).__name__}: {e}"[:400], "device_free_gb_after": free / 2 ** 30,
+                    "torch_reserved_gb": torch.cuda.memory_reserved() / 2 ** 30}
 
     def step(profile=False, o=None, sysx=None, nipx=None, tol=0.0, occ=False):
         """One pass of the path; sysx / nipx / tol: another system, pivot cap
@@ -697,7 +704,8 @@ def main():
                      "graph_capture_s": tc["capture_s"], "exchange_graph_replay_s": t_k,
                      "s_iter_per_cell": ((tc["plan_s"] + tc["isdf_s"]) / SCF_CHARGE + t_k) / len(cells),
                      "pivots_equal_3_vs_1_stream": bool(same), "max_abs_dK_3_vs_1_stream_Ha": dK,
-                     "autotuned_shapes": len(B.isdf_autotune_table())}
+                     "autotuned_shapes": len(B.isdf_autotune_table()),
+                 "device_free_gb_after_plans": tc["device_free_gb_after_plans"], "mem_budget_gb": tc["mem_budget_gb"]}
         return batch
 
     batch = soft(_sec_batch)

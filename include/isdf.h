@@ -318,6 +318,18 @@ const char* isdf_autotune_table(void);
  * truncated or malformed file gives ISDF_ERR_ARG.  `path` is a host string;
  * both calls return after the data are written / on the device. */
 isdf_status isdf_save(isdf_plan_t plan, const char* path);
+
+/* Free every buffer of a plan that the exchange build does not read (needs
+ * isdf_coulomb first): the basis values and their 1-D factors (except the
+ * coarsest level's with options.coarse_sinc, whose exchange reads them), the
+ * fit's ZC^T, R^-1 and interpolation vectors, the spectra, residuals and
+ * selection leftovers, and the local grids' per-atom buffers.  The pivots,
+ * X^L, X^N and V stay: isdf_exchange, isdf_exchange_occ, isdf_exchange_graph,
+ * isdf_save and isdf_get of those keep working; isdf_select_points, isdf_fit,
+ * isdf_coulomb and the learned proposal return ISDF_ERR_STATE afterwards.
+ * For batches of cells whose ISDF runs once before many exchange builds
+ * (the paper runs the ISDF once, before the SCF iterations). */
+isdf_status isdf_release_fit(isdf_plan_t plan);
 isdf_status isdf_load(isdf_plan_t plan, const char* path);
 
 /* Copy plan data out (host or device destination) for tests and tools.
@@ -429,7 +441,10 @@ isdf_status isdf_propose_residual(isdf_plan_t plan, const int64_t* quota, int64_
  * summed exactly (512-wide chunks, integer accumulation) and the rest, below
  * 2^-42 of the result, in FP32: with 7 the error is below 2^-47 * K *
  * max_k|A[m,k]| * max_k|B[n,k]|, with 8 (FP64-grade) below 2^-52 * K *
- * max_k|A[m,k]| * max_k|B[n,k]| + 2^-53 |C[m,n]|.
+ * max_k|A[m,k]| * max_k|B[n,k]| + 2^-53 |C[m,n]|.  With 8, A's digit planes
+ * are stored as 8-bit integers (its row scale two powers of two higher, 54
+ * fraction bits) and expanded to BF16 in shared memory, halving A's stream
+ * (the 8-digit bound above covers this rounding).
  * splits > 1 divides K over that many CTAs (needs splits*M*N*8 bytes of
  * scratch, allocated by the call).  Enqueued on `stream`; returns after the
  * stream is idle.  A pipeline wait that exceeds its bound returns

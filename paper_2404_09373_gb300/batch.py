@@ -6,7 +6,8 @@
    CUDA stream: a pool of ``n_streams`` host threads keeps cells in flight so that
    small cells, whose kernels cannot fill the GPU, overlap with each other
    and with the large ones; a device-memory budget bounds how many are in
-   flight at once.
+   flight at once, and a finished cell keeps only its exchange inputs
+   (``isdf_release_fit``: its basis values, fit and spectra are freed).
 3. The exchange builds of all cells -- the per-SCF-iteration part -- are
    captured once into one CUDA graph (``isdf_exchange_graph``, one branch per
    cell) and replayed with each iteration's orbitals.
@@ -77,7 +78,8 @@ def run_batch(cells, opts=None, n_streams=4, mem_budget=120 * 2 ** 30, iteration
     # the budget never exceeds what the device has free once every cell's
     # basis values are resident (other work of the process holds the rest)
     torch.cuda.empty_cache()
-    mem_budget = min(mem_budget, int(0.8 * torch.cuda.mem_get_info(dev)[0]))
+    free_after_plans = torch.cuda.mem_get_info(dev)[0]
+    mem_budget = min(mem_budget, int(0.8 * free_after_plans))
     lock = threading.Condition()
     state = {"bytes": 0}
     piv = [None] * len(cells)
@@ -94,6 +96,8 @@ def run_batch(cells, opts=None, n_streams=4, mem_budget=120 * 2 ** 30, iteration
             p, _ = B.isdf_select_points(plans[i], nip)
             B.isdf_fit(plans[i], p)
             B.isdf_coulomb(plans[i])
+            # only the exchange's inputs (X^L, X^N, V) stay for the SCF iterations
+            B.isdf_release_fit(plans[i])
             piv[i] = p
         finally:
             with lock:
@@ -125,4 +129,5 @@ def run_batch(cells, opts=None, n_streams=4, mem_budget=120 * 2 ** 30, iteration
             p.close()
     res = [{"pivots": piv[i], "K": Ks[i], "Ex": exs[i]} for i in range(len(cells))]
     return res, {"plan_s": t_plan, "isdf_s": t_isdf, "capture_s": t_capture, "exchange_replay_s": reps,
-                 "wall_s": t_plan + t_isdf + t_capture + reps[0]}
+                 "wall_s": t_plan + t_isdf + t_capture + reps[0], "device_free_gb_after_plans": free_after_plans / 2 ** 30,
+                 "mem_budget_gb": mem_budget / 2 ** 30}

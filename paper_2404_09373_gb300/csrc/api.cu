@@ -53,6 +53,7 @@ void prof_flush(Plan* p) {
       k.launches += e.launches;
       k.ms += ms;
       k.work += e.work;
+      k.flop += e.flop;
       k.unit = e.unit;
     }
     cudaEventDestroy(e.a);
@@ -494,6 +495,7 @@ isdf_status isdf_select_points(isdf_plan_t h, int nip, double tol, const int64_t
                                int64_t* piv_out, double* dval_out, int* nip_out) {
   if (!h) return ISDF_ERR_ARG;
   Plan* p = &h->p;
+  if (p->released) return fail(p, ISDF_ERR_STATE, "the plan's basis values were released (isdf_release_fit)");
   if (nip < 1 || !piv_out || !nip_out || !(tol >= 0.0) || (cand && ncand < 1) || (!cand && ncand != 0))
     return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_select_points");
   if (nip > (p->opt.coarse_sinc ? p->off[p->nlev - 1] : p->ntot) - p->off[p->sel_lo])
@@ -555,6 +557,7 @@ isdf_status isdf_select_points(isdf_plan_t h, int nip, double tol, const int64_t
 isdf_status isdf_fit(isdf_plan_t h, const int64_t* piv, int nip) {
   if (!h) return ISDF_ERR_ARG;
   Plan* p = &h->p;
+  if (p->released) return fail(p, ISDF_ERR_STATE, "the plan's basis values were released (isdf_release_fit)");
   if (!piv || nip < 1) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_fit");
   std::vector<int64_t> pv;
   isdf_status st = to_host(p, piv, size_t(nip), pv);
@@ -626,7 +629,7 @@ isdf_status isdf_fit(isdf_plan_t h, const int64_t* piv, int nip) {
 isdf_status isdf_coulomb(isdf_plan_t h, double* V_out) {
   if (!h) return ISDF_ERR_ARG;
   Plan* p = &h->p;
-  if (p->state < 2) return fail(p, ISDF_ERR_STATE, "isdf_coulomb needs isdf_fit first");
+  if (p->state < 2 || p->released) return fail(p, ISDF_ERR_STATE, "isdf_coulomb needs isdf_fit first");
   p->state = 2;
   isdf_status st = coulomb_run(p);
   if (st) return st;
@@ -719,7 +722,14 @@ struct isdf_exchange_graph_s {
 void isdf_exchange_graph_destroy(isdf_exchange_graph_t g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
-  if (g->exec) cudaGraphExecDestroy(g->exec);
+  if (g->exec) {
+    cudaGraphExecDestroy(g->exec);
+    // the graph's allocations return to the device's graph memory pool, which
+    // keeps their physical memory until trimmed: give it back to the device
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGraphMemTrim(dev);
+    cudaGetLastError();
+  }
   for (double* q : g->dC) cudaFree(q);
   for (double* q : g->dOut) cudaFree(q);
   cudaFree(g->dEx);
@@ -899,6 +909,33 @@ const char* isdf_autotune_table(void) {
   return t.c_str();
 }
 
+isdf_status isdf_release_fit(isdf_plan_t h) {
+  if (!h) return ISDF_ERR_ARG;
+  Plan* p = &h->p;
+  if (p->state < 3) return fail(p, ISDF_ERR_STATE, "isdf_release_fit needs isdf_coulomb first");
+  isdf_status st = cuda_check(p, cudaStreamSynchronize(p->stream), "release");
+  if (st) return st;
+  auto release = [&](Plan* q, bool keep_coarse_phi) {
+    for (int l = 0; l < q->nlev; ++l) {
+      Level& lv = q->lev[l];
+      const bool keep = keep_coarse_phi && l == q->nlev - 1;  // the sinc grid's exchange reads them
+      if (!keep) {
+        for (int a = 0; a < 3; ++a) dfree(lv.tab[a]), lv.tab[a] = nullptr;
+        dfree(lv.phi), lv.phi = nullptr;
+      }
+      dfree(lv.fac), dfree(lv.xiT), dfree(lv.resid), dfree(lv.zct), dfree(lv.rinv), dfree(lv.spec);
+      lv.fac = lv.xiT = lv.zct = lv.rinv = nullptr;
+      lv.resid = nullptr;
+      lv.spec = nullptr;
+    }
+    dfree(q->d_diag), q->d_diag = nullptr;
+  };
+  for (Plan* q : p->sub) release(q, false);
+  release(p, p->opt.coarse_sinc != 0);
+  p->released = true;
+  return ISDF_OK;
+}
+
 isdf_status isdf_save(isdf_plan_t h, const char* path) {
   if (!h) return ISDF_ERR_ARG;
   Plan* p = &h->p;
@@ -1023,7 +1060,7 @@ int64_t isdf_get_size(isdf_plan_t h, int what) {
     case ISDF_GET_NPOINTS:
       return 1;
     case ISDF_GET_FIT_RESIDUAL:
-      return p->state >= 2 ? 2 * p->nlev : 0;
+      return (p->state >= 2 && (!p->released || p->resid_ready)) ? 2 * p->nlev : 0;
     case ISDF_GET_SELECT_STATS:
       return p->state >= 1 ? 3 : 0;
     case ISDF_GET_V_COARSE:
@@ -1041,7 +1078,7 @@ int64_t isdf_get_size(isdf_plan_t h, int what) {
   }
   if (what >= ISDF_GET_PHI_LEVEL0 && what < ISDF_GET_PHI_LEVEL0 + p->nlev) {
     const Level& lv = p->lev[what - ISDF_GET_PHI_LEVEL0];
-    return int64_t(lv.nG) * lv.ng;
+    return lv.phi ? int64_t(lv.nG) * lv.ng : 0;
   }
   return 0;
 }
@@ -1124,9 +1161,10 @@ const char* isdf_profile_json(isdf_plan_t h) {
   bool first = true;
   for (const auto& kv : p->stats) {
     char buf[512];
-    snprintf(buf, sizeof(buf), "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"work\": %.6e, \"unit\": \"%s\"}",
+    snprintf(buf, sizeof(buf),
+             "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f, \"work\": %.6e, \"unit\": \"%s\", \"flop\": %.6e}",
              first ? "" : ", ", kv.first.c_str(), (long long)kv.second.launches, kv.second.ms, kv.second.work,
-             kv.second.unit.c_str());
+             kv.second.unit.c_str(), kv.second.flop);
     s += buf;
     first = false;
   }
@@ -1143,6 +1181,7 @@ isdf_status isdf_features(isdf_plan_t h, float* feat_out) {
   if (!h) return ISDF_ERR_ARG;
   Plan* p = &h->p;
   if (!feat_out) return fail(p, ISDF_ERR_ARG, "feat_out is NULL");
+  if (p->released) return fail(p, ISDF_ERR_STATE, "the plan's basis values were released (isdf_release_fit)");
   if (p->opt.local_grids) return fail(p, ISDF_ERR_ARG, "the learned proposal does not take options.local_grids");
   const size_t n = size_t(p->ntot) * 8;
   float* d = feat_out;
@@ -1194,6 +1233,7 @@ isdf_status isdf_propose(isdf_plan_t h, const float* params, const int64_t* quot
   if (!h) return ISDF_ERR_ARG;
   Plan* p = &h->p;
   if (!params || !quota || !cand_out) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_propose");
+  if (p->released) return fail(p, ISDF_ERR_STATE, "the plan's basis values were released (isdf_release_fit)");
   if (p->opt.local_grids) return fail(p, ISDF_ERR_ARG, "the learned proposal does not take options.local_grids");
   std::vector<int64_t> q(p->nlev);
   int64_t ncand = 0;
@@ -1220,7 +1260,7 @@ isdf_status isdf_propose_residual(isdf_plan_t h, const int64_t* quota, int64_t* 
   Plan* p = &h->p;
   if (!quota || !cand_out) return fail(p, ISDF_ERR_ARG, "invalid arguments to isdf_propose_residual");
   if (p->opt.local_grids) return fail(p, ISDF_ERR_ARG, "the learned proposal does not take options.local_grids");
-  if (p->state < 2) return fail(p, ISDF_ERR_STATE, "isdf_propose_residual needs isdf_fit first");
+  if (p->state < 2 || p->released) return fail(p, ISDF_ERR_STATE, "isdf_propose_residual needs isdf_fit first");
   std::vector<int64_t> q(p->nlev);
   int64_t ncand = 0;
   for (int l = 0; l < p->nlev; ++l) {
@@ -1258,7 +1298,8 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
   OzOperand a, b;
   double* work = nullptr;
   int* err = nullptr;
-  isdf_status st = oz_alloc(nullptr, a, M, K, 128, slices, "A slices");
+  // 8 digits: A's digit planes in int8 (half the stream; expanded on chip)
+  isdf_status st = oz_alloc(nullptr, a, M, K, 128, slices, "A slices", slices == 8);
   if (!st) st = oz_alloc(nullptr, b, N, K, oz_bn(slices), slices, "B slices");
   if (!st && splits > 1) st = dalloc_t(nullptr, &work, size_t(splits) * M * N, "split-K partials");
   if (!st) st = dalloc_t(nullptr, &err, 1, "error word");

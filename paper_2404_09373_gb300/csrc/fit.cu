@@ -61,7 +61,7 @@ __global__ void k_fill_kw(int nL, int nG, double* kw) {
 isdf_status fit_products_tc(Plan* p, Level& lv, int k, const double* phiP, double* zct, double* y, const double* li,
                             int64_t ng) {
   cudaStream_t s = p->stream;
-  const int S = 5;
+  const int S = p->fit_slices;
   OzOperand aL, aG, bL, bG, az, bli;
   double* kw = nullptr;
   isdf_status st = ISDF_OK;
@@ -107,7 +107,7 @@ isdf_status fit_products_tc(Plan* p, Level& lv, int k, const double* phiP, doubl
 // (which may be zct itself).
 isdf_status fit_solve_tc(Plan* p, int k, const double* zct, double* y, const double* li, int64_t ng, double* xi_out) {
   cudaStream_t s = p->stream;
-  const int S = 5;
+  const int S = p->fit_slices;
   OzOperand a, b;
   isdf_status st;
   Prof pr(p, "fit_solve", (xi_out ? 2.0 : 1.0) * double(k) * double(k + 1) * double(ng), "flop", kLaunchesInside);

@@ -60,10 +60,11 @@ struct ProfEvent {
   double work = 0.0;
   const char* unit = "flop";
   int64_t launches = 0;
+  double flop = 0.0;  // FP64-equivalent flops of a byte-counted tensor-core family (else 0)
 };
 struct KStat {
   int64_t launches = 0;
-  double ms = 0.0, work = 0.0;
+  double ms = 0.0, work = 0.0, flop = 0.0;
   std::string unit;
 };
 
@@ -88,6 +89,7 @@ struct Plan {
   int nlev = 0;
   Level lev[ISDF_MAX_LEVELS];
   int state = 0;  // 0 planned, 1 selected, 2 fitted, 3 Coulomb done
+  bool released = false;  // isdf_release_fit: only the exchange's inputs remain
   // selection (all levels concatenated)
   int64_t ntot = 0;
   int64_t off[ISDF_MAX_LEVELS + 1] = {0};
@@ -125,6 +127,10 @@ struct Plan {
   std::vector<Plan*> sub;
   double r_max = 0.0;
   int sel_lo = 0;  // first level of this plan's own greedy selection
+  // BF16 digits of the fit's tensor-core products: 5 for the full-cell levels;
+  // 8 (FP64-grade) on an atom's local grid, where a threshold-driven
+  // selection leaves CC^T conditioned up to the inverse of the threshold
+  int fit_slices = 5;
   // profiling
   std::vector<ProfEvent> pend;
   std::map<std::string, KStat> stats;
@@ -233,14 +239,21 @@ inline OzMap oz_stride(int64_t st) {
 }
 constexpr int kOzBK = 32;  // k values per digit tile (two K = 16 tcgen05.mma steps, one pipeline stage)
 struct OzOperand {
-  void* tiles = nullptr;  // __nv_bfloat16 slices
+  void* tiles = nullptr;  // digit slices: __nv_bfloat16, or int8 when eb == 1
   int* exps = nullptr;    // per-row power-of-two scale
   int64_t rows = 0, K = 0, nrt = 0, nkt = 0;
   int64_t kst = 0;        // k-tile stride of the tile array (capacity in k tiles)
   int rt = 0, S = 0;
+  // bytes per digit: 2 (BF16 slices) or 1 (int8 slices of an 8-digit A
+  // operand, expanded to BF16 in shared memory by the product; their row
+  // scales are two powers of two higher (54 fraction bits), so every digit,
+  // the leading one included, lies in [-64, 63])
+  int eb = 2;
 };
 int oz_bn(int S);
-isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, int S, const char* what);
+isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, int S, const char* what,
+                     bool i8 = false);
+int64_t oz_tile_bytes(const OzOperand& op);  // bytes of the whole tile array
 void oz_free(OzOperand& op);
 // X(r, k) = mul * kw[k] * src[r*sr + k*sk]  (kw nullable)
 void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s);

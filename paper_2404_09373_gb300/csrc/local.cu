@@ -88,6 +88,7 @@ isdf_status local_setup(Plan* p, double alpha_min) {
     q->opt.coarse_sinc = 0;
     q->opt.profile = 0;
     q->fault = p->fault;
+    q->fit_slices = 8;
     for (int a = 0; a < 3; ++a) q->edge[a] = p->edge[a];
     q->omega = p->omega;
     q->image_tol = p->image_tol;

@@ -654,12 +654,14 @@ __global__ void k_blk_combine(double* __restrict__ aL, const double* __restrict_
 }
 
 // per-candidate power-of-two bound of the factor rows: sum_k L[t,k]^2 <= d0(t)
+// Fixed row scales of the factor columns: |L[c][k]| <= sqrt(d0_c); the int8
+// digit planes take two powers of two more (see OzOperand)
 __global__ void k_fac_exps(const double* __restrict__ d0c, int64_t nc, int64_t npad, int* __restrict__ exps) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= npad) return;
   int e = 0;
   if (t < nc && d0c[t] > 0.0) frexp(sqrt(d0c[t]) * (1.0 + 0x1p-20), &e);
-  exps[t] = e;
+  exps[t] = e + 2;
 }
 
 __global__ void k_blk_begin(SelState* st) {
@@ -1165,6 +1167,18 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
   *aborted = false;
   int64_t nc[ISDF_MAX_LEVELS] = {0, 0, 0, 0};
   for (int l = 0; l < nlev; ++l) nc[l] = nc_in[l];
+  // with the cooperative block steps the factor storage of a level starts at
+  // a quarter of nip and grows between blocks (a level rarely takes more);
+  // the captured graph of the other form holds fixed arrays: full capacity
+  bool growable = false;
+  {
+    int d = 0, coop_attr = 0, spsm = 0;
+    cudaGetDevice(&d);
+    cudaDeviceGetAttribute(&coop_attr, cudaDevAttrCooperativeLaunch, d);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&spsm, k_blk_steps, 512, 0);
+    cudaGetLastError();
+    growable = coop_attr && spsm > 0;
+  }
   int* cur_cidx[ISDF_MAX_LEVELS] = {nullptr, nullptr, nullptr, nullptr};  // after compaction: owned here
   for (int l = 0; l < nlev; ++l) cur_cidx[l] = cidx[l];
   std::vector<int*> own_cidx;
@@ -1224,6 +1238,8 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
     dfree(lv.fac);
     lv.fac = nullptr;
     lv.fac_cap = std::min<int64_t>(nip, nc[l]);
+    if (growable)
+      lv.fac_cap = std::min<int64_t>(lv.fac_cap, std::max<int64_t>(4 * int64_t(smax) + 1, nip / 4));
     if ((st = dalloc_t(p, &lv.fac, size_t(std::max<int64_t>(lv.fac_cap * nc[l], 1)), "selection factor columns")))
       return bail(st);
     P.fac[l] = lv.fac;
@@ -1246,14 +1262,16 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
     }
     Q.gpos[l] = b.gpos;
     const int bn = oz_bn(kSlices);
-    if ((st = oz_alloc(p, b.aL, nc[l], std::max(lv.nL, 1), 128, kSlices, "selection slices")) ||
+    // candidate-side digit planes in int8 (half the bytes of the stream the
+    // products read), the speculative set's in BF16
+    if ((st = oz_alloc(p, b.aL, nc[l], std::max(lv.nL, 1), 128, kSlices, "selection slices", true)) ||
         (st = oz_alloc(p, b.bL, smax, std::max(lv.nL, 1), bn, kSlices, "selection slices")) ||
-        (st = oz_alloc(p, b.aF, nc[l], lv.fac_cap, 128, kSlices, "selection slices")) ||
+        (st = oz_alloc(p, b.aF, nc[l], lv.fac_cap, 128, kSlices, "selection slices", true)) ||
         (st = oz_alloc(p, b.bF, smax, lv.fac_cap, bn, kSlices, "selection slices")) ||
         (st = dalloc_t(p, &b.cL, size_t(smax) * nc[l], "selection columns")) ||
         (st = dalloc_t(p, &b.cF, size_t(smax) * nc[l], "selection columns")))
       return bail(st);
-    if (lv.nN > 0 && ((st = oz_alloc(p, b.aN, nc[l], lv.nN, 128, kSlices, "selection slices")) ||
+    if (lv.nN > 0 && ((st = oz_alloc(p, b.aN, nc[l], lv.nN, 128, kSlices, "selection slices", true)) ||
                       (st = oz_alloc(p, b.bN, smax, lv.nN, bn, kSlices, "selection slices")) ||
                       (st = dalloc_t(p, &b.cN, size_t(smax) * nc[l], "selection columns"))))
       return bail(st);
@@ -1264,7 +1282,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
         oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, cidx[l], b.aN, 0, b.aN.nkt * (kOzBK / 8), false, s);
       // factor-column digits are written group by group as columns appear:
       // groups not yet written must read as zero
-      cudaMemsetAsync(b.aF.tiles, 0, size_t(oz_tile_elems(nc[l], lv.fac_cap, 128, kSlices)) * 2, s);
+      cudaMemsetAsync(b.aF.tiles, 0, size_t(oz_tile_bytes(b.aF)), s);
       // factor rows are bounded by sqrt(d0): fixed scales, columns appended in place
       k_fac_exps<<<unsigned((b.aF.nrt * 128 + 255) / 256), 256, 0, s>>>(p->d_diag + P.coff[l], nc[l], b.aF.nrt * 128,
                                                                          b.aF.exps);
@@ -1426,7 +1444,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
         if (lv.nN > 0)
           oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, ci, b.aN, 0, b.aN.nkt * (kOzBK / 8), false, s);
         const int64_t kst_keep = b.aF.kst;
-        cudaMemsetAsync(b.aF.tiles, 0, size_t(b.aF.nrt) * size_t(kst_keep) * kSlices * 128 * kOzBK * 2, s);
+        cudaMemsetAsync(b.aF.tiles, 0, size_t(b.aF.nrt) * size_t(kst_keep) * kSlices * 128 * kOzBK * b.aF.eb, s);
         k_fac_exps<<<unsigned((b.aF.nrt * 128 + 255) / 256), 256, 0, s>>>(d0c, nn, b.aF.nrt * 128, b.aF.exps);
         count_launches(1);
         if (h.kl[l] > 0) oz_slice_ex(fnew, 1, nn, nullptr, b.aF, 0, (h.kl[l] + 7) / 8, true, s);
@@ -1459,9 +1477,63 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
     ++p->sel_compactions;
     return ISDF_OK;
   };
+  // ---- factor capacity: before a block that could fill a level (at most
+  // smax block steps and one single step), that level's factor columns move
+  // to twice the storage and their digits are sliced again (fixed scales
+  // from sqrt(d0), as at set-up)
+  auto grow = [&]() -> isdf_status {
+    isdf_status gst;
+    for (int l = 0; l < nlev; ++l) {
+      Level& lv = p->lev[l];
+      LevBuf& b = lb[l];
+      if (!nc[l]) continue;
+      const int64_t full = std::min<int64_t>(nip, nc[l]);
+      const int64_t need = std::min<int64_t>(full, int64_t(h.kl[l]) + smax + 1);
+      if (need <= lv.fac_cap) continue;
+      const int64_t cap = std::min<int64_t>(full, std::max<int64_t>(2 * lv.fac_cap, need));
+      const int kl = h.kl[l];
+      double *fnew = nullptr, *d0c = nullptr;
+      if ((gst = dalloc_t(p, &fnew, size_t(cap * nc[l]), "selection factor columns"))) return gst;
+      if (kl > 0)
+        cudaMemcpyAsync(fnew, lv.fac, sizeof(double) * size_t(kl) * size_t(nc[l]), cudaMemcpyDeviceToDevice, s);
+      const double* d0src = d0full + p->off[l];
+      if (cur_cidx[l]) {
+        if ((gst = dalloc_t(p, &d0c, size_t(nc[l]), "initial residuals"))) {
+          dfree(fnew);
+          return gst;
+        }
+        k_gather_diag<<<unsigned((nc[l] + 255) / 256), 256, 0, s>>>(d0full + p->off[l], cur_cidx[l], nc[l], d0c);
+        count_launches(1);
+        d0src = d0c;
+      }
+      oz_free(b.aF);
+      oz_free(b.bF);
+      if ((gst = oz_alloc(p, b.aF, nc[l], cap, 128, kSlices, "selection slices", true)) ||
+          (gst = oz_alloc(p, b.bF, smax, cap, oz_bn(kSlices), kSlices, "selection slices"))) {
+        dfree(fnew), dfree(d0c);
+        return gst;
+      }
+      cudaMemsetAsync(b.aF.tiles, 0, size_t(oz_tile_bytes(b.aF)), s);
+      k_fac_exps<<<unsigned((b.aF.nrt * 128 + 255) / 256), 256, 0, s>>>(d0src, nc[l], b.aF.nrt * 128, b.aF.exps);
+      count_launches(1);
+      b.aF.K = kl;
+      if (kl > 0) oz_slice_ex(fnew, 1, nc[l], nullptr, b.aF, 0, (kl + 7) / 8, true, s);
+      b.sliced = kl;
+      gst = cuda_check(p, cudaStreamSynchronize(s), "factor capacity");
+      dfree(lv.fac);
+      dfree(d0c);
+      lv.fac = fnew;
+      lv.fac_cap = cap;
+      P.fac[l] = fnew;
+      if (gst) return gst;
+    }
+    BP.P = P;
+    return ISDF_OK;
+  };
   int64_t nblocks = 0, nplain = 0;
   std::vector<int> hcount(ISDF_MAX_LEVELS + 1);
   while (true) {
+    if (growable && (st = grow())) return bail(st);
     // ---- 1. the speculative set S
     {
       Prof pr(p, "select_spec", double(P.ntot) * 8.0, "byte", 4);
@@ -1503,6 +1575,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
       }
       // algorithmic traffic: the candidates' FP64 basis values and factor rows, read once per block
       Prof pr(p, "select_gemm", 8.0 * double(nc[l]) * (lv.nL + lv.nN + kb), "byte", 3);
+      pr.e.flop = 2.0 * double(nc[l]) * double(sl) * double(lv.nL + lv.nN + kb);
       oz_gemm(b.aL, b.bL, b.cL, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
       if (lv.nN > 0) oz_gemm(b.aN, b.bN, b.cN, nc[l], 1, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
       if (kb > 0) {

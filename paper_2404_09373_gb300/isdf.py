@@ -62,6 +62,7 @@ EXPORTED = [
     "isdf_exchange_graph_run",
     "isdf_exchange_graph_destroy",
     "isdf_autotune_table",
+    "isdf_release_fit",
 ]
 
 
@@ -179,6 +180,8 @@ def load_library(build_if_missing: bool = True):
     lib.isdf_autotune_table.restype = ctypes.c_char_p
     lib.isdf_save.argtypes = [c_void_p, ctypes.c_char_p]
     lib.isdf_save.restype = c_int
+    lib.isdf_release_fit.argtypes = [c_void_p]
+    lib.isdf_release_fit.restype = c_int
     lib.isdf_load.argtypes = [c_void_p, ctypes.c_char_p]
     lib.isdf_load.restype = c_int
     lib.isdf_exchange_occ.argtypes = [c_void_p, c_void_p, c_int, c_void_p, POINTER(c_double)]
@@ -451,6 +454,11 @@ def isdf_autotune_table():
     import json
 
     return json.loads(load_library().isdf_autotune_table().decode())
+
+
+def isdf_release_fit(plan: Plan):
+    """Free the buffers the exchange build does not read (after isdf_coulomb)."""
+    plan._check(plan._lib.isdf_release_fit(plan.handle))
 
 
 def isdf_save(plan: Plan, path):

@@ -114,3 +114,34 @@ def test_autotuner_records_measured_split_choices(batch_and_oracle):
     for row in table:
         assert row["splits"] in (1, 2, 4, 8, 16, 32, 64) or row["splits"] >= 1
         assert row["ms"] > 0.0 and row["M"] > 0 and row["N"] > 0 and row["k_tiles"] > 0
+
+
+@pytest.mark.parametrize("sinc", [0, 1])
+def test_release_fit_keeps_the_exchange(sinc, tmp_path):
+    """isdf_release_fit frees the basis values, fit and spectra: the exchange
+    builds afterwards are bitwise those before, saving still works, and the
+    stages that need the basis values refuse with ISDF_ERR_STATE."""
+    sysd, C, nip = reduced_batch()[1]
+    plan = B.isdf_plan(sysd, {"precision": 1, "prefilter": 1, "coarse_sinc": sinc})
+    try:
+        nsel = nip // 2 if sinc else nip
+        piv, _ = B.isdf_select_points(plan, nsel)
+        B.isdf_fit(plan, piv)
+        B.isdf_coulomb(plan)
+        K1, E1 = B.isdf_exchange(plan, C)
+        KC1, _ = B.isdf_exchange_occ(plan, C)
+        assert B.load_library().isdf_get_size(plan.handle, B.GET_PHI_LEVEL0) > 0
+        B.isdf_release_fit(plan)
+        assert B.load_library().isdf_get_size(plan.handle, B.GET_PHI_LEVEL0) == 0
+        K2, E2 = B.isdf_exchange(plan, C)
+        KC2, _ = B.isdf_exchange_occ(plan, C)
+        assert np.array_equal(K1, K2) and E1 == E2 and np.array_equal(KC1, KC2)
+        if not sinc:
+            B.isdf_save(plan, str(tmp_path / "f.isdf"))
+        for call in (lambda: B.isdf_select_points(plan, nsel), lambda: B.isdf_fit(plan, piv),
+                     lambda: B.isdf_coulomb(plan)):
+            with pytest.raises(B.IsdfError) as e:
+                call()
+            assert e.value.status == B.ISDF_ERR_STATE
+    finally:
+        plan.close()

@@ -39,13 +39,49 @@ def gpu_local(sysd, C, nip, opts):
         plan.close()
 
 
-def check(g, o, C, natom, precision, sinc=False):
+def pivot_gram(o, sysd):
+    """Block-diagonal CC^T = M[P, P] over the level-ordered pivots: every
+    atom's local block, then every coarser level's, from the oracle's own
+    basis values at the pivots."""
+    from oracle import isdf as O
+
+    blocks = []
+    atoms = o["local_pivots"] >> B.LOCAL_ATOM_SHIFT
+    for A, blk in enumerate(o["blocks"]):
+        b = o["local_pivots"][atoms == A] & ((1 << B.LOCAL_ATOM_SHIFT) - 1)
+        P = np.searchsorted(blk["box_index"], b)
+        sub = {"PhiL": blk["PhiL"][:, P], "PhiN": blk["PhiN"][:, P]}
+        blocks.append(O.m_columns(sub, np.arange(P.size)))
+    funcs = o["funcs"]
+    main = o["pivots"]
+    for lev in range(1, int(main.max() >> B.PIVOT_SHIFT) + 1 if main.size else 1):
+        P = main[(main >> B.PIVOT_SHIFT) == lev] & ((1 << B.PIVOT_SHIFT) - 1)
+        if not P.size:
+            continue
+        L, N, _ = O.level_sets(funcs, lev)
+        sub = {"PhiL": O.basis_on_level(sysd, funcs, L, lev)[:, P], "PhiN": O.basis_on_level(sysd, funcs, N, lev)[:, P]}
+        blocks.append(O.m_columns(sub, np.arange(P.size)))
+    n = sum(b.shape[0] for b in blocks)
+    M = np.zeros((n, n))
+    c = 0
+    for b in blocks:
+        M[c:c + b.shape[0], c:c + b.shape[0]] = b
+        c += b.shape[0]
+    return M
+
+
+def check(g, o, C, natom, precision, sinc=False, sysd=None):
     nloc = o["local_pivots"].size
     # pivots: every atom's sequence, then the coarser levels' greedy ones
     assert np.array_equal(g["pivots"][:nloc], o["local_pivots"])
     assert np.array_equal(g["pivots"][nloc:], o["pivots"])
-    assert np.allclose(g["dvals"][:nloc], o["local_dvals"], rtol=1e-9, atol=0)
-    assert np.allclose(g["dvals"][nloc:], o["dvals"], rtol=1e-9, atol=0)
+    # a pivot value is a difference d_0 - sum L^2: its rounding is relative to
+    # the atom's (level's) largest initial residual, not to itself
+    atoms = o["local_pivots"] >> B.LOCAL_ATOM_SHIFT
+    for A in range(natom):
+        ga, oa = g["dvals"][:nloc][atoms == A], o["local_dvals"][atoms == A]
+        assert np.max(np.abs(ga - oa), initial=0.0) <= 1e-12 * oa.max()
+    assert np.max(np.abs(g["dvals"][nloc:] - o["dvals"])) <= 1e-12 * o["dvals"].max()
     assert np.array_equal(g["per_atom"], np.bincount(o["local_pivots"] >> B.LOCAL_ATOM_SHIFT, minlength=natom))
     b = o["blocks"][0]["box"]
     assert g["box"][0] == pytest.approx(o["r_max"], rel=1e-15) and list(g["box"][1:]) == list(b)
@@ -53,11 +89,19 @@ def check(g, o, C, natom, precision, sinc=False):
     nf = g["XL"].shape[1]
     assert np.max(np.abs(g["XL"] - o["XL"][:, :nf])) <= 1e-13 and np.max(np.abs(g["XN"] - o["XN"][:, :nf])) <= 1e-13
     if not sinc:
-        # precision 1: V = W (ZC^T v ZC) W with W = (CC^T)^-1 per atom, whose
-        # conditioning (up to the inverse of local_tol) scales the products'
-        # rounding; K below is held to the absolute bar
-        vr = np.max(np.abs(g["V"] - o["V"])) / np.max(np.abs(o["V"]))
-        assert vr <= (1e-9 if precision == 0 else 1e-5), vr
+        dV = g["V"] - o["V"]
+        if precision == 0:
+            vr = np.max(np.abs(dV)) / np.max(np.abs(o["V"]))
+            assert vr <= 1e-9, vr
+        else:
+            # V = W (ZC^T v ZC) W with W = (CC^T)^-1 per atom and per level:
+            # W's conditioning (up to the inverse of local_tol on every atom)
+            # multiplies the products' rounding twice in the forward error, so
+            # V is compared in the conditioning-free form CC^T dV CC^T (the
+            # Coulomb matrix of the pair-density columns ZC)
+            M = pivot_gram(o, sysd)
+            vr = np.max(np.abs(M @ dV @ M)) / np.max(np.abs(M @ o["V"] @ M))
+            assert vr <= 1e-7, vr
     dk = np.max(np.abs(g["K"] - o["K"]))
     assert dk <= 1e-6, dk
     assert abs(g["Ex"] - o["Ex"]) <= 1e-6 * natom
@@ -76,7 +120,7 @@ def test_local_grids_match_oracle(precision, block):
     o = oracle.run_local(sysd, C, 3 * N, local_tol=1e-6, local_cap=64)
     g = gpu_local(sysd, C, 3 * N, {"precision": precision, "local_grids": 1, "local_tol": 1e-6, "local_cap": 64,
                                    "prefilter": 1, "select_block": block})
-    check(g, o, C, 8, precision)
+    check(g, o, C, 8, precision, sysd=sysd)
 
 
 def test_local_grids_two_cells_and_cap():
@@ -87,7 +131,7 @@ def test_local_grids_two_cells_and_cap():
     assert np.all(np.bincount(o["local_pivots"] >> B.LOCAL_ATOM_SHIFT) == 16)
     g = gpu_local(sysd, C, 2 * N, {"precision": 1, "local_grids": 1, "local_tol": 1e-9, "local_cap": 16,
                                    "prefilter": 1, "select_block": 96})
-    check(g, o, C, 16, 1)
+    check(g, o, C, 16, 1, sysd=sysd)
 
 
 def test_local_grids_with_the_sinc_coarse_level():
@@ -98,7 +142,7 @@ def test_local_grids_with_the_sinc_coarse_level():
     o = oracle.run_local(sysd, C, 2 * N, local_tol=1e-6, local_cap=64, sinc=True)
     g = gpu_local(sysd, C, 2 * N, {"precision": 1, "local_grids": 1, "coarse_sinc": 1, "local_tol": 1e-6,
                                    "local_cap": 64, "prefilter": 1})
-    check(g, o, C, 8, 1, sinc=True)
+    check(g, o, C, 8, 1, sinc=True, sysd=sysd)
 
 
 def test_local_grids_at_the_full_resolution():
@@ -110,7 +154,7 @@ def test_local_grids_at_the_full_resolution():
     o = oracle.run_local(sysd, C, 3 * N, local_tol=1e-8, local_cap=128)
     g = gpu_local(sysd, C, 3 * N, {"precision": 1, "local_grids": 1, "local_tol": 1e-8, "local_cap": 128,
                                    "prefilter": 1, "select_block": 96})
-    check(g, o, C, 8, 1)
+    check(g, o, C, 8, 1, sysd=sysd)
 
 
 def test_local_grids_refusals():
