@@ -294,6 +294,9 @@ def cpu_baseline_sample(reps=1):
         out["value"] = full["s_iter"] * t / full["sample_s"]
         out["full_run"] = {"s_iter": full["s_iter"], "stages_s": full["stages"], "host": full["host"],
                            "threads": full["cpu_threads"], "sample_s": full["sample_s"]}
+        if full.get("sample_s_1thread"):
+            # one core: the recording host's sample with the BLAS on one thread
+            out["one_core_estimate_s_iter"] = out["value"] * full["sample_s_1thread"] / full["sample_s"]
     else:
         out["value"] = None
     return out

@@ -19,7 +19,8 @@ Run:  python tests/golden/make_diamond2x2x2.py   (about 60 GB of host memory)
       python tests/golden/make_diamond2x2x2.py --augment   (adds cond(CC^T) per
       level to an existing result)
       python tests/golden/make_diamond2x2x2.py --time-sample   (records the time
-      of oracle/sample.py's bounded sample on this host beside the full run)
+      of oracle/sample.py's bounded sample on this host beside the full run,
+      with all BLAS threads and with one)
 """
 from __future__ import annotations
 
@@ -139,14 +140,21 @@ def make(sysd, C, nip, prefix, col_batch=256, log=print):
 def time_sample(prefix, reps=3):
     """Time the bounded sample of oracle/sample.py on this host (median of
     ``reps``) and record it beside the full run, so that other hosts can
-    scale their own sample time to the full run."""
+    scale their own sample time to the full run; also the same sample with
+    the BLAS limited to one thread (threadpoolctl), for a one-core estimate."""
+    from threadpoolctl import threadpool_limits
+
     from oracle import sample as OS
 
     sysd, C, _ = S.config(2)
-    t = OS.median_seconds(OS.Sample(sysd, C), reps)
+    smp = OS.Sample(sysd, C)
+    t = OS.median_seconds(smp, reps)
+    with threadpool_limits(limits=1):
+        t1 = OS.median_seconds(smp, reps)
     meta = json.load(open(prefix + ".json"))
     meta["sample_s"] = t
     meta["sample_threads"] = OS.threads()
+    meta["sample_s_1thread"] = t1
     with open(prefix + ".json", "w") as fh:
         json.dump(meta, fh, indent=1)
     return t
