@@ -441,10 +441,7 @@ isdf_status isdf_propose_residual(isdf_plan_t plan, const int64_t* quota, int64_
  * summed exactly (512-wide chunks, integer accumulation) and the rest, below
  * 2^-42 of the result, in FP32: with 7 the error is below 2^-47 * K *
  * max_k|A[m,k]| * max_k|B[n,k]|, with 8 (FP64-grade) below 2^-52 * K *
- * max_k|A[m,k]| * max_k|B[n,k]| + 2^-53 |C[m,n]|.  With 8, A's digit planes
- * are stored as 8-bit integers (its row scale two powers of two higher, 54
- * fraction bits) and expanded to BF16 in shared memory, halving A's stream
- * (the 8-digit bound above covers this rounding).
+ * max_k|A[m,k]| * max_k|B[n,k]| + 2^-53 |C[m,n]|.
  * splits > 1 divides K over that many CTAs (needs splits*M*N*8 bytes of
  * scratch, allocated by the call).  Enqueued on `stream`; returns after the
  * stream is idle.  A pipeline wait that exceeds its bound returns

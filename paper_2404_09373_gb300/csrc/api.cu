@@ -1298,8 +1298,7 @@ isdf_status isdf_gemm_f64(const double* A, const double* B, double* C, int64_t M
   OzOperand a, b;
   double* work = nullptr;
   int* err = nullptr;
-  // 8 digits: A's digit planes in int8 (half the stream; expanded on chip)
-  isdf_status st = oz_alloc(nullptr, a, M, K, 128, slices, "A slices", slices == 8);
+  isdf_status st = oz_alloc(nullptr, a, M, K, 128, slices, "A slices");
   if (!st) st = oz_alloc(nullptr, b, N, K, oz_bn(slices), slices, "B slices");
   if (!st && splits > 1) st = dalloc_t(nullptr, &work, size_t(splits) * M * N, "split-K partials");
   if (!st) st = dalloc_t(nullptr, &err, 1, "error word");

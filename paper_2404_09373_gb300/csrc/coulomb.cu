@@ -320,7 +320,12 @@ isdf_status coulomb_run(Plan* p) {
     lv.nq = int64_t(lv.nh[0]) * lv.nh[1] * lv.nh[2];
     if (lv.k == 0) continue;
     if ((st = dalloc_t(p, &lv.spec, size_t(lv.k) * lv.nq, "spectra"))) return st;
-    if (p->opt.precision == 1 && p->fault != "fft_plan" && rfft3_df_supported(lv.n[0], lv.n[1], lv.n[2])) {
+    // local grids' level 0 keeps the FP64 transform: W = (CC^T)^-1 of a
+    // threshold-driven atom selection (cond up to the inverse of local_tol)
+    // would amplify the double-float transform's ~1e-12 relative error
+    const bool fp64_fft = p->opt.local_grids && l == 0;
+    if (p->opt.precision == 1 && p->fault != "fft_plan" && !fp64_fft &&
+        rfft3_df_supported(lv.n[0], lv.n[1], lv.n[2])) {
       // double-float transform on the FP32 pipes (the FP64 one is bound by the FP64 rate)
       Prof pr(p, "coulomb_fft", double(lv.k) * (8.0 * double(lv.ng) + 16.0 * double(lv.nq)), "byte", 3);
       if ((st = rfft3_df(p, lv.zct ? lv.zct : lv.xiT, lv.n[0], lv.n[1], lv.n[2], lv.k, lv.spec, s))) return st;

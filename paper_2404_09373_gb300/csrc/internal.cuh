@@ -239,20 +239,14 @@ inline OzMap oz_stride(int64_t st) {
 }
 constexpr int kOzBK = 32;  // k values per digit tile (two K = 16 tcgen05.mma steps, one pipeline stage)
 struct OzOperand {
-  void* tiles = nullptr;  // digit slices: __nv_bfloat16, or int8 when eb == 1
+  void* tiles = nullptr;  // __nv_bfloat16 slices
   int* exps = nullptr;    // per-row power-of-two scale
   int64_t rows = 0, K = 0, nrt = 0, nkt = 0;
   int64_t kst = 0;        // k-tile stride of the tile array (capacity in k tiles)
   int rt = 0, S = 0;
-  // bytes per digit: 2 (BF16 slices) or 1 (int8 slices of an 8-digit A
-  // operand, expanded to BF16 in shared memory by the product; their row
-  // scales are two powers of two higher (54 fraction bits), so every digit,
-  // the leading one included, lies in [-64, 63])
-  int eb = 2;
 };
 int oz_bn(int S);
-isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, int S, const char* what,
-                     bool i8 = false);
+isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, int S, const char* what);
 int64_t oz_tile_bytes(const OzOperand& op);  // bytes of the whole tile array
 void oz_free(OzOperand& op);
 // X(r, k) = mul * kw[k] * src[r*sr + k*sk]  (kw nullable)

@@ -353,7 +353,7 @@ __device__ __forceinline__ void oz_digit_group(const double* __restrict__ src, c
                                                int64_t rows, int64_t K, const double* __restrict__ kw, double mul,
                                                const int* __restrict__ exps, int rt, int64_t kst,
                                                const int* __restrict__ ridx, __nv_bfloat16* __restrict__ tiles, int r,
-                                               int64_t kg, bool i8) {
+                                               int64_t kg) {
   const bool live = r < rows;
   const int e = live ? exps[r] : 0;
   const double* row = src + (live ? row_base(rm, ridx, r) : 0);
@@ -392,7 +392,7 @@ __device__ __forceinline__ void oz_digit_group(const double* __restrict__ src, c
   const int64_t jt = kg / (kBK / 8);
   const int kc = int(kg % (kBK / 8));
   const int64_t tile_elems = int64_t(rt) * kBK;
-  const int64_t base_e = ((int64_t(it) * kst + jt) * S) * tile_elems;  // element offset of the tile group
+  __nv_bfloat16* base = tiles + ((int64_t(it) * kst + jt) * S) * tile_elems;
   const int inner = (rr >> 3) * (8 * kBK) + kc * 64 + (rr & 7) * 8;  // element offset in a tile
   // Balanced digits from the least significant end (in [-64, 63]; the top one
   // takes the rest, |d_0| <= 128), one slice at a time.  |X| < 2^(7S + 1), so
@@ -416,25 +416,14 @@ __device__ __forceinline__ void oz_digit_group(const double* __restrict__ src, c
       } else {
         dig = Y[u];
       }
-      b[u] = i8 ? (uint32_t(dig) & 0xFFu) : bf16_bits_of_small(dig);
+      b[u] = bf16_bits_of_small(dig);
     }
-    const int64_t off = base_e + int64_t(s) * tile_elems + inner;
-    if (i8) {
-      // the row scale is two powers of two above the row's largest value, so
-      // the leading digit is at most 33 in magnitude: every digit lies in
-      // [-64, 63], which the product's on-chip expansion relies on
-      uint2 w;
-      w.x = b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24);
-      w.y = b[4] | (b[5] << 8) | (b[6] << 16) | (b[7] << 24);
-      *reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(tiles) + off) = w;
-    } else {
-      uint4 w;
-      w.x = __byte_perm(b[0], b[1], 0x7632);
-      w.y = __byte_perm(b[2], b[3], 0x7632);
-      w.z = __byte_perm(b[4], b[5], 0x7632);
-      w.w = __byte_perm(b[6], b[7], 0x7632);
-      *reinterpret_cast<uint4*>(tiles + off) = w;
-    }
+    uint4 w;
+    w.x = __byte_perm(b[0], b[1], 0x7632);
+    w.y = __byte_perm(b[2], b[3], 0x7632);
+    w.z = __byte_perm(b[4], b[5], 0x7632);
+    w.w = __byte_perm(b[6], b[7], 0x7632);
+    *reinterpret_cast<uint4*>(base + int64_t(s) * tile_elems + inner) = w;
   }
 }
 
@@ -448,20 +437,20 @@ template <int S>
 __global__ void k_oz_digits(const double* __restrict__ src, OzMap rm, OzMap km, int64_t rows, int64_t K,
                             const double* __restrict__ kw, double mul, const int* __restrict__ exps, int rt,
                             int64_t nrt, int64_t kg0, int64_t ngrp, int64_t kst, int order,
-                            const int* __restrict__ ridx, __nv_bfloat16* __restrict__ tiles, bool i8) {
+                            const int* __restrict__ ridx, __nv_bfloat16* __restrict__ tiles) {
   const int64_t rows_pad = nrt * rt;
   if (order == 0) {
     const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
     if (r >= rows_pad) return;
     for (int64_t g = blockIdx.y; g < ngrp; g += gridDim.y)
-      oz_digit_group<S>(src, rm, km, rows, K, kw, mul, exps, rt, kst, ridx, tiles, int(r), kg0 + g, i8);
+      oz_digit_group<S>(src, rm, km, rows, K, kw, mul, exps, rt, kst, ridx, tiles, int(r), kg0 + g);
   } else {
     const int lane = threadIdx.x & 31;
     const int64_t g = (int64_t(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 4 + (lane >> 3);
     if (g >= ngrp) return;
     for (int64_t g8 = blockIdx.y; g8 * 8 < rows_pad; g8 += gridDim.y)
       oz_digit_group<S>(src, rm, km, rows, K, kw, mul, exps, rt, kst, ridx, tiles, int(g8 * 8 + (lane & 7)),
-                        kg0 + g, i8);
+                        kg0 + g);
   }
 }
 
@@ -506,16 +495,16 @@ void launch_digits(const double* src, OzMap rm, OzMap km, const double* kw, doub
   __nv_bfloat16* t = static_cast<__nv_bfloat16*>(op.tiles);
   if (op.S == 7)
     k_oz_digits<7><<<grid, 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.rt, op.nrt, kg0, ngrp,
-                                        op.kst, order, ridx, t, op.eb == 1);
+                                        op.kst, order, ridx, t);
   else if (op.S == 5)
     k_oz_digits<5><<<grid, 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.rt, op.nrt, kg0, ngrp,
-                                        op.kst, order, ridx, t, op.eb == 1);
+                                        op.kst, order, ridx, t);
   else if (op.S == 6)
     k_oz_digits<6><<<grid, 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.rt, op.nrt, kg0, ngrp,
-                                        op.kst, order, ridx, t, op.eb == 1);
+                                        op.kst, order, ridx, t);
   else
     k_oz_digits<8><<<grid, 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, op.exps, op.rt, op.nrt, kg0, ngrp,
-                                        op.kst, order, ridx, t, op.eb == 1);
+                                        op.kst, order, ridx, t);
 }
 
 // ---------------------------------------------------------------- GEMM
@@ -539,7 +528,7 @@ struct OzGemmParams {
   unsigned long long wait_ns;  // limit of each pipeline wait (device time)
 };
 
-template <int S, int BN, bool A8 = false>
+template <int S, int BN>
 struct OzCfg {
   static constexpr int tileA = kBM * kBK * 2;  // bytes per slice tile
   static constexpr int tileB = BN * kBK * 2;
@@ -552,14 +541,9 @@ struct OzCfg {
   // one CTA's pipeline fill and accumulator drain overlap the other's MMAs
   static constexpr bool dual = !exact && cols <= 256;
   static constexpr int min_blocks = dual ? 2 : 1;
-  // int8 A digits (A8): two staging buffers of half a stage's A digits each,
-  // filled by bulk copies and expanded to BF16 into the stage by `conv` warps
-  static constexpr int half8 = A8 ? (S / 2) * kBM * kBK : 0;
-  static constexpr int stg = 2 * half8;
-  static constexpr int conv = A8 ? 2 : 0;
-  static constexpr int budget = (dual ? 115712 - 2048 : 220 * 1024 - 2048) - stg;
+  static constexpr int budget = dual ? 115712 - 2048 : 220 * 1024 - 2048;
   static constexpr int nst = budget / stage < 4 ? budget / stage : 4;
-  static constexpr int smem = nst * stage + stg + 2048;  // + barriers and 1024-byte alignment slack
+  static constexpr int smem = nst * stage + 2048;  // + barriers and 1024-byte alignment slack
   static constexpr uint32_t tcols = cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : cols <= 256 ? 256 : 512;
   // S = 8: levels 0..5 are kept exact (chunks of 512 k keep their integer
   // sums at most 2^24; levels 6, 7 weigh less than 2^-42, where FP32 rounding
@@ -569,8 +553,7 @@ struct OzCfg {
   // three when exact (BN/3 columns each, so the integer state fits in
   // registers), one when two CTAs share the SM
   static constexpr int epi = exact ? 12 : dual ? 4 : 8;
-  static constexpr int threads = 32 * (2 + epi + conv);
-  static_assert(!A8 || (S % 2 == 0 && !dual), "int8 A digits: an even number of digits, one CTA per SM");
+  static constexpr int threads = 32 * (2 + epi);
   static_assert(!exact || S == 7 || S == 8, "the integer epilogue pairs the levels of 7 or 8 digits");
   static_assert(cols <= 512, "levels x BN must fit in tensor memory");
   static_assert(nst >= 2, "need at least two pipeline stages");
@@ -578,37 +561,17 @@ struct OzCfg {
   static_assert(smem <= 232448, "shared memory per CTA");
 };
 
-// Four int8 digits d in [-64, 63] (one word) -> four BF16 (two words), exact
-// and without conversion instructions: v = d + 64 = (b ^ 0x40) & 0x7F per
-// byte (one LOP3 for all four), the byte permute puts 0x43 above each v
-// (the BF16 pattern of 128 + v = 192 + d, exact since 128 <= 192 + d < 256),
-// and one BF16x2 subtraction of 192 per pair leaves d.
-__device__ __forceinline__ void s8x4_bf16(uint32_t w, uint32_t& lo, uint32_t& hi) {
-  const uint32_t v = (w ^ 0x40404040u) & 0x7F7F7F7Fu;
-  const uint32_t p0 = __byte_perm(v, 0x43434343u, 0x4140);  // bytes v0, 0x43, v1, 0x43
-  const uint32_t p1 = __byte_perm(v, 0x43434343u, 0x4342);  // bytes v2, 0x43, v3, 0x43
-  const __nv_bfloat162 c = __floats2bfloat162_rn(192.0f, 192.0f);
-  const __nv_bfloat162 r0 = __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&p0), c);
-  const __nv_bfloat162 r1 = __hsub2(*reinterpret_cast<const __nv_bfloat162*>(&p1), c);
-  lo = *reinterpret_cast<const uint32_t*>(&r0);
-  hi = *reinterpret_cast<const uint32_t*>(&r1);
-}
-
-template <int S, int BN, bool A8>
-__global__ void __launch_bounds__(OzCfg<S, BN, A8>::threads, OzCfg<S, BN, A8>::min_blocks) k_oz_gemm(OzGemmParams P) {
-  using Cfg = OzCfg<S, BN, A8>;
+template <int S, int BN>
+__global__ void __launch_bounds__(OzCfg<S, BN>::threads, OzCfg<S, BN>::min_blocks) k_oz_gemm(OzGemmParams P) {
+  using Cfg = OzCfg<S, BN>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* stg = smem + Cfg::nst * Cfg::stage;  // int8 staging (A8)
-  uint64_t* full = reinterpret_cast<uint64_t*>(stg + Cfg::stg);
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + Cfg::nst * Cfg::stage);
   uint64_t* empty = full + Cfg::nst;
   uint64_t* acc_full = empty + Cfg::nst;
   uint64_t* acc_empty = acc_full + 1;
   uint64_t* drain = acc_empty + 1;
-  uint64_t* sfull = drain + 1;    // A8: staging buffer h holds its copy
-  uint64_t* sempty = sfull + 2;   // A8: staging buffer h was read
-  uint64_t* bfull = sempty + 2;   // A8: the stage's B digits have landed (full[]: its A digits are expanded)
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bfull + Cfg::nst);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
   int* abort_flag = reinterpret_cast<int*>(tmem_slot + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
@@ -646,15 +609,8 @@ __global__ void __launch_bounds__(OzCfg<S, BN, A8>::threads, OzCfg<S, BN, A8>::m
 
   if (threadIdx.x == 0) {
     for (int i = 0; i < Cfg::nst; ++i) {
-      mbar_init(&full[i], A8 ? Cfg::conv : 1);
+      mbar_init(&full[i], 1);
       mbar_init(&empty[i], 1);
-      if (A8) mbar_init(&bfull[i], 1);
-    }
-    if (A8) {
-      for (int i = 0; i < 2; ++i) {
-        mbar_init(&sfull[i], 1);
-        mbar_init(&sempty[i], Cfg::conv);
-      }
     }
     mbar_init(acc_full, 1);
     mbar_init(acc_empty, Cfg::epi);
@@ -678,11 +634,10 @@ __global__ void __launch_bounds__(OzCfg<S, BN, A8>::threads, OzCfg<S, BN, A8>::m
       const unsigned char* gA = reinterpret_cast<const unsigned char*>(P.A);
       const unsigned char* gB = reinterpret_cast<const unsigned char*>(P.B);
       int64_t g = 0;  // stages issued so far (all tiles)
-      int64_t q = 0;  // A8: staging copies issued so far
       for (int64_t t = blockIdx.x; t < ntiles && !*(volatile int*)abort_flag; t += gridDim.x) {
         const Tile T = tile_at(t);
         if (T.skip) continue;
-        for (int64_t it = 0; it < T.nk; ++it) {
+        for (int64_t it = 0; it < T.nk; ++it, ++g) {
           const int st = int(g % Cfg::nst);
           const int64_t round = g / Cfg::nst;
           if (round > 0 && !mbar_wait(&empty[st], uint32_t((round - 1) & 1), P.err, P.wait_ns)) {
@@ -694,40 +649,15 @@ __global__ void __launch_bounds__(OzCfg<S, BN, A8>::threads, OzCfg<S, BN, A8>::m
           const int64_t kt = T.kt_lo + it;
           unsigned char* sA = smem + st * Cfg::stage;
           unsigned char* sB = sA + Cfg::stageA;
-          if constexpr (A8) {
-            // B digits straight into the stage; the A digits (int8, half a
-            // stage at a time) into the staging buffers for the expansion warps
-            mbar_expect_tx(&bfull[st], Cfg::stageB);
-            bulk_g2s(sB, gB + (T.nt * P.bkst + kt) * int64_t(Cfg::stageB), Cfg::stageB, &bfull[st]);
-            ++g;
-            const unsigned char* a8 = gA + (T.mt * P.akst + kt) * int64_t(2 * Cfg::half8);
-            for (int hh = 0; hh < 2; ++hh) {
-              const int hb = int(q & 1);
-              if (q >= 2 && !mbar_wait(&sempty[hb], uint32_t(((q >> 1) - 1) & 1), P.err, P.wait_ns)) {
-                set_err(P.err, 17);
-                *(volatile int*)abort_flag = 1;
-                break;
-              }
-              mbar_expect_tx(&sfull[hb], Cfg::half8);
-              bulk_g2s(stg + hb * Cfg::half8, a8 + hh * Cfg::half8, Cfg::half8, &sfull[hb]);
-              ++q;
-            }
-            if (*(volatile int*)abort_flag) break;
-          } else {
-            mbar_expect_tx(&full[st], Cfg::stageA + Cfg::stageB);
-            bulk_g2s(sA, gA + (T.mt * P.akst + kt) * int64_t(Cfg::stageA), Cfg::stageA, &full[st]);
-            bulk_g2s(sB, gB + (T.nt * P.bkst + kt) * int64_t(Cfg::stageB), Cfg::stageB, &full[st]);
-            ++g;
-          }
+          mbar_expect_tx(&full[st], Cfg::stageA + Cfg::stageB);
+          bulk_g2s(sA, gA + (T.mt * P.akst + kt) * int64_t(Cfg::stageA), Cfg::stageA, &full[st]);
+          bulk_g2s(sB, gB + (T.nt * P.bkst + kt) * int64_t(Cfg::stageB), Cfg::stageB, &full[st]);
         }
       }
       // copies that were issued but never consumed must land before exit
       if (*(volatile int*)abort_flag) {
         const int64_t first = g > Cfg::nst ? g - Cfg::nst : 0;
-        for (int64_t it = first; it < g; ++it)
-          mbar_wait(A8 ? &bfull[it % Cfg::nst] : &full[it % Cfg::nst], uint32_t((it / Cfg::nst) & 1), nullptr);
-        if (A8)
-          for (int64_t x = q > 2 ? q - 2 : 0; x < q; ++x) mbar_wait(&sfull[x & 1], uint32_t((x >> 1) & 1), nullptr);
+        for (int64_t it = first; it < g; ++it) mbar_wait(&full[it % Cfg::nst], uint32_t((it / Cfg::nst) & 1), nullptr);
       }
     }
   } else if (warp == 1) {
@@ -748,8 +678,7 @@ __global__ void __launch_bounds__(OzCfg<S, BN, A8>::threads, OzCfg<S, BN, A8>::m
             stop = true;
             break;
           }
-          if ((A8 && !mbar_wait(&bfull[st], uint32_t(round & 1), P.err, P.wait_ns)) ||
-              !mbar_wait(&full[st], uint32_t(round & 1), P.err, P.wait_ns)) {
+          if (!mbar_wait(&full[st], uint32_t(round & 1), P.err, P.wait_ns)) {
             set_err(P.err, 13);
             *(volatile int*)abort_flag = 1;
             stop = true;
@@ -793,62 +722,6 @@ __global__ void __launch_bounds__(OzCfg<S, BN, A8>::threads, OzCfg<S, BN, A8>::m
       // all MMAs issued by this thread complete before tensor memory is freed
       umma_commit(drain);
       mbar_wait(drain, 0, nullptr);
-    }
-  } else if (A8 && warp >= 2 + Cfg::epi) {
-    // ------------------------------------------------ A digit expansion (int8 -> BF16)
-    // Each staging buffer holds half a stage's A digits in the tile layout,
-    // one byte per element; element e becomes BF16 element e of the stage's
-    // A area (bytes 2e), so the UMMA layout carries over unchanged.
-    const int ct = int(threadIdx.x) - 32 * (2 + Cfg::epi);
-    int64_t g = 0, q = 0;
-    bool stop = false;
-    for (int64_t t = blockIdx.x; t < ntiles && !stop; t += gridDim.x) {
-      const Tile T = tile_at(t);
-      if (T.skip) continue;
-      for (int64_t it = 0; it < T.nk; ++it, ++g) {
-        const int st = int(g % Cfg::nst);
-        const int64_t round = g / Cfg::nst;
-        if (round > 0 && !mbar_wait(&empty[st], uint32_t((round - 1) & 1), P.err, P.wait_ns)) {
-          set_err(P.err, 15);
-          *(volatile int*)abort_flag = 1;
-          stop = true;
-          break;
-        }
-        uint4* dA = reinterpret_cast<uint4*>(smem + st * Cfg::stage);
-        for (int hh = 0; hh < 2; ++hh, ++q) {
-          const int hb = int(q & 1);
-          if (!mbar_wait(&sfull[hb], uint32_t((q >> 1) & 1), P.err, P.wait_ns)) {
-            set_err(P.err, 16);
-            *(volatile int*)abort_flag = 1;
-            stop = true;
-            break;
-          }
-          if (*(volatile int*)abort_flag) {
-            stop = true;
-            break;
-          }
-          const uint4* src = reinterpret_cast<const uint4*>(stg + hb * Cfg::half8);
-          uint4* dst = dA + hh * (Cfg::half8 / 8);
-#pragma unroll 4
-          for (int c = ct; c < Cfg::half8 / 16; c += 32 * Cfg::conv) {
-            const uint4 v = src[c];
-            uint4 o0, o1;
-            s8x4_bf16(v.x, o0.x, o0.y);
-            s8x4_bf16(v.y, o0.z, o0.w);
-            s8x4_bf16(v.z, o1.x, o1.y);
-            s8x4_bf16(v.w, o1.z, o1.w);
-            dst[2 * c] = o0;
-            dst[2 * c + 1] = o1;
-          }
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&sempty[hb]);
-        }
-        if (stop) break;
-        // the expanded digits are read by tcgen05.mma (async proxy)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&full[st]);
-      }
     }
   } else {
     // ------------------------------------------------ epilogue warps
@@ -1023,9 +896,9 @@ __global__ void k_oz_reduce(const double* __restrict__ work, int splits, int64_t
 // then overlaps the next tile's copies and MMAs); else one CTA per tile, the
 // hardware scheduler balancing tiles of uneven length (split or triangular
 // products) across the SMs.
-template <int S, int BN, bool A8 = false>
+template <int S, int BN>
 void launch_oz(const OzGemmParams& P, bool persistent, cudaStream_t s) {
-  using Cfg = OzCfg<S, BN, A8>;
+  using Cfg = OzCfg<S, BN>;
   // the shared-memory attributes belong to the current device: set them, and
   // count the CTAs of this configuration the device holds at once, per device
   static std::atomic<int> resident[kMaxDevices];
@@ -1036,43 +909,40 @@ void launch_oz(const OzGemmParams& P, bool persistent, cudaStream_t s) {
   }
   int res = resident[dev].load(std::memory_order_acquire);
   if (!res) {
-    cudaFuncSetAttribute(k_oz_gemm<S, BN, A8>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::smem);
-    cudaFuncSetAttribute(k_oz_gemm<S, BN, A8>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg::smem);
+    cudaFuncSetAttribute(k_oz_gemm<S, BN>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
     int nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_oz_gemm<S, BN, A8>, Cfg::threads, Cfg::smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_oz_gemm<S, BN>, Cfg::threads, Cfg::smem);
     cudaGetLastError();
     res = std::max(1, nsm) * std::max(1, per);
     resident[dev].store(res, std::memory_order_release);
   }
   const int64_t ntiles = P.ntn * P.ntm * P.splits;
   const unsigned grid = unsigned(std::max<int64_t>(1, persistent ? std::min<int64_t>(ntiles, res) : ntiles));
-  k_oz_gemm<S, BN, A8><<<grid, Cfg::threads, Cfg::smem, s>>>(P);
+  k_oz_gemm<S, BN><<<grid, Cfg::threads, Cfg::smem, s>>>(P);
 }
 
 }  // namespace
 
-int64_t oz_tile_bytes(const OzOperand& op) {
-  return op.nrt * op.kst * op.S * int64_t(op.rt) * kBK * op.eb;
-}
+int64_t oz_tile_bytes(const OzOperand& op) { return op.nrt * op.kst * op.S * int64_t(op.rt) * kBK * 2; }
 
 int64_t oz_tile_elems(int64_t rows, int64_t K, int rt, int S) {
   const int64_t nrt = (rows + rt - 1) / rt, nkt = (K + kBK - 1) / kBK;
   return nrt * nkt * S * int64_t(rt) * kBK;
 }
 
-isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, int S, const char* what, bool i8) {
+isdf_status oz_alloc(Plan* p, OzOperand& op, int64_t rows, int64_t K, int rt, int S, const char* what) {
   op.rows = rows;
   op.K = K;
   op.tiles = nullptr;
   op.exps = nullptr;
   op.rt = rt;
   op.S = S;
-  op.eb = i8 ? 1 : 2;
   op.nrt = (rows + rt - 1) / rt;
   op.nkt = (K + kBK - 1) / kBK;
   op.kst = op.nkt;
-  isdf_status st = dalloc(p, &op.tiles, size_t(oz_tile_bytes(op)), what);
+  isdf_status st = dalloc(p, &op.tiles, size_t(oz_tile_elems(rows, K, rt, S)) * 2, what);
   if (st) return st;
   return dalloc_t(p, &op.exps, size_t(op.nrt * rt), what);
 }
@@ -1084,19 +954,6 @@ void oz_free(OzOperand& op) {
   op.exps = nullptr;
 }
 
-namespace {
-// int8 slices: every row scale two powers of two higher (see OzOperand)
-__global__ void k_oz_exp_bump(int64_t rows, int* __restrict__ exps) {
-  const int64_t r = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
-  if (r < rows) exps[r] += 2;
-}
-void bump_if_i8(OzOperand& op, cudaStream_t s) {
-  if (op.eb != 1 || op.rows <= 0) return;
-  k_oz_exp_bump<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(op.rows, op.exps);
-  count_launches(1);
-}
-}  // namespace
-
 void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, double mul, OzOperand& op, cudaStream_t s) {
   const bool rowwise = sr >= sk;  // k contiguous: one block per row
   const OzMap rm = oz_stride(sr), km = oz_stride(sk);
@@ -1107,7 +964,6 @@ void oz_slice(const double* src, int64_t sr, int64_t sk, const double* kw, doubl
     k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, kw, mul, nullptr,
                                                                         op.exps);
   }
-  bump_if_i8(op, s);
   launch_digits(src, rm, km, kw, mul, nullptr, op, 0, op.nkt * (kBK / 8), rowwise ? 1 : 0, s);
   count_launches(2);
 }
@@ -1136,7 +992,6 @@ void oz_slice_ex(const double* src, int64_t sr, int64_t sk, const int* ridx, OzO
       k_oz_rowexp_thread<<<unsigned((op.rows + 255) / 256), 256, 0, s>>>(src, rm, km, op.rows, op.K, nullptr, 1.0,
                                                                           ridx, op.exps);
     count_launches(1);
-    bump_if_i8(op, s);
   }
   launch_digits(src, rm, km, nullptr, 1.0, ridx, op, kg0, kg1 - kg0, rowwise ? 1 : 0, s);
   count_launches(1);
@@ -1147,12 +1002,6 @@ int oz_bn(int S) { return S == 6 ? 64 : 48; }
 
 void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int trans, double alpha, int tri, int sym,
              int splits, double* work, int* err, cudaStream_t s) {
-  if (A.eb == 1 && (A.S != 8 || B.S != 8 || B.eb != 2)) {
-    // int8 A digits exist for the 8-digit product against BF16 B digits only
-    const int code = 18;
-    cudaMemcpyAsync(err, &code, sizeof(int), cudaMemcpyHostToDevice, s);
-    return;
-  }
   OzGemmParams P;
   P.A = static_cast<const __nv_bfloat16*>(A.tiles);
   P.B = static_cast<const __nv_bfloat16*>(B.tiles);
@@ -1186,9 +1035,7 @@ void oz_gemm(const OzOperand& A, const OzOperand& B, double* C, int64_t ldc, int
   // per SM already overlap their epilogues) and on split or triangular
   // products one CTA per tile is faster.
   const bool persistent = A.S >= 7 && P.splits == 1 && !P.sym && P.tri == 0 && P.nkt * kBK <= 4096;
-  if (A.eb == 1)  // int8 A digits (8 digits; B is always BF16)
-    launch_oz<8, 48, true>(P, persistent, s);
-  else if (A.S == 5)
+  if (A.S == 5)
     launch_oz<5, 48>(P, persistent, s);
   else if (A.S == 8)
     launch_oz<8, 48>(P, persistent, s);

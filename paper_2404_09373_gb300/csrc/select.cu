@@ -654,14 +654,13 @@ __global__ void k_blk_combine(double* __restrict__ aL, const double* __restrict_
 }
 
 // per-candidate power-of-two bound of the factor rows: sum_k L[t,k]^2 <= d0(t)
-// Fixed row scales of the factor columns: |L[c][k]| <= sqrt(d0_c); the int8
-// digit planes take two powers of two more (see OzOperand)
+// Fixed row scales of the factor columns: |L[c][k]| <= sqrt(d0_c)
 __global__ void k_fac_exps(const double* __restrict__ d0c, int64_t nc, int64_t npad, int* __restrict__ exps) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (t >= npad) return;
   int e = 0;
   if (t < nc && d0c[t] > 0.0) frexp(sqrt(d0c[t]) * (1.0 + 0x1p-20), &e);
-  exps[t] = e + 2;
+  exps[t] = e;
 }
 
 __global__ void k_blk_begin(SelState* st) {
@@ -1262,16 +1261,14 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
     }
     Q.gpos[l] = b.gpos;
     const int bn = oz_bn(kSlices);
-    // candidate-side digit planes in int8 (half the bytes of the stream the
-    // products read), the speculative set's in BF16
-    if ((st = oz_alloc(p, b.aL, nc[l], std::max(lv.nL, 1), 128, kSlices, "selection slices", true)) ||
+    if ((st = oz_alloc(p, b.aL, nc[l], std::max(lv.nL, 1), 128, kSlices, "selection slices")) ||
         (st = oz_alloc(p, b.bL, smax, std::max(lv.nL, 1), bn, kSlices, "selection slices")) ||
-        (st = oz_alloc(p, b.aF, nc[l], lv.fac_cap, 128, kSlices, "selection slices", true)) ||
+        (st = oz_alloc(p, b.aF, nc[l], lv.fac_cap, 128, kSlices, "selection slices")) ||
         (st = oz_alloc(p, b.bF, smax, lv.fac_cap, bn, kSlices, "selection slices")) ||
         (st = dalloc_t(p, &b.cL, size_t(smax) * nc[l], "selection columns")) ||
         (st = dalloc_t(p, &b.cF, size_t(smax) * nc[l], "selection columns")))
       return bail(st);
-    if (lv.nN > 0 && ((st = oz_alloc(p, b.aN, nc[l], lv.nN, 128, kSlices, "selection slices", true)) ||
+    if (lv.nN > 0 && ((st = oz_alloc(p, b.aN, nc[l], lv.nN, 128, kSlices, "selection slices")) ||
                       (st = oz_alloc(p, b.bN, smax, lv.nN, bn, kSlices, "selection slices")) ||
                       (st = dalloc_t(p, &b.cN, size_t(smax) * nc[l], "selection columns"))))
       return bail(st);
@@ -1444,7 +1441,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
         if (lv.nN > 0)
           oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, ci, b.aN, 0, b.aN.nkt * (kOzBK / 8), false, s);
         const int64_t kst_keep = b.aF.kst;
-        cudaMemsetAsync(b.aF.tiles, 0, size_t(b.aF.nrt) * size_t(kst_keep) * kSlices * 128 * kOzBK * b.aF.eb, s);
+        cudaMemsetAsync(b.aF.tiles, 0, size_t(b.aF.nrt) * size_t(kst_keep) * kSlices * 128 * kOzBK * 2, s);
         k_fac_exps<<<unsigned((b.aF.nrt * 128 + 255) / 256), 256, 0, s>>>(d0c, nn, b.aF.nrt * 128, b.aF.exps);
         count_launches(1);
         if (h.kl[l] > 0) oz_slice_ex(fnew, 1, nn, nullptr, b.aF, 0, (h.kl[l] + 7) / 8, true, s);
@@ -1508,7 +1505,7 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
       }
       oz_free(b.aF);
       oz_free(b.bF);
-      if ((gst = oz_alloc(p, b.aF, nc[l], cap, 128, kSlices, "selection slices", true)) ||
+      if ((gst = oz_alloc(p, b.aF, nc[l], cap, 128, kSlices, "selection slices")) ||
           (gst = oz_alloc(p, b.bF, smax, cap, oz_bn(kSlices), kSlices, "selection slices"))) {
         dfree(fnew), dfree(d0c);
         return gst;
