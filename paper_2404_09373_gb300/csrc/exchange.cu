@@ -141,7 +141,7 @@ GemmArgs gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, const double* A, 
 isdf_status tc_product(Plan* p, const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t N,
                        int64_t sbr, int64_t sbk, int64_t K, double* C, int64_t ldc, int sym) {
   cudaStream_t s = p->stream;
-  const int S = 5;
+  const int S = p->ex_slices;
   OzOperand A, B;
   double* work = nullptr;
   isdf_status st;
@@ -166,7 +166,7 @@ isdf_status tc_product(Plan* p, const double* a, int64_t M, int64_t sar, int64_t
 
 }  // namespace
 
-isdf_status tc_product5(Plan* p, const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t N,
+isdf_status tc_product_ex(Plan* p, const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t N,
                         int64_t sbr, int64_t sbk, int64_t K, double* C, int64_t ldc) {
   return tc_product(p, a, M, sar, sak, b, N, sbr, sbk, K, C, ldc, 0);
 }

@@ -131,6 +131,11 @@ struct Plan {
   // 8 (FP64-grade) on an atom's local grid, where a threshold-driven
   // selection leaves CC^T conditioned up to the inverse of the threshold
   int fit_slices = 5;
+  // BF16 digits of the exchange build's tensor-core products: 5, or 8
+  // (FP64-grade) with local grids, whose V carries W = (CC^T)^-1 of
+  // threshold-driven atom selections (entries up to cond(CC^T) times larger
+  // than K, which forms by cancellation)
+  int ex_slices = 5;
   // profiling
   std::vector<ProfEvent> pend;
   std::map<std::string, KStat> stats;
@@ -178,8 +183,8 @@ isdf_status sinc_exchange(Plan* p, const double* dC, const double* yl, const dou
 void fold_spectra(int k, const double2* spf, int fx, int fy, int fz, double2* H, int cx, int cy, int cz,
                   cudaStream_t s);
 isdf_status transform_real(Plan* p, const double* f, int nx, int ny, int nz, int64_t batch, double2* spec);
-// 5-digit tensor-core product C = A B^T over strided operands (exchange.cu)
-isdf_status tc_product5(Plan* p, const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t N,
+// the exchange build's tensor-core product C = A B^T over strided operands (exchange.cu)
+isdf_status tc_product_ex(Plan* p, const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t N,
                         int64_t sbr, int64_t sbk, int64_t K, double* C, int64_t ldc);
 // dK (N x N) and dKC (N x n, K C) are nullable; exchange.cu
 isdf_status exchange_run(Plan* p, const double* dC, int n, double* dK, double* dKC, double* Ex);

@@ -255,7 +255,7 @@ isdf_status sinc_exchange(Plan* p, const double* dC, const double* yl, const dou
   // exchange build; FP64 SIMT at precision 0
   auto prod = [&](const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t Nn, int64_t sbr,
                   int64_t sbk, int64_t K, double* C, int64_t ldc) {
-    return p->opt.precision == 1 ? tc_product5(p, a, M, sar, sak, b, Nn, sbr, sbk, K, C, ldc)
+    return p->opt.precision == 1 ? tc_product_ex(p, a, M, sar, sak, b, Nn, sbr, sbk, K, C, ldc)
                                  : product(p, a, M, sar, sak, b, Nn, sbr, sbk, K, C, ldc, 5);
   };
   isdf_status st;
