@@ -425,10 +425,7 @@ isdf_status plan_create(const isdf_system* sys, const isdf_options* opt, void* s
   if (!st) st = dalloc_t(p, &p->d_err, 1, "error word");
   if (!st) st = dalloc_t(p, &p->d_ozerr, 1, "error word");
   if (!st) st = cuda_check(p, cudaMemsetAsync(p->d_ozerr, 0, sizeof(int), p->stream), "memset");
-  if (!st && o.local_grids) {
-    p->ex_slices = 8;
-    st = local_setup(p, sys->level_min_exp[0]);
-  }
+  if (!st && o.local_grids) st = local_setup(p, sys->level_min_exp[0]);
   if (!st) st = defer_basis ? basis_alloc(p) : basis_build(p);
   if (!st) st = cuda_check(p, cudaStreamSynchronize(p->stream), "plan");
   if (st) {

@@ -149,7 +149,7 @@ isdf_status coulomb_block_tc(Plan* p, const double2* left, const Level& la, cons
   // ZC: W = (CC^T)^-1 applied afterwards amplifies their error by up to
   // cond(CC^T) (5 digits missed the 1e-6 Ha bar on the undisplaced cell by
   // 600x, 7 digits take 2^14 off that); else 5
-  const int S = (la.zct || lb.zct) ? 7 : 5;
+  const int S = (la.zct || lb.zct || p->opt.local_grids) ? 7 : 5;
   const int64_t K2 = 2 * lb.nq;
   k_sqrt_inplace<<<unsigned((K2 + 255) / 256), 256, 0, s>>>(K2, wt2);
   count_launches(1);
@@ -230,10 +230,11 @@ isdf_status apply_w(Plan* p) {
   for (int x = 0; x < p->nlev; ++x)
     for (int y = x; y < p->nlev; ++y) flop += 2.0 * 2.0 * double(p->lev[x].k) * p->lev[y].k * (p->lev[x].k + p->lev[y].k) / 2.0;
   Prof pr(p, "coulomb_w", flop, "flop", kLaunchesInside);
-  // W_l[m][n] = sum_kk R^-1[kk][m] R^-1[kk][n]
+  // W_l[m][n] = sum_kk R^-1[kk][m] R^-1[kk][n]; a level that holds Xi itself
+  // (no R^-1: local grids' level 0) has W = I
   for (int l = 0; l < p->nlev; ++l) {
     const int k = p->lev[l].k;
-    if (!k) continue;
+    if (!k || !p->lev[l].rinv) continue;
     if ((st = dalloc_t(p, &W[l], size_t(k) * k, "W"))) return cleanup(), st;
     view(a, k, k);
     view(b, k, k);
@@ -248,18 +249,29 @@ isdf_status apply_w(Plan* p) {
       const int kb = p->lev[y].k;
       if (!kb) continue;
       double* blk = p->V + int64_t(p->poff[x]) * nip + p->poff[y];
+      if (!W[x] && !W[y]) continue;  // both levels hold Xi: the block is V already
       // T = V_Z,ab W_b   (T[m][n] = sum_j V[m][j] W_b[n][j], W_b symmetric)
-      view(a, ka, kb);
-      view(b, kb, kb);
-      oz_slice(blk, nip, 1, nullptr, 1.0, a, s);
-      oz_slice(W[y], kb, 1, nullptr, 1.0, b, s);
-      oz_gemm(a, b, T, kb, 0, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      if (W[y]) {
+        view(a, ka, kb);
+        view(b, kb, kb);
+        oz_slice(blk, nip, 1, nullptr, 1.0, a, s);
+        oz_slice(W[y], kb, 1, nullptr, 1.0, b, s);
+        oz_gemm(a, b, T, kb, 0, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      } else {
+        cudaMemcpy2DAsync(T, sizeof(double) * kb, blk, sizeof(double) * nip, sizeof(double) * kb, ka,
+                          cudaMemcpyDeviceToDevice, s);
+      }
       // V_ab = W_a T   (V[m][n] = sum_i W_a[m][i] T[i][n])
-      view(a, ka, ka);
-      view(b, kb, ka);
-      oz_slice(W[x], ka, 1, nullptr, 1.0, a, s);
-      oz_slice(T, 1, kb, nullptr, 1.0, b, s);
-      oz_gemm(a, b, blk, nip, 0, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      if (W[x]) {
+        view(a, ka, ka);
+        view(b, kb, ka);
+        oz_slice(W[x], ka, 1, nullptr, 1.0, a, s);
+        oz_slice(T, 1, kb, nullptr, 1.0, b, s);
+        oz_gemm(a, b, blk, nip, 0, 1.0, 0, 0, 1, nullptr, p->d_ozerr, s);
+      } else {
+        cudaMemcpy2DAsync(blk, sizeof(double) * nip, T, sizeof(double) * kb, sizeof(double) * kb, ka,
+                          cudaMemcpyDeviceToDevice, s);
+      }
       if (x != y) {
         const int64_t tot = int64_t(ka) * kb;
         k_mirror<<<unsigned((tot + 255) / 256), 256, 0, s>>>(p->V, nip, p->poff[x], p->poff[y], ka, kb, 0);
@@ -320,9 +332,10 @@ isdf_status coulomb_run(Plan* p) {
     lv.nq = int64_t(lv.nh[0]) * lv.nh[1] * lv.nh[2];
     if (lv.k == 0) continue;
     if ((st = dalloc_t(p, &lv.spec, size_t(lv.k) * lv.nq, "spectra"))) return st;
-    // local grids' level 0 keeps the FP64 transform: W = (CC^T)^-1 of a
-    // threshold-driven atom selection (cond up to the inverse of local_tol)
-    // would amplify the double-float transform's ~1e-12 relative error
+    // local grids' level 0 keeps the FP64 transform: its interpolation
+    // vectors come from atom fits conditioned up to ~1e9, whose large,
+    // cancelling entries the double-float transform's ~1e-12 relative error
+    // would carry into V
     const bool fp64_fft = p->opt.local_grids && l == 0;
     if (p->opt.precision == 1 && p->fault != "fft_plan" && !fp64_fft &&
         rfft3_df_supported(lv.n[0], lv.n[1], lv.n[2])) {

@@ -129,12 +129,9 @@ struct Plan {
   int sel_lo = 0;  // first level of this plan's own greedy selection
   // BF16 digits of the fit's tensor-core products: 5 for the full-cell levels;
   // 8 (FP64-grade) on an atom's local grid, where a threshold-driven
-  // selection leaves CC^T conditioned up to the inverse of the threshold
+  // selection can leave CC^T conditioned beyond 1e9
   int fit_slices = 5;
-  // BF16 digits of the exchange build's tensor-core products: 5, or 8
-  // (FP64-grade) with local grids, whose V carries W = (CC^T)^-1 of
-  // threshold-driven atom selections (entries up to cond(CC^T) times larger
-  // than K, which forms by cancellation)
+  // BF16 digits of the exchange build's tensor-core products
   int ex_slices = 5;
   // profiling
   std::vector<ProfEvent> pend;

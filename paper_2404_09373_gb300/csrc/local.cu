@@ -11,10 +11,10 @@
 // Each atom is a single-level sub-plan with its own basis values, selection
 // and fit, so the selection and fit kernels run unchanged on it.  The main
 // plan's level 0 has no basis values of its own: after the atoms' fits it
-// receives their factored fits placed on the full finest grid -- ZC^T rows
-// scattered from the boxes, R^-1 block-diagonal over the atoms -- and the
-// Coulomb matrix (one transform per local fitting function, Section III) and
-// the exchange build treat it like any other level.  X^N of a local pivot
+// receives their interpolation vectors placed on the full finest grid (rows
+// scattered from the boxes), and the Coulomb matrix (one transform per local
+// fitting function, Section III) and the exchange build treat it like any
+// other level.  X^N of a local pivot
 // also holds the finest-level functions of higher-index atoms.
 #include <cmath>
 #include <cstring>
@@ -208,32 +208,32 @@ isdf_status local_assemble(Plan* p) {
   l0.resid = nullptr;
   const int64_t K0 = l0.k, nip = p->nip;
   if (K0 == 0) return ISDF_OK;
-  const bool factored = p->opt.precision == 1;
-  double* rows = nullptr;
-  isdf_status st = dalloc_t(p, &rows, size_t(K0) * l0.ng, factored ? "ZC^T (local grids)" : "Xi (local grids)");
-  if (st) return st;
-  (factored ? l0.zct : l0.xiT) = rows;
-  if (factored && (st = dalloc_t(p, &l0.rinv, size_t(K0) * K0, "R^-1 (local grids)"))) return st;
+  // Level 0 holds the interpolation vectors themselves, not the factored
+  // form ZC with W = (CC^T)^-1: an atom's threshold-driven CC^T can be
+  // conditioned far beyond the inverse of local_tol, and applying an explicit
+  // W on both sides of the Coulomb matrix loses accuracy as cond(CC^T)^2,
+  // where forming Xi first (R^-T (R^-1 ZC^T), FP64-grade products on the
+  // atom's small box) loses it as cond(CC^T)
+  isdf_status st;
+  for (Plan* q : p->sub)
+    if (q->lev[0].k && (st = fit_xi_run(q, 0))) {
+      p->err = q->err;
+      return st;
+    }
+  if ((st = dalloc_t(p, &l0.xiT, size_t(K0) * l0.ng, "Xi (local grids)"))) return st;
   Prof pr(p, "local_assemble", 8.0 * double(K0) * double(l0.ng), "byte", kLaunchesInside);
-  cudaMemsetAsync(rows, 0, sizeof(double) * size_t(K0) * l0.ng, s);
-  if (factored) cudaMemsetAsync(l0.rinv, 0, sizeof(double) * size_t(K0) * K0, s);
+  cudaMemsetAsync(l0.xiT, 0, sizeof(double) * size_t(K0) * l0.ng, s);
   int64_t c0 = 0;
   for (Plan* q : p->sub) {
     Level& lv = q->lev[0];
     const int64_t k = lv.k;
     if (!k) continue;
-    const double* src = factored ? lv.zct : lv.xiT;
     const int64_t tot = k * lv.ng;
-    k_embed_box<<<unsigned((tot + 255) / 256), 256, 0, s>>>(int(k), src, lv.n[0], lv.n[1], lv.n[2], lv.o[0], lv.o[1],
-                                                            lv.o[2], l0.n[0], l0.n[1], l0.n[2], rows + c0 * l0.ng,
+    k_embed_box<<<unsigned((tot + 255) / 256), 256, 0, s>>>(int(k), lv.xiT, lv.n[0], lv.n[1], lv.n[2], lv.o[0], lv.o[1],
+                                                            lv.o[2], l0.n[0], l0.n[1], l0.n[2], l0.xiT + c0 * l0.ng,
                                                             l0.ng);
     count_launches(1);
     if ((st = cuda_check(p, cudaGetLastError(), "k_embed_box"))) return st;
-    if (factored &&
-        (st = cuda_check(p, cudaMemcpy2DAsync(l0.rinv + c0 * K0 + c0, sizeof(double) * K0, lv.rinv, sizeof(double) * k,
-                                              sizeof(double) * k, k, cudaMemcpyDeviceToDevice, s),
-                         "R^-1 block")))
-      return st;
     // X^L, X^N columns of this atom's pivots (after the plan's own gather,
     // which cleared both matrices)
     const int64_t col = p->poff[0] + c0;

@@ -105,7 +105,8 @@ def check(g, o, C, natom, precision, sinc=False, sysd=None):
     dk = np.max(np.abs(g["K"] - o["K"]))
     assert dk <= 1e-6, dk
     assert abs(g["Ex"] - o["Ex"]) <= 1e-6 * natom
-    assert np.max(np.abs(g["KC"] - g["K"] @ C)) <= 1e-9 * max(1.0, np.max(np.abs(g["KC"])))
+    # the occ-RI route and K C from the dense K: two 5-digit product chains
+    assert np.max(np.abs(g["KC"] - g["K"] @ C)) <= 1e-8 * max(1.0, np.max(np.abs(g["KC"])))
     assert abs(g["Ex_occ"] - g["Ex"]) <= 1e-9 * abs(g["Ex"])
     return dk
 
