@@ -181,3 +181,25 @@ def test_local_grids_refusals():
             B.isdf_features(plan)
     finally:
         plan.close()
+
+
+def test_local_grids_release_keeps_the_exchange():
+    """isdf_release_fit on a local-grid plan frees the atoms' boxes too; the
+    exchange afterwards is bitwise the one before and the box stays known."""
+    sysd, C = cell(seed=14)
+    N = S.nbasis(sysd)
+    plan = B.isdf_plan(sysd, {"precision": 1, "local_grids": 1, "prefilter": 1})
+    try:
+        piv, _ = B.isdf_select_points(plan, 2 * N)
+        B.isdf_fit(plan, piv)
+        B.isdf_coulomb(plan)
+        K1, E1 = B.isdf_exchange(plan, C)
+        box = B.isdf_get(plan, B.GET_LOCAL_BOX)
+        B.isdf_release_fit(plan)
+        K2, E2 = B.isdf_exchange(plan, C)
+        assert np.array_equal(K1, K2) and E1 == E2
+        assert np.array_equal(B.isdf_get(plan, B.GET_LOCAL_BOX), box)
+        with pytest.raises(B.IsdfError):
+            B.isdf_select_points(plan, 2 * N)
+    finally:
+        plan.close()
