@@ -87,6 +87,10 @@ isdf_status local_setup(Plan* p, double alpha_min) {
     q->opt.local_grids = 0;
     q->opt.coarse_sinc = 0;
     q->opt.profile = 0;
+    // an atom takes some tens of pivots over some ten thousand points: the
+    // step-by-step selection (four graph-captured kernels per step, same
+    // pivots) costs less there than the speculative blocks' set-up
+    q->opt.select_block = 0;
     q->fault = p->fault;
     q->fit_slices = 8;
     for (int a = 0; a < 3; ++a) q->edge[a] = p->edge[a];
