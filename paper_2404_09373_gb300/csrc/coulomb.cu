@@ -149,7 +149,7 @@ isdf_status coulomb_block_tc(Plan* p, const double2* left, const Level& la, cons
   // ZC: W = (CC^T)^-1 applied afterwards amplifies their error by up to
   // cond(CC^T) (5 digits missed the 1e-6 Ha bar on the undisplaced cell by
   // 600x, 7 digits take 2^14 off that); else 5
-  const int S = (la.zct || lb.zct || p->opt.local_grids) ? 7 : 5;
+  const int S = (la.zct || lb.zct) ? 7 : 5;
   const int64_t K2 = 2 * lb.nq;
   k_sqrt_inplace<<<unsigned((K2 + 255) / 256), 256, 0, s>>>(K2, wt2);
   count_launches(1);
@@ -332,13 +332,7 @@ isdf_status coulomb_run(Plan* p) {
     lv.nq = int64_t(lv.nh[0]) * lv.nh[1] * lv.nh[2];
     if (lv.k == 0) continue;
     if ((st = dalloc_t(p, &lv.spec, size_t(lv.k) * lv.nq, "spectra"))) return st;
-    // local grids' level 0 keeps the FP64 transform: its interpolation
-    // vectors come from atom fits conditioned up to ~1e9, whose large,
-    // cancelling entries the double-float transform's ~1e-12 relative error
-    // would carry into V
-    const bool fp64_fft = p->opt.local_grids && l == 0;
-    if (p->opt.precision == 1 && p->fault != "fft_plan" && !fp64_fft &&
-        rfft3_df_supported(lv.n[0], lv.n[1], lv.n[2])) {
+    if (p->opt.precision == 1 && p->fault != "fft_plan" && rfft3_df_supported(lv.n[0], lv.n[1], lv.n[2])) {
       // double-float transform on the FP32 pipes (the FP64 one is bound by the FP64 rate)
       Prof pr(p, "coulomb_fft", double(lv.k) * (8.0 * double(lv.ng) + 16.0 * double(lv.nq)), "byte", 3);
       if ((st = rfft3_df(p, lv.zct ? lv.zct : lv.xiT, lv.n[0], lv.n[1], lv.n[2], lv.k, lv.spec, s))) return st;
