@@ -14,8 +14,8 @@
 // receives their interpolation vectors placed on the full finest grid (rows
 // scattered from the boxes), and the Coulomb matrix (one transform per local
 // fitting function, Section III) and the exchange build treat it like any
-// other level.  X^N of a local pivot
-// also holds the finest-level functions of higher-index atoms.
+// other level.  X^N of a local pivot also holds the finest-level functions of
+// higher-index atoms.
 #include <cmath>
 #include <cstring>
 

@@ -94,11 +94,11 @@ def check(g, o, C, natom, precision, sinc=False, sysd=None):
             vr = np.max(np.abs(dV)) / np.max(np.abs(o["V"]))
             assert vr <= 1e-9, vr
         else:
-            # V = W (ZC^T v ZC) W with W = (CC^T)^-1 per atom and per level:
-            # W's conditioning (up to the inverse of local_tol on every atom)
-            # multiplies the products' rounding twice in the forward error, so
-            # V is compared in the conditioning-free form CC^T dV CC^T (the
-            # Coulomb matrix of the pair-density columns ZC)
+            # the atoms' Xi = ZC (CC^T)^-1 come from fits conditioned up to
+            # ~1e9 (and the coarser levels' V from W (ZC^T v ZC) W): the
+            # forward error of V carries that conditioning, so V is compared
+            # in the conditioning-free form CC^T dV CC^T (the Coulomb matrix
+            # of the pair-density columns ZC)
             M = pivot_gram(o, sysd)
             vr = np.max(np.abs(M @ dV @ M)) / np.max(np.abs(M @ o["V"] @ M))
             assert vr <= 1e-7, vr
@@ -203,3 +203,30 @@ def test_local_grids_release_keeps_the_exchange():
             B.isdf_select_points(plan, 2 * N)
     finally:
         plan.close()
+
+
+def test_local_grids_in_a_batch_and_one_exchange_graph():
+    """Local-grid plans made by isdf_plan_batch (the atoms' boxes evaluated in
+    the batch's one basis launch) and their exchange builds captured into one
+    graph give the results of the same cells planned and run one by one."""
+    cells = [cell(seed=21), cell(reps=(1, 1, 2), seed=22)]
+    opts = {"precision": 1, "local_grids": 1, "prefilter": 1}
+    alone = [gpu_local(sysd, C, 2 * S.nbasis(sysd), opts) for sysd, C in cells]
+    plans = B.isdf_plan_batch([c[0] for c in cells], opts)
+    try:
+        for (sysd, C), p, a in zip(cells, plans, alone):
+            piv, _ = B.isdf_select_points(p, 2 * S.nbasis(sysd))
+            assert np.array_equal(piv, a["pivots"])
+            B.isdf_fit(p, piv)
+            B.isdf_coulomb(p)
+        g = B.ExchangeGraph(plans, [C.shape[1] for _, C in cells])
+        try:
+            Ks, exs = g.run([C for _, C in cells])
+        finally:
+            g.close()
+        for K, ex, a in zip(Ks, exs, alone):
+            # same kernels; a captured product may take another split-K factor
+            assert np.max(np.abs(K - a["K"])) <= 1e-9 and abs(ex - a["Ex"]) <= 1e-9 * abs(a["Ex"])
+    finally:
+        for p in plans:
+            p.close()
