@@ -57,7 +57,7 @@ def parse():
                          "cells as one captured CUDA graph")
     ap.add_argument("--learned", type=int, default=40,
                     help="train the point proposer on this many seeded 1x1x1/2x2x1 cells (0: skip), then time the "
-                         "learned path on the workload: 1.2 N_ip points among 4x as many candidates, residual check")
+                         "learned path on the workload: 1.1 N_ip points among 4x as many candidates, residual check")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-profile", action="store_true", help="skip the separately profiled step")
@@ -637,7 +637,7 @@ def main():
     local = soft(_sec_local)
 
     # ---- learned point proposal (trained here on a reduced set of cells; reported
-    # beside the main number): 1.2 N_ip points among 4x as many candidates; the
+    # beside the main number): 1.1 N_ip points among 4x as many candidates; the
     # residual trace (pair-fit error^2) of both paths measures their accuracy
     def _sec_learned():
         learned = None

@@ -654,6 +654,13 @@ __global__ void k_blk_combine(double* __restrict__ aL, const double* __restrict_
 }
 
 // per-candidate power-of-two bound of the factor rows: sum_k L[t,k]^2 <= d0(t)
+// Row scales of the speculative set's basis-value rows: those of the same
+// candidates' rows on the candidate side (the same rows, the same exact max)
+__global__ void k_gather_exps(const int* __restrict__ pos, int n, const int* __restrict__ src, int* __restrict__ dst) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r < n) dst[r] = src[pos[r]];
+}
+
 // Fixed row scales of the factor columns: |L[c][k]| <= sqrt(d0_c)
 __global__ void k_fac_exps(const double* __restrict__ d0c, int64_t nc, int64_t npad, int* __restrict__ exps) {
   const int64_t t = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -1559,12 +1566,19 @@ isdf_status select_loop_blocked(Plan* p, int nip, double tol, const double* d0fu
       };
       {
         // digits of S's rows: basis values and factor rows of the set
-        Prof pb(p, "select_sslice", 8.0 * sl * (lv.nL + lv.nN + kb), "byte", 6);
+        Prof pb(p, "select_sslice", 8.0 * sl * (lv.nL + lv.nN + kb), "byte", kLaunchesInside);
+        const unsigned gb = unsigned((sl + 127) / 128);
         setrows(b.bL, sl);
-        oz_slice_ex(lv.phi, 1, lv.ng, sg + soff, b.bL, 0, b.bL.nkt * (kOzBK / 8), false, s);
+        if (lv.nL > 0) {
+          k_gather_exps<<<gb, 128, 0, s>>>(stp + soff, sl, b.aL.exps, b.bL.exps);
+          count_launches(1);
+        }
+        oz_slice_ex(lv.phi, 1, lv.ng, sg + soff, b.bL, 0, b.bL.nkt * (kOzBK / 8), lv.nL > 0, s);
         if (lv.nN > 0) {
           setrows(b.bN, sl);
-          oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, sg + soff, b.bN, 0, b.bN.nkt * (kOzBK / 8), false, s);
+          k_gather_exps<<<gb, 128, 0, s>>>(stp + soff, sl, b.aN.exps, b.bN.exps);
+          count_launches(1);
+          oz_slice_ex(lv.phi + int64_t(lv.nL) * lv.ng, 1, lv.ng, sg + soff, b.bN, 0, b.bN.nkt * (kOzBK / 8), true, s);
         }
         if (kb > 0) {
           setrows(b.bF, sl);

@@ -138,7 +138,7 @@ def quotas(grids, level_density, nip, factor):
     return np.minimum(q, pts.astype(np.int64))
 
 
-def select_learned(plan, params, nip, level_density, factor=4, oversub=1.2, kappa=100.0, repair=1):
+def select_learned(plan, params, nip, level_density, factor=4, oversub=1.1, kappa=100.0, repair=1):
     """Candidate-restricted selection + fit with the residual check.
 
     The learned selection picks ``oversub * nip`` points among ``factor``

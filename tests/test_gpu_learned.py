@@ -168,7 +168,7 @@ def _timed_path(sysd, C, nip, opts, select):
 
 def test_learned_proposer_gains_over_the_full_selection():
     """What the trained network gains over the method without it (the full
-    pivoted selection of N_ip points).  The learned path selects 1.2 N_ip
+    pivoted selection of N_ip points).  The learned path selects 1.1 N_ip
     points among 4x as many proposed candidates.
 
     Accuracy, judged by the oracle: on the held-out 2x2x2 cell of the
