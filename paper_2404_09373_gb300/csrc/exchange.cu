@@ -141,7 +141,7 @@ GemmArgs gemm(int ta, int tb, int64_t M, int64_t N, int64_t K, const double* A, 
 isdf_status tc_product(Plan* p, const double* a, int64_t M, int64_t sar, int64_t sak, const double* b, int64_t N,
                        int64_t sbr, int64_t sbk, int64_t K, double* C, int64_t ldc, int sym) {
   cudaStream_t s = p->stream;
-  const int S = p->ex_slices;
+  const int S = 5;
   OzOperand A, B;
   double* work = nullptr;
   isdf_status st;

@@ -131,8 +131,6 @@ struct Plan {
   // 8 (FP64-grade) on an atom's local grid, where a threshold-driven
   // selection can leave CC^T conditioned beyond 1e9
   int fit_slices = 5;
-  // BF16 digits of the exchange build's tensor-core products
-  int ex_slices = 5;
   // profiling
   std::vector<ProfEvent> pend;
   std::map<std::string, KStat> stats;
