@@ -201,7 +201,9 @@ void isdf_options_default(isdf_options* opt);
 isdf_status isdf_plan(const isdf_system* sys, const isdf_options* opt, void* stream, isdf_plan_t* out);
 
 /* Plans for a batch of independent cells (cells of uneven size, each with
- * its own grids): isdf_plan for every systems[i] (plan i on streams[i]; a
+ * its own grids; the paper treats one cell at a time, so batching is an
+ * extension of this library, and every plan is exactly what isdf_plan makes
+ * for its cell: levels by exponent, Section II.B): isdf_plan for every systems[i] (plan i on streams[i]; a
  * NULL `streams` puts every plan on the legacy default stream), except that
  * the basis values of all cells and all levels are evaluated by one launch
  * of each basis kernel (1-D image-sum factors, then their outer products) on
@@ -377,14 +379,16 @@ isdf_status isdf_get(isdf_plan_t plan, int what, void* dst);
 const char* isdf_profile_json(isdf_plan_t plan);
 
 /* Number of kernels this library has launched in this process so far (its
- * own kernels; cuFFT's are not counted).  Host-side counter. */
+ * own kernels; cuFFT's are not counted).  Host-side counter; instrumentation
+ * of this library with no counterpart in the paper. */
 int64_t isdf_kernel_launches(void);
 
 /* ---- Learned point proposer (not in the paper: an extension of this
  * library).  A small network (8 inputs, two hidden layers of 64 with ReLU,
  * one logistic output; 4801 FP32 parameters in the order W1 8x64, b1, W2
  * 64x64, b2, W3 64, b3) scores grid points so that isdf_select_points can
- * run on a short candidate list.  The full selection stays the reference. */
+ * run on a short candidate list: the greedy of Section II.A, Eq. 2 then
+ * runs over those candidates only.  The full selection stays the reference. */
 
 int isdf_mlp_num_params(void);
 
@@ -509,7 +513,8 @@ isdf_status isdf_rfft3(const double* f, int nx, int ny, int nz, int64_t batch, d
  * isdf_plan when plan is NULL).  Valid until the next call. */
 const char* isdf_last_error(isdf_plan_t plan);
 
-/* Free every device buffer and the plan.  NULL is ignored. */
+/* Free every device buffer and the plan (resource management of this
+ * library; no counterpart in the paper).  NULL is ignored. */
 void isdf_destroy(isdf_plan_t plan);
 
 #ifdef __cplusplus
